@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused LBM step with curved-wall links and momentum exchange.
+
+Workload (default): D3Q19 periodic box 512x256x256, tau 0.6, fluid at rest,
+64 spheres of radius U[6,12] (seed 1407): even index static, odd index
+translating (|U| <= 0.02) and rotating (|W| <= 0.001); FP32 arithmetic with
+populations stored as f - w in FP32; per-body force and torque every step;
+cut-link lists and covered/uncovered sets rebuilt every step for the moving
+bodies.  One "step" is the whole path: geometry of the moving bodies, wall
+values + momentum exchange on every cut link, stream-collide of every cell,
+impulsive terms / refill, per-body reduction.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU (the path has no
+exchange step between solves); value = all cells updated / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+if "OMP_NUM_THREADS" not in os.environ:
+    os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "D3Q19 MLUPS + %HBM roofline w/ fused ME force; served-solve p50/p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _workload(name: str, precision: str):
+    from paper_1407_4524_gb300 import workloads as W
+    if name == "sphere_swarm_3d":
+        return W.sphere_swarm_3d(precision=precision)
+    if name == "sphere_channel_3d":
+        return W.sphere_channel_3d(precision=precision)
+    if name == "moving_cylinders_2d":
+        return W.moving_cylinders_2d(precision=precision)
+    if name == "channel_cylinder_2d":
+        return W.channel_cylinder_2d(precision=precision)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _describe(spec) -> str:
+    n = "x".join(str(v) for v in spec["n"])
+    nb = len(spec.get("bodies", []))
+    nm = sum(1 for b in spec.get("bodies", []) if any(np.abs(b.get("U", (0, 0, 0)))) or
+             any(np.atleast_1d(b.get("W", 0.0))))
+    return f"{spec['name']} {spec['lattice']} {n}, tau {spec['tau']}, {nb} bodies ({nm} moving)"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier_max(x: float, world: int):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(spec, budget_s: float = 15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload: a
+    periodic sub-box with the same lattice, tau and body density."""
+    import oracle
+    from paper_1407_4524_gb300 import workloads as W
+    if spec["lattice"] == "D3Q19" and spec["name"] == "sphere_swarm_3d":
+        sample = W.sphere_swarm_3d(precision="fp64", n=(128, 96, 96), n_bodies=2, seed=1407)
+        desc = "periodic 128x96x96 sub-box, 2 spheres (1 moving), same tau / radii / speeds"
+    else:
+        sample = dict(spec)
+        desc = "the full workload"
+    o = oracle.Oracle(sample)
+    cells = int(np.prod(o.shape))
+    o.step(1)  # warm-up
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 200:
+            break
+    mlups = cells * steps / el / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+            "kind": "oracle", "sample": f"{desc}; {steps} steps, {el:.1f} s, FP64"}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    spec = _workload(args.workload, "fp64")
+    import oracle
+    from paper_1407_4524_gb300 import workloads as W
+    # size the sample so that W + K oracle steps take a few minutes at most
+    probe = W.sphere_swarm_3d(precision="fp64", n=(64, 64, 64), n_bodies=1, seed=1407)
+    o = oracle.Oracle(probe)
+    t0 = time.perf_counter()
+    o.step(2)
+    rate = 2 * 64 ** 3 / (time.perf_counter() - t0)  # cell updates per second
+    budget = 150.0
+    cells_per_step = max(32 ** 3, min(512 * 256 * 256, rate * budget / max(1, args.steps + args.warmup)))
+    nz = max(32, int(round((cells_per_step / 4) ** (1 / 3) / 8)) * 8)
+    n = (4 * nz, nz, nz) if 4 * nz <= 512 else (512, min(256, nz), min(256, nz))
+    nbod = max(1, int(round(64 * np.prod(n) / (512 * 256 * 256))))
+    sample = W.sphere_swarm_3d(precision="fp64", n=n, n_bodies=nbod, seed=1407)
+    o = oracle.Oracle(sample)
+    cells = int(np.prod(o.shape))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    mlups = cells * args.steps / el / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / max(1, args.steps), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _describe(spec), "sample": "x".join(map(str, n)) + f", {nbod} spheres",
+                   "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"periodic {'x'.join(map(str, n))} sub-box of the workload, {nbod} spheres"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1407_4524_gb300 import lbm
+    spec = _workload(args.workload, args.precision)
+    stream = torch.cuda.Stream(dev)
+    dom = lbm.Domain(spec, device=dev, stream=stream, series_capacity=max(8192, args.steps + args.warmup + 16))
+    cells = dom.N
+    st0 = dom.stats()
+    fluid_cells = st0["fluid_cells"]
+    Q = dom.q
+    sbytes = {"fp64": 8, "fp32": 4, "fp16": 2}[args.precision]
+
+    # warm-up
+    dom.step(args.warmup)
+    torch.cuda.synchronize()
+    launches_per_step = dom.launches_per_step()
+
+    # device-timed region: K steps, events on the launching stream
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    dom.set_kernel_timing(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    dom.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n_bulk, bulk_ms = dom.kernel_time()
+    dom.set_kernel_timing(False)
+    clocks = sampler.stop() if sampler else None
+    ms = _barrier_max(ms, world)
+    mlups = world * cells * args.steps / (ms * 1e-3) / 1e6
+
+    # end-to-end through the C ABI with host buffers: each step uploads the
+    # bodies' kinematics (lbm_update_bodies) and reads the step's force/torque
+    # row back (lbm_get_force_torque)
+    bodies = list(dom.bodies)
+    nb = len(bodies)
+    out = np.zeros((1, max(nb, 1), 6))
+    e2e_steps = max(10, min(args.steps, 200))
+    s0 = dom.stats()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dom.update_bodies(bodies)
+        dom.step(1)
+        dom.lib.lbm_get_force_torque(dom.h, dom.t - 1, 1, 0, out.ctypes.data)
+    torch.cuda.synchronize()
+    e2e_s = _barrier_max(time.perf_counter() - t0, world)
+    s1 = dom.stats()
+    e2e = {"value": round(world * cells * e2e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / e2e_steps),
+           "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / e2e_steps)}
+
+    if rank != 0:
+        dom.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    bulk_avg_s = bulk_ms * 1e-3 / max(1, n_bulk)
+    alg_bytes = 2.0 * Q * sbytes * fluid_cells
+    achieved = alg_bytes / bulk_avg_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tpath) as fh:
+            tj = json.load(fh)
+        key = f"{args.workload}:{args.precision}"
+        if key in tj and tj[key].get("kernel_rev") == _kernel_rev():
+            traffic = tj[key]["bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_bulk (pull-stream + BGK collide)", "kernel_ms": round(bulk_avg_s * 1e3, 4),
+                "alg_bytes_per_launch": int(alg_bytes)}
+    step_frac = (bulk_ms / max(1e-9, ms)) if world == 1 else None
+    cpu = cpu_baseline(spec, budget_s=args.cpu_budget) if (world == 1 and not args.no_cpu) else None
+    line = {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": _describe(spec), "cells": cells, "fluid_cells": fluid_cells,
+                   "precision": args.precision + (" (f - w stored)" if args.precision != "fp64" else ""),
+                   "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * Q * sbytes * cells / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "bulk_share_of_step": round(step_frac, 4) if step_frac else None},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    dom.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _kernel_rev() -> str:
+    """hash of the kernel sources the traffic figure was taken on"""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1407_4524_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere_swarm_3d")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--print-kernel-rev", action="store_true")
+    args = ap.parse_args()
+    if args.print_kernel_rev:
+        print(_kernel_rev())
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice-Boltzmann library (liblbm.so).
+ *
+ * One library call advances a lattice-Boltzmann domain by BGK collision and
+ * streaming (Giovacchini & Ortiz, arXiv:1407.4524, Sec. 2, Eqs. LBE,
+ * collision, streaming) on the D2Q9 or D3Q19 lattice, applies the curved-wall
+ * rule on every cut solid link (Sec. 2.1, Eqs. Fillipova_interpolation and
+ * Fillipova_equilibrium) and accumulates, per body and per step, the
+ * momentum-exchange force and torque in the paper's static, moving
+ * (impulsive-correction) and moving-frame forms (Sec. 3, Eqs. flow_force_2,
+ * flow_torque_2, ForceInMovement, TorqueInMovement,
+ * ForceInMovementMovingFrame, TorqueInMovementMovingFrame).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status (LBM_OK = 0 on success).  On
+ *    failure lbm_last_error() returns a message for the calling thread.  The
+ *    library never aborts the process and never traps on the device.
+ *  - Pointers named host_* / out are HOST memory owned by the caller.  The
+ *    library owns every device buffer of a domain; it allocates them through
+ *    the optional allocator callbacks of the descriptor (so a caller can plug
+ *    in its own caching allocator) or with cudaMalloc.
+ *  - Work is enqueued asynchronously on the domain's CUDA stream; functions
+ *    that return data to the host synchronise that stream first.
+ *  - Lattice units: delta_x = delta_t = 1; velocities in cells per step.
+ *    Node (x, y, z) sits at integer coordinates; cell index
+ *    (z * ny + y) * nx + x; populations are laid out [Q][nz][ny][nx].
+ *  - Direction order (shared with every array the library returns):
+ *      D2Q9 : 0 rest, 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1),
+ *             5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1)
+ *      D3Q19: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z,
+ *             7 (1,1,0), 8 (-1,-1,0), 9 (1,-1,0), 10 (-1,1,0),
+ *             11 (1,0,1), 12 (-1,0,-1), 13 (1,0,-1), 14 (-1,0,1),
+ *             15 (0,1,1), 16 (0,-1,-1), 17 (0,1,-1), 18 (0,-1,1)
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_ERR_ARG 1      /* invalid argument or descriptor */
+#define LBM_ERR_OOM 2      /* device or host allocation failed */
+#define LBM_ERR_CUDA 3     /* a CUDA runtime call failed (message has the reason) */
+#define LBM_ERR_UNSTABLE 4 /* a NaN or |u| > 0.3 was detected in a checked step */
+#define LBM_ERR_TIMEOUT 5  /* a bounded device wait gave up (serving kernel) */
+#define LBM_ERR_STATE 6    /* call not allowed in the current state */
+
+/* ---- enumerations -------------------------------------------------------------- */
+#define LBM_D2Q9 9
+#define LBM_D3Q19 19
+
+/* Precision modes.  FP64: FP64 arithmetic and FP64 storage of f.
+ * FP32 / FP16: FP32 arithmetic, populations stored as deviations f_i - w_i
+ * in FP32 / FP16.  The momentum-exchange sums are FP64 in every mode. */
+#define LBM_FP64 0
+#define LBM_FP32 1
+#define LBM_FP16 2
+
+/* Equilibrium: quasi-incompressible model (Sec. 2, rho replaced by rho0 in
+ * the momentum) or the standard truncated Maxwellian. */
+#define LBM_EQ_INCOMP 0
+#define LBM_EQ_STANDARD 1
+
+/* Edge kinds for the six faces.  Walls and the inlet are links at
+ * Delta = 1/2 handled by the same curved-wall rule (u_B = 0 for walls,
+ * u_B = inlet profile at the wall point for the inlet); the outlet copies the
+ * last interior column (zero gradient).  Inlet only on x-low, outlet only on
+ * x-high; a wall takes precedence at corners. */
+#define LBM_EDGE_PERIODIC 0
+#define LBM_EDGE_WALL 1
+#define LBM_EDGE_INLET 2
+#define LBM_EDGE_OUTLET 3
+
+#define LBM_INLET_UNIFORM 0
+#define LBM_INLET_PARABOLIC 1 /* u_x(y) = 4 u_in (y+1/2)(ny-1/2-y)/ny^2 */
+
+/* Refill of nodes uncovered by a moving body (Sec. 3, after Eq.
+ * ForceInMovement): equilibrium at the mean density of the fluid neighbours
+ * with the body velocity at the node (default) or the neighbour-mean velocity. */
+#define LBM_REFILL_RHOBAR_UB 0
+#define LBM_REFILL_RHOBAR_UBAR 1
+
+#define LBM_SHAPE_CYLINDER 0 /* disc in the x-y plane (infinite along z in 3-D) */
+#define LBM_SHAPE_SPHERE 1
+
+/* Which force/torque form lbm_get_force_torque returns. */
+#define LBM_FT_STATIC 0    /* Eqs. flow_force_2 / flow_torque_2 */
+#define LBM_FT_LATTICE 1   /* Eqs. ForceInMovement / TorqueInMovement */
+#define LBM_FT_MOVING 2    /* Eqs. ForceInMovementMovingFrame / ... (last two terms dropped) */
+#define LBM_FT_IMPULSIVE 3 /* the A+/A- impulsive terms alone */
+
+/* Number of doubles per body per step in the raw series:
+ * Fs[3] Ts[3] (static form), Fi[3] Ti[3] (impulsive terms),
+ * Fm[3] Tm[3] (moving frame).  Torques are about the body centre at step t,
+ * r = x_A - X(t) taken at the fluid node x_A (Eq. H). */
+#define LBM_SERIES_ROW 18
+
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+
+typedef struct lbm_domain_desc {
+    int lattice;       /* LBM_D2Q9 or LBM_D3Q19 */
+    int nx, ny, nz;    /* nz = 1 for D2Q9; each >= 1 */
+    int precision;     /* LBM_FP64 / LBM_FP32 / LBM_FP16 */
+    int equilibrium;   /* LBM_EQ_* */
+    int edge[6];       /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: LBM_EDGE_* */
+    int inlet_profile; /* LBM_INLET_* */
+    int refill;        /* LBM_REFILL_* */
+    int has_force;     /* 1: Guo body force `force` (channel checks) */
+    int device;        /* CUDA device ordinal */
+    double tau;        /* BGK relaxation time, > 1/2 */
+    double rho0;       /* reference density (quasi-incompressible model) */
+    double u_in;       /* inlet velocity (maximum of the parabolic profile) */
+    double force[3];   /* body-force density */
+    double u0[3];      /* initial uniform velocity: f(x,0) = f^eq(1, u0) */
+    int64_t series_capacity; /* steps kept in the device force ring; 0 -> 8192 */
+    void *stream;            /* cudaStream_t to enqueue on; NULL -> default stream */
+    lbm_alloc_fn alloc;      /* optional device allocator (NULL -> cudaMalloc) */
+    lbm_free_fn free;        /* matching free */
+    void *alloc_ctx;         /* passed through to alloc / free */
+} lbm_domain_desc;
+
+typedef struct lbm_body {
+    int shape;       /* LBM_SHAPE_* */
+    int halfway;     /* 1: every cut link of the body takes Delta = 1/2 */
+    int reserved[2]; /* must be 0 */
+    double R;        /* radius */
+    double X0[3];    /* centre at step t0 */
+    double U[3];     /* translation velocity: X(t) = X0 + (t - t0) U */
+    double W[3];     /* angular velocity (2-D: W[2]) */
+    int64_t t0;      /* step at which the body is at X0 */
+} lbm_body;
+
+typedef struct lbm_stats {
+    int64_t step;            /* current time step t */
+    int64_t cells;           /* nx*ny*nz */
+    int64_t fluid_cells;     /* cells outside every body at t */
+    int64_t links;           /* cut body links at t */
+    int64_t fallback_links;  /* Delta < 1/2 links whose u_G node was missing
+                                (plain bounce-back used), summed over steps */
+    int64_t covered;         /* A+ nodes, summed over steps */
+    int64_t uncovered;       /* A- nodes, summed over steps */
+    int64_t device_bytes;    /* device memory held by the domain */
+    int64_t h2d_bytes;       /* bytes copied host -> device by API calls */
+    int64_t d2h_bytes;       /* bytes copied device -> host by API calls */
+} lbm_stats;
+
+typedef struct lbm_domain lbm_domain;
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *lbm_last_error(void);
+
+/* Library version string. */
+const char *lbm_version(void);
+
+/* Lattice tables in the direction order above: c[Q][3], w[Q], opp[Q]
+ * (host arrays, caller-owned).  Needs no GPU. */
+int lbm_lattice_table(int lattice, int *c, double *w, int *opp);
+
+/* Create a domain: validates the descriptor, allocates its device buffers,
+ * and sets f(x, 0) = f^eq(1, u0) everywhere (collided state of step 0).
+ * LBM_ERR_ARG for an invalid descriptor, LBM_ERR_OOM / LBM_ERR_CUDA on
+ * allocation or device failure (nothing is leaked). */
+int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out);
+
+/* Free every device buffer of the domain (synchronises its stream). */
+int lbm_destroy_domain(lbm_domain *dom);
+
+/* Place n bodies (host array, copied).  Allowed only at t = 0; rebuilds the
+ * solid flags and cut-link lists and re-initialises f(x,0).  Bodies must not
+ * overlap, must keep a surface gap >= 2 cells from each other and >= 3 cells
+ * from non-periodic faces, and must be smaller than half the domain on
+ * periodic axes (LBM_ERR_ARG otherwise).  Bodies with U or W != 0 move by the
+ * prescribed motion and have their links and A+/A- sets rebuilt every step. */
+int lbm_set_bodies(lbm_domain *dom, const lbm_body *host_bodies, int n);
+
+/* Replace the motion of existing bodies between steps (free-body coupling):
+ * new X0, U, W, t0 for each body; shape and R must stay the same.  The pose
+ * at the current step must equal the pose the domain already holds within
+ * 1e-9 cells (the solid set at t does not jump); LBM_ERR_ARG otherwise. */
+int lbm_update_bodies(lbm_domain *dom, const lbm_body *host_bodies, int n);
+
+/* Advance n steps, asynchronously on the domain's stream.  Step t -> t+1
+ * appends one row per body to the force/torque series (the force at time t
+ * of Sec. 3). */
+int lbm_step(lbm_domain *dom, int n);
+
+/* Copy series rows [first, first+count) of every body into host memory:
+ * out[count][n_bodies][6] = (Fx, Fy, Fz, Tx, Ty, Tz) in form `kind`
+ * (LBM_FT_*).  Synchronises.  Rows older than the ring capacity are gone
+ * (LBM_ERR_ARG). */
+int lbm_get_force_torque(lbm_domain *dom, int64_t first, int64_t count, int kind, double *out);
+
+/* Raw series rows: out[count][n_bodies][LBM_SERIES_ROW]. */
+int lbm_get_series(lbm_domain *dom, int64_t first, int64_t count, double *out);
+
+/* Post-collision populations fhat(x, t) of the current step as FP64 f (not
+ * f - w), out[Q][nz][ny][nx]; values at solid nodes are unspecified.
+ * Synchronises. */
+int lbm_get_populations(lbm_domain *dom, double *out);
+
+/* Owning body index of every node at the current step (-1: fluid),
+ * out[nz][ny][nx].  Synchronises. */
+int lbm_get_solid(lbm_domain *dom, int32_t *out);
+
+/* Counters of the domain (synchronises). */
+int lbm_get_stats(lbm_domain *dom, lbm_stats *out);
+
+/* Current step t. */
+int64_t lbm_time(const lbm_domain *dom);
+
+/* Change the stream work is enqueued on (the old stream is synchronised). */
+int lbm_set_stream(lbm_domain *dom, void *stream);
+
+/* Kernel timing for roofline reports: while enabled, lbm_step records CUDA
+ * events around every launch of the bulk stream-collide kernel on the
+ * domain's stream.  lbm_kernel_time returns (and clears) the number of timed
+ * launches and their total device time in milliseconds.  Synchronises. */
+int lbm_set_kernel_timing(lbm_domain *dom, int enable);
+int lbm_kernel_time(lbm_domain *dom, int64_t *launches, double *total_ms);
+
+/* Number of kernel launches lbm_step(dom, 1) issues at the current state. */
+int lbm_launches_per_step(const lbm_domain *dom, int *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,759 @@
+// lbm_api.cu -- host implementation of the C ABI declared in include/lbm.h.
+//
+// A domain owns: two population buffers (fhat at t and t+1), two moment
+// buffers (rho,u at the nodes flagged FL_MAC), the node flags, two owner
+// arrays (solid owner at t and t+1), two cut-link buffers (t and t+1), the
+// per-link momentum-exchange contributions, the covered/uncovered lists and
+// the force/torque ring.  lbm_step enqueues, per step:
+//   moving bodies only: k_geom_a, k_geom_b, k_geom_c  (geometry of t+1)
+//   k_links (wall values + ME per link), k_bulk (stream-collide),
+//   moving bodies only: k_imp (A+/A- impulsive terms, refill),
+//   k_reduce (per-body series row).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+cudaError_t launch_init_p0(int Q, const Params &p, void *dst, void *mac, const uint8_t *flags, const double u0[3],
+                           cudaStream_t s);
+cudaError_t launch_links_p0(int Q, const Params &p, const StepBufs &sb, int grid, cudaStream_t s);
+cudaError_t launch_bulk_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_imp_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_init_p12(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
+                            const double u0[3], cudaStream_t s);
+cudaError_t launch_links_p12(int Q, int prec, const Params &p, const StepBufs &sb, int grid, cudaStream_t s);
+cudaError_t launch_bulk_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_imp_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+
+cudaError_t launch_init(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
+                        const double u0[3], cudaStream_t s) {
+    return prec == 0 ? launch_init_p0(Q, p, dst, mac, flags, u0, s) : launch_init_p12(Q, prec, p, dst, mac, flags, u0, s);
+}
+cudaError_t launch_links(int Q, int prec, const Params &p, const StepBufs &sb, int grid, cudaStream_t s) {
+    return prec == 0 ? launch_links_p0(Q, p, sb, grid, s) : launch_links_p12(Q, prec, p, sb, grid, s);
+}
+cudaError_t launch_bulk(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    return prec == 0 ? launch_bulk_p0(Q, p, sb, s) : launch_bulk_p12(Q, prec, p, sb, s);
+}
+cudaError_t launch_imp(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    return prec == 0 ? launch_imp_p0(Q, p, sb, s) : launch_imp_p12(Q, prec, p, sb, s);
+}
+} // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(x)                                                                                                   \
+    do {                                                                                                        \
+        cudaError_t e_ = (x);                                                                                   \
+        if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr double PI = 3.14159265358979323846;
+
+} // namespace
+
+struct lbm_domain {
+    lbm_domain_desc d{};
+    Params p{};
+    int Q = 0, prec = 0;
+    size_t Ssize = 0, Csize = 0;
+    cudaStream_t s = nullptr;
+    size_t bytes = 0;
+    long long h2d = 0, d2h = 0;
+    // lattice state
+    void *pop[2] = {nullptr, nullptr};
+    void *mac[2] = {nullptr, nullptr};
+    uint8_t *flags = nullptr;
+    uint16_t *owner[2] = {nullptr, nullptr};
+    unsigned long long *counters = nullptr;
+    // bodies
+    int nb = 0, n_moving = 0;
+    std::vector<lbm_body> hb;
+    std::vector<BodyDev> hbd;
+    std::vector<void *> body_allocs;
+    BodyDev *dbodies = nullptr;
+    int *dmoving = nullptr;
+    int2 *chunk_all = nullptr, *chunk_mov = nullptr;
+    int nchunk_all = 0, nchunk_mov = 0;
+    int *chunk_cnt_apm = nullptr, *chunk_cnt_link = nullptr;
+    uint32_t *Lcell[2] = {nullptr, nullptr};
+    uint8_t *Ldir[2] = {nullptr, nullptr};
+    double *Ldelta[2] = {nullptr, nullptr};
+    long long *link_cnt[2] = {nullptr, nullptr};
+    long long link_cap_total = 0;
+    double *me = nullptr;
+    uint32_t *apm_cell = nullptr;
+    int8_t *apm_sign = nullptr;
+    long long *apm_cnt = nullptr;
+    long long apm_cap_total = 0;
+    double *imp = nullptr;
+    double *series = nullptr;
+    long long series_cap = 0;
+    int links_grid = 0;
+    int64_t t = 0;
+    // timing of the bulk kernel
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+
+    void *alloc(size_t n) {
+        if (n == 0) n = 256;
+        void *ptr = nullptr;
+        if (d.alloc) ptr = d.alloc(n, d.alloc_ctx);
+        else if (cudaMalloc(&ptr, n) != cudaSuccess) ptr = nullptr;
+        return ptr;
+    }
+    void release(void *ptr) {
+        if (!ptr) return;
+        if (d.free) d.free(ptr, d.alloc_ctx);
+        else cudaFree(ptr);
+    }
+};
+
+namespace {
+
+int alloc_into(lbm_domain *D, void **slot, size_t n, std::vector<void *> *track) {
+    void *ptr = D->alloc(n);
+    if (!ptr) return fail(LBM_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed");
+    D->bytes += n;
+    if (cudaMemsetAsync(ptr, 0, n, D->s) != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaMemsetAsync failed");
+    *slot = ptr;
+    if (track) track->push_back(ptr);
+    return LBM_OK;
+}
+
+template <class T> int alloc_t(lbm_domain *D, T **slot, size_t count, std::vector<void *> *track) {
+    void *v = nullptr;
+    int rc = alloc_into(D, &v, count * sizeof(T), track);
+    *slot = (T *)v;
+    return rc;
+}
+
+void free_body_buffers(lbm_domain *D) {
+    for (void *ptr : D->body_allocs) D->release(ptr);
+    D->body_allocs.clear();
+    D->dbodies = nullptr;
+    D->dmoving = nullptr;
+    D->chunk_all = D->chunk_mov = nullptr;
+    D->chunk_cnt_apm = D->chunk_cnt_link = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        D->Lcell[k] = nullptr;
+        D->Ldir[k] = nullptr;
+        D->Ldelta[k] = nullptr;
+        D->link_cnt[k] = nullptr;
+    }
+    D->me = nullptr;
+    D->apm_cell = nullptr;
+    D->apm_sign = nullptr;
+    D->apm_cnt = nullptr;
+    D->imp = nullptr;
+    D->series = nullptr;
+    D->nb = D->n_moving = 0;
+    D->nchunk_all = D->nchunk_mov = 0;
+    D->link_cap_total = D->apm_cap_total = 0;
+}
+
+bool is_moving(const lbm_body &b) {
+    for (int k = 0; k < 3; ++k)
+        if (b.U[k] != 0.0 || b.W[k] != 0.0) return true;
+    return false;
+}
+
+// upper bound of the cut links of a body: boundary nodes lie in the shell
+// R < |x - X| <= R + sqrt(2); their unit cells fit in the shell widened by
+// half a cell diagonal, so the shell volume bounds their number.
+long long link_capacity(const lbm_domain *D, const lbm_body &b) {
+    const double cmax = std::sqrt(2.0);
+    double nodes;
+    if (b.shape == LBM_SHAPE_SPHERE) {
+        const double h = std::sqrt(3.0) / 2.0;
+        double ro = b.R + cmax + h, ri = std::max(0.0, b.R - h);
+        nodes = 4.0 / 3.0 * PI * (ro * ro * ro - ri * ri * ri);
+    } else {
+        const double h = std::sqrt(2.0) / 2.0;
+        double ro = b.R + cmax + h, ri = std::max(0.0, b.R - h);
+        nodes = PI * (ro * ro - ri * ri) * D->p.nz;
+    }
+    return (long long)std::ceil(nodes) * (D->Q - 1) + 256;
+}
+
+void body_params(const lbm_domain *D, const lbm_body &b, BodyDev &o) {
+    std::memset(&o, 0, sizeof(o));
+    o.shape = b.shape;
+    o.halfway = b.halfway;
+    o.moving = is_moving(b) ? 1 : 0;
+    o.R = b.R;
+    for (int k = 0; k < 3; ++k) {
+        o.X0[k] = b.X0[k];
+        o.U[k] = b.U[k];
+        o.W[k] = b.W[k];
+    }
+    o.t0 = b.t0;
+    const int n[3] = {D->p.nx, D->p.ny, D->p.nz};
+    for (int a = 0; a < 3; ++a) {
+        int e = 2 * (int)std::ceil(b.R) + 2 * REGION_MARGIN + 5;
+        if ((a == 2 && b.shape == LBM_SHAPE_CYLINDER) || e >= n[a]) e = n[a];
+        o.ext[a] = e;
+    }
+    long long vol = (long long)o.ext[0] * o.ext[1] * o.ext[2];
+    o.nchunks = (int)((vol + GEOM_THREADS - 1) / GEOM_THREADS);
+    o.link_cap = link_capacity(D, b);
+    o.apm_cap = vol;
+}
+
+double min_image(double v, int n, bool per) {
+    if (!per) return v;
+    return v - n * std::floor(v / n + 0.5);
+}
+
+int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
+    const int nn[3] = {D->p.nx, D->p.ny, D->p.nz};
+    for (int k = 0; k < n; ++k) {
+        const lbm_body &B = b[k];
+        if (B.shape != LBM_SHAPE_CYLINDER && B.shape != LBM_SHAPE_SPHERE)
+            return fail(LBM_ERR_ARG, "body " + std::to_string(k) + ": unknown shape");
+        if (B.shape == LBM_SHAPE_SPHERE && D->Q == 9)
+            return fail(LBM_ERR_ARG, "body " + std::to_string(k) + ": spheres need D3Q19 (use a cylinder in 2-D)");
+        if (!(B.R > 0.0) || !std::isfinite(B.R)) return fail(LBM_ERR_ARG, "body radius must be positive");
+        if (B.reserved[0] || B.reserved[1]) return fail(LBM_ERR_ARG, "reserved body fields must be 0");
+        if (B.halfway != 0 && B.halfway != 1) return fail(LBM_ERR_ARG, "halfway must be 0 or 1");
+        for (int a = 0; a < 3; ++a) {
+            if (a == 2 && (B.shape == LBM_SHAPE_CYLINDER)) continue;
+            if (!std::isfinite(B.X0[a]) || !std::isfinite(B.U[a]) || !std::isfinite(B.W[a]))
+                return fail(LBM_ERR_ARG, "body state must be finite");
+            if (D->p.per[a]) {
+                if (2.0 * B.R + 4.0 >= nn[a])
+                    return fail(LBM_ERR_ARG, "body " + std::to_string(k) + " is too large for the periodic axis");
+            } else {
+                if (B.X0[a] - B.R < 3.0 || B.X0[a] + B.R > nn[a] - 4.0)
+                    return fail(LBM_ERR_ARG, "body " + std::to_string(k) +
+                                                 " must keep 3 cells from non-periodic faces");
+                if (B.U[a] != 0.0)
+                    return fail(LBM_ERR_ARG, "bodies may not translate along a non-periodic axis");
+            }
+        }
+        double umax = std::sqrt(B.U[0] * B.U[0] + B.U[1] * B.U[1] + B.U[2] * B.U[2]) +
+                      B.R * std::sqrt(B.W[0] * B.W[0] + B.W[1] * B.W[1] + B.W[2] * B.W[2]);
+        if (umax > 0.5) return fail(LBM_ERR_ARG, "body surface may move at most 0.5 cells per step");
+        for (int m = 0; m < k; ++m) {
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                if (a == 2 && (B.shape == LBM_SHAPE_CYLINDER || b[m].shape == LBM_SHAPE_CYLINDER)) continue;
+                double v = min_image(B.X0[a] + (0 - B.t0) * B.U[a] - (b[m].X0[a] + (0 - b[m].t0) * b[m].U[a]),
+                                     nn[a], D->p.per[a] != 0);
+                d2 += v * v;
+            }
+            if (std::sqrt(d2) - B.R - b[m].R < 2.0)
+                return fail(LBM_ERR_ARG, "bodies " + std::to_string(m) + " and " + std::to_string(k) +
+                                             " are closer than a 2-cell gap");
+        }
+    }
+    return LBM_OK;
+}
+
+StepBufs step_bufs(lbm_domain *D) {
+    const int cur = (int)(D->t & 1), nxt = cur ^ 1;
+    StepBufs sb{};
+    sb.src = D->pop[cur];
+    sb.dst = D->pop[nxt];
+    sb.mac_t = D->mac[cur];
+    sb.mac_t1 = D->mac[nxt];
+    sb.flags = D->flags;
+    sb.owner_t = D->owner[cur];
+    sb.bodies = D->dbodies;
+    sb.moving_ids = D->dmoving;
+    sb.n_moving = D->n_moving;
+    sb.link_cnt = D->link_cnt[cur];
+    sb.Lcell = D->Lcell[cur];
+    sb.Ldir = D->Ldir[cur];
+    sb.Ldelta = D->Ldelta[cur];
+    sb.me = D->me;
+    sb.apm_cnt = D->apm_cnt;
+    sb.apm_cell = D->apm_cell;
+    sb.apm_sign = D->apm_sign;
+    sb.imp = D->imp;
+    sb.series = D->series;
+    sb.counters = D->counters;
+    sb.t = D->t;
+    return sb;
+}
+
+GeomArgs geom_args(lbm_domain *D, bool moving_step) {
+    const int cur = (int)(D->t & 1), nxt = cur ^ 1;
+    GeomArgs g{};
+    g.bodies = D->dbodies;
+    g.chunk_map = moving_step ? D->chunk_mov : D->chunk_all;
+    g.nchunks = moving_step ? D->nchunk_mov : D->nchunk_all;
+    g.owner_t = D->owner[cur];
+    g.owner_t1 = moving_step ? D->owner[nxt] : D->owner[cur];
+    g.flags = D->flags;
+    g.chunk_cnt_apm = D->chunk_cnt_apm;
+    g.chunk_cnt_link = D->chunk_cnt_link;
+    g.apm_cell = D->apm_cell;
+    g.apm_sign = D->apm_sign;
+    g.apm_cnt = D->apm_cnt;
+    const int lb = moving_step ? nxt : cur;
+    g.Lcell = D->Lcell[lb];
+    g.Ldir = D->Ldir[lb];
+    g.Ldelta = D->Ldelta[lb];
+    g.link_cnt = D->link_cnt[lb];
+    g.t = D->t;
+    g.t_link = moving_step ? D->t + 1 : D->t;
+    g.do_apm = moving_step ? 1 : 0;
+    g.do_flags = moving_step ? 1 : 0;
+    return g;
+}
+
+int init_populations(lbm_domain *D) {
+    CK(launch_init(D->Q, D->prec, D->p, D->pop[D->t & 1], D->mac[D->t & 1], D->flags, D->d.u0, D->s));
+    return LBM_OK;
+}
+
+int upload_body_array(lbm_domain *D) {
+    CK(cudaMemcpyAsync(D->dbodies, D->hbd.data(), sizeof(BodyDev) * D->nb, cudaMemcpyHostToDevice, D->s));
+    D->h2d += (long long)(sizeof(BodyDev) * D->nb);
+    return LBM_OK;
+}
+
+int upload_bodies(lbm_domain *D) {
+    // moving list and chunk maps
+    std::vector<int> mov;
+    std::vector<int2> all, mv;
+    for (int b = 0; b < D->nb; ++b) {
+        BodyDev &B = D->hbd[b];
+        B.chunk_base = (int)all.size();
+        for (int c = 0; c < B.nchunks; ++c) all.push_back(make_int2(b, c));
+        if (B.moving) {
+            mov.push_back(b);
+            for (int c = 0; c < B.nchunks; ++c) mv.push_back(make_int2(b, c));
+        }
+    }
+    D->n_moving = (int)mov.size();
+    D->nchunk_all = (int)all.size();
+    D->nchunk_mov = (int)mv.size();
+    CK(cudaMemcpyAsync(D->dbodies, D->hbd.data(), sizeof(BodyDev) * D->nb, cudaMemcpyHostToDevice, D->s));
+    D->h2d += (long long)(sizeof(BodyDev) * D->nb);
+    if (!mov.empty()) CK(cudaMemcpyAsync(D->dmoving, mov.data(), sizeof(int) * mov.size(), cudaMemcpyHostToDevice, D->s));
+    CK(cudaMemcpyAsync(D->chunk_all, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice, D->s));
+    if (!mv.empty()) CK(cudaMemcpyAsync(D->chunk_mov, mv.data(), sizeof(int2) * mv.size(), cudaMemcpyHostToDevice, D->s));
+    CK(cudaStreamSynchronize(D->s)); // host vectors go out of scope
+    return LBM_OK;
+}
+
+int do_step(lbm_domain *D) {
+    const int Q = D->Q, prec = D->prec;
+    if (D->n_moving) {
+        GeomArgs g = geom_args(D, true);
+        CK(launch_geom_a(Q, D->p, g, D->s));
+        CK(launch_geom_b(Q, D->p, g, D->s));
+        CK(launch_geom_c(Q, D->p, g, D->s));
+    }
+    StepBufs sb = step_bufs(D);
+    if (D->nb) CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
+    if (D->timing) {
+        if (D->ev_used + 2 > D->ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                D->ev.push_back(e);
+            }
+        }
+        CK(cudaEventRecord(D->ev[D->ev_used], D->s));
+    }
+    CK(launch_bulk(Q, prec, D->p, sb, D->s));
+    if (D->timing) {
+        CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
+        D->ev_used += 2;
+    }
+    if (D->n_moving) CK(launch_imp(Q, prec, D->p, sb, D->s));
+    if (D->nb) CK(launch_reduce(prec, D->p, sb, D->s));
+    D->t += 1;
+    return LBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+const char *lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
+
+int lbm_lattice_table(int lattice, int *c, double *w, int *opp) {
+    if (!c || !w || !opp) return fail(LBM_ERR_ARG, "null output");
+    LatTab t;
+    if (lattice == LBM_D2Q9) t = make_tab<Lat<9>>();
+    else if (lattice == LBM_D3Q19) t = make_tab<Lat<19>>();
+    else return fail(LBM_ERR_ARG, "lattice must be 9 or 19");
+    for (int i = 0; i < lattice; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = t.c[i][a];
+        w[i] = t.w[i];
+        opp[i] = t.opp[i];
+    }
+    return LBM_OK;
+}
+
+int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
+    if (!desc || !out) return fail(LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    const lbm_domain_desc &d = *desc;
+    if (d.lattice != LBM_D2Q9 && d.lattice != LBM_D3Q19) return fail(LBM_ERR_ARG, "lattice must be LBM_D2Q9 or LBM_D3Q19");
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return fail(LBM_ERR_ARG, "grid sizes must be >= 1");
+    if (d.lattice == LBM_D2Q9 && d.nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz = 1");
+    if ((long long)d.nx * d.ny * d.nz >= (1ll << 32)) return fail(LBM_ERR_ARG, "more than 2^32 cells");
+    if (d.ny > 65535 || d.nz > 65535) return fail(LBM_ERR_ARG, "ny and nz must be <= 65535");
+    if (d.precision < LBM_FP64 || d.precision > LBM_FP16) return fail(LBM_ERR_ARG, "unknown precision");
+    if (d.equilibrium != LBM_EQ_INCOMP && d.equilibrium != LBM_EQ_STANDARD) return fail(LBM_ERR_ARG, "unknown equilibrium");
+    if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return fail(LBM_ERR_ARG, "tau must be > 1/2");
+    if (!(d.rho0 > 0.0)) return fail(LBM_ERR_ARG, "rho0 must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if ((d.edge[2 * a] == LBM_EDGE_PERIODIC) != (d.edge[2 * a + 1] == LBM_EDGE_PERIODIC))
+            return fail(LBM_ERR_ARG, "an axis is periodic on both faces or on neither");
+    for (int e = 0; e < 6; ++e) {
+        if (d.edge[e] < 0 || d.edge[e] > 3) return fail(LBM_ERR_ARG, "unknown edge kind");
+        if (d.edge[e] == LBM_EDGE_INLET && e != 0) return fail(LBM_ERR_ARG, "the inlet must be the x-low face");
+        if (d.edge[e] == LBM_EDGE_OUTLET && e != 1) return fail(LBM_ERR_ARG, "the outlet must be the x-high face");
+    }
+    if (d.lattice == LBM_D2Q9 && d.edge[4] != LBM_EDGE_PERIODIC) return fail(LBM_ERR_ARG, "D2Q9: z must be periodic");
+    if (d.refill != LBM_REFILL_RHOBAR_UB && d.refill != LBM_REFILL_RHOBAR_UBAR) return fail(LBM_ERR_ARG, "unknown refill rule");
+    if (d.inlet_profile != LBM_INLET_UNIFORM && d.inlet_profile != LBM_INLET_PARABOLIC)
+        return fail(LBM_ERR_ARG, "unknown inlet profile");
+    if ((d.alloc == nullptr) != (d.free == nullptr)) return fail(LBM_ERR_ARG, "alloc and free go together");
+
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+
+    lbm_domain *D = new lbm_domain();
+    D->d = d;
+    D->Q = d.lattice;
+    D->prec = d.precision;
+    D->s = (cudaStream_t)d.stream;
+    D->Ssize = d.precision == LBM_FP64 ? 8 : (d.precision == LBM_FP32 ? 4 : 2);
+    D->Csize = d.precision == LBM_FP64 ? 8 : 4;
+    Params &p = D->p;
+    p.nx = d.nx;
+    p.ny = d.ny;
+    p.nz = d.nz;
+    p.N = (long long)d.nx * d.ny * d.nz;
+    for (int a = 0; a < 3; ++a) p.per[a] = d.edge[2 * a] == LBM_EDGE_PERIODIC;
+    for (int k = 0; k < 6; ++k) p.edge[k] = d.edge[k];
+    p.nonper = !(p.per[0] && p.per[1] && p.per[2]);
+    p.eq = d.equilibrium;
+    p.inlet_parabolic = d.inlet_profile == LBM_INLET_PARABOLIC;
+    p.has_force = d.has_force ? 1 : 0;
+    p.refill = d.refill;
+    p.tau = d.tau;
+    p.omega = 1.0 / d.tau;
+    p.rho0 = d.rho0;
+    p.u_in = d.u_in;
+    for (int k = 0; k < 3; ++k) {
+        p.g[k] = d.has_force ? d.force[k] : 0.0;
+        p.gf[k] = (float)p.g[k];
+    }
+    p.omegaf = (float)p.omega;
+    p.rho0f = (float)d.rho0;
+    p.u_inf = (float)d.u_in;
+    p.nb = 0;
+    D->series_cap = d.series_capacity > 0 ? d.series_capacity : 8192;
+    p.series_cap = D->series_cap;
+
+    auto bail = [&](int rc) {
+        lbm_destroy_domain(D);
+        return rc;
+    };
+    const size_t N = (size_t)p.N;
+    int rc;
+    for (int k = 0; k < 2; ++k) {
+        if ((rc = alloc_into(D, &D->pop[k], N * D->Q * D->Ssize, nullptr))) return bail(rc);
+        if ((rc = alloc_into(D, &D->mac[k], N * 4 * D->Csize, nullptr))) return bail(rc);
+        if ((rc = alloc_t(D, &D->owner[k], N, nullptr))) return bail(rc);
+    }
+    if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
+    if ((rc = alloc_t(D, &D->counters, 4, nullptr))) return bail(rc);
+    if ((e = launch_flags_full(D->Q, p, D->owner[0], D->flags, D->s)) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, std::string("flags: ") + cudaGetErrorString(e)));
+    if ((rc = init_populations(D))) return bail(rc);
+    if ((e = cudaStreamSynchronize(D->s)) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+    *out = D;
+    return LBM_OK;
+}
+
+int lbm_destroy_domain(lbm_domain *D) {
+    if (!D) return LBM_OK;
+    cudaStreamSynchronize(D->s);
+    free_body_buffers(D);
+    for (int k = 0; k < 2; ++k) {
+        D->release(D->pop[k]);
+        D->release(D->mac[k]);
+        D->release(D->owner[k]);
+    }
+    D->release(D->flags);
+    D->release(D->counters);
+    for (cudaEvent_t e : D->ev) cudaEventDestroy(e);
+    delete D;
+    return LBM_OK;
+}
+
+int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
+    if (!D || n < 0 || (n > 0 && !hb)) return fail(LBM_ERR_ARG, "invalid arguments");
+    if (D->t != 0) return fail(LBM_ERR_STATE, "bodies can only be placed at t = 0");
+    if (n > 65534) return fail(LBM_ERR_ARG, "at most 65534 bodies");
+    int rc = validate_bodies(D, hb, n);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(D->s));
+    free_body_buffers(D);
+    D->nb = n;
+    D->p.nb = n;
+    D->hb.assign(hb, hb + n);
+    D->hbd.resize(n);
+    long long loff = 0, aoff = 0, chunks = 0;
+    for (int b = 0; b < n; ++b) {
+        body_params(D, hb[b], D->hbd[b]);
+        D->hbd[b].link_off = loff;
+        D->hbd[b].apm_off = aoff;
+        loff += D->hbd[b].link_cap;
+        aoff += D->hbd[b].apm_cap;
+        chunks += D->hbd[b].nchunks;
+    }
+    D->link_cap_total = loff;
+    D->apm_cap_total = aoff;
+    auto &T = D->body_allocs;
+    const size_t nbx = (size_t)std::max(n, 1);
+    if ((rc = alloc_t(D, &D->dbodies, nbx, &T))) return rc;
+    if ((rc = alloc_t(D, &D->dmoving, nbx, &T))) return rc;
+    if ((rc = alloc_t(D, &D->chunk_all, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
+    if ((rc = alloc_t(D, &D->chunk_mov, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
+    if ((rc = alloc_t(D, &D->chunk_cnt_apm, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
+    if ((rc = alloc_t(D, &D->chunk_cnt_link, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
+    for (int k = 0; k < 2; ++k) {
+        if ((rc = alloc_t(D, &D->Lcell[k], (size_t)std::max<long long>(loff, 1), &T))) return rc;
+        if ((rc = alloc_t(D, &D->Ldir[k], (size_t)std::max<long long>(loff, 1), &T))) return rc;
+        if ((rc = alloc_t(D, &D->Ldelta[k], (size_t)std::max<long long>(loff, 1), &T))) return rc;
+        if ((rc = alloc_t(D, &D->link_cnt[k], nbx, &T))) return rc;
+    }
+    if ((rc = alloc_t(D, &D->me, (size_t)std::max<long long>(loff, 1) * ME_PER_LINK, &T))) return rc;
+    if ((rc = alloc_t(D, &D->apm_cell, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
+    if ((rc = alloc_t(D, &D->apm_sign, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
+    if ((rc = alloc_t(D, &D->apm_cnt, nbx, &T))) return rc;
+    if ((rc = alloc_t(D, &D->imp, nbx * 6, &T))) return rc;
+    if ((rc = alloc_t(D, &D->series, (size_t)D->series_cap * nbx * SERIES_ROW, &T))) return rc;
+    long long maxcnt = 0;
+    for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
+    D->links_grid = (int)std::min<long long>(4 * 152, (maxcnt + LINK_THREADS - 1) / LINK_THREADS);
+    if ((rc = upload_bodies(D))) return rc;
+
+    // solid owners at t = 0, flags, links (both buffers), initial state
+    const size_t N = (size_t)D->p.N;
+    CK(cudaMemsetAsync(D->owner[0], 0, N * sizeof(uint16_t), D->s));
+    GeomArgs g = geom_args(D, false);
+    CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
+    CK(cudaMemcpyAsync(D->owner[1], D->owner[0], N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
+    CK(launch_flags_full(D->Q, D->p, D->owner[0], D->flags, D->s));
+    CK(launch_geom_b(D->Q, D->p, g, D->s));
+    CK(launch_geom_c(D->Q, D->p, g, D->s));
+    const size_t L = (size_t)std::max<long long>(loff, 1);
+    CK(cudaMemcpyAsync(D->Lcell[1], D->Lcell[0], L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, D->s));
+    CK(cudaMemcpyAsync(D->Ldir[1], D->Ldir[0], L, cudaMemcpyDeviceToDevice, D->s));
+    CK(cudaMemcpyAsync(D->Ldelta[1], D->Ldelta[0], L * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
+    CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice, D->s));
+    if ((rc = init_populations(D))) return rc;
+    CK(cudaStreamSynchronize(D->s));
+    return LBM_OK;
+}
+
+int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
+    if (!D || !hb || n != D->nb) return fail(LBM_ERR_ARG, "update needs the same number of bodies");
+    for (int b = 0; b < n; ++b) {
+        const lbm_body &o = D->hb[b], &v = hb[b];
+        if (o.shape != v.shape || o.R != v.R || o.halfway != v.halfway)
+            return fail(LBM_ERR_ARG, "shape, radius and halfway cannot change");
+        for (int a = 0; a < 3; ++a) {
+            double xo = o.X0[a] + (double)(D->t - o.t0) * o.U[a];
+            double xv = v.X0[a] + (double)(D->t - v.t0) * v.U[a];
+            if (std::fabs(xo - xv) > 1e-9) return fail(LBM_ERR_ARG, "the pose at the current step may not jump");
+            if (!D->p.per[a] && v.U[a] != 0.0 && !(a == 2 && v.shape == LBM_SHAPE_CYLINDER))
+                return fail(LBM_ERR_ARG, "bodies may not translate along a non-periodic axis");
+        }
+    }
+    CK(cudaStreamSynchronize(D->s));
+    const int cur = (int)(D->t & 1), nxt = cur ^ 1;
+    bool maps_changed = false;
+    for (int b = 0; b < n; ++b) {
+        bool was = D->hbd[b].moving != 0;
+        BodyDev nb = D->hbd[b];
+        BodyDev tmp;
+        body_params(D, hb[b], tmp);
+        nb.moving = tmp.moving;
+        for (int a = 0; a < 3; ++a) {
+            nb.X0[a] = hb[b].X0[a];
+            nb.U[a] = hb[b].U[a];
+            nb.W[a] = hb[b].W[a];
+        }
+        nb.t0 = hb[b].t0;
+        D->hbd[b] = nb;
+        D->hb[b] = hb[b];
+        if (was != (nb.moving != 0)) maps_changed = true;
+        if (was && !nb.moving) { // static from now on: both link buffers must hold the links of t
+            const size_t off = (size_t)nb.link_off, cap = (size_t)nb.link_cap;
+            CK(cudaMemcpyAsync(D->Lcell[nxt] + off, D->Lcell[cur] + off, cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, D->s));
+            CK(cudaMemcpyAsync(D->Ldir[nxt] + off, D->Ldir[cur] + off, cap, cudaMemcpyDeviceToDevice, D->s));
+            CK(cudaMemcpyAsync(D->Ldelta[nxt] + off, D->Ldelta[cur] + off, cap * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
+            CK(cudaMemcpyAsync(D->link_cnt[nxt] + b, D->link_cnt[cur] + b, sizeof(long long), cudaMemcpyDeviceToDevice, D->s));
+            CK(cudaMemcpyAsync(D->owner[nxt], D->owner[cur], (size_t)D->p.N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
+        }
+    }
+    if (maps_changed) return upload_bodies(D);
+    return upload_body_array(D);
+}
+
+int lbm_step(lbm_domain *D, int n) {
+    if (!D || n < 0) return fail(LBM_ERR_ARG, "invalid arguments");
+    CK(cudaSetDevice(D->d.device));
+    for (int k = 0; k < n; ++k) {
+        int rc = do_step(D);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
+    if (!D || !out || first < 0 || count < 0) return fail(LBM_ERR_ARG, "invalid arguments");
+    if (first + count > D->t) return fail(LBM_ERR_ARG, "rows beyond the current step");
+    if (first < D->t - D->series_cap) return fail(LBM_ERR_ARG, "rows older than the series ring");
+    if (D->nb == 0 || count == 0) return LBM_OK;
+    CK(cudaStreamSynchronize(D->s));
+    const size_t row = (size_t)D->nb * SERIES_ROW;
+    int64_t done = 0;
+    while (done < count) {
+        int64_t r = (first + done) % D->series_cap;
+        int64_t m = std::min<int64_t>(count - done, D->series_cap - r);
+        CK(cudaMemcpy(out + done * row, D->series + r * row, m * row * sizeof(double), cudaMemcpyDeviceToHost));
+        D->d2h += (long long)(m * row * sizeof(double));
+        done += m;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_force_torque(lbm_domain *D, int64_t first, int64_t count, int kind, double *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    if (kind < LBM_FT_STATIC || kind > LBM_FT_IMPULSIVE) return fail(LBM_ERR_ARG, "unknown force kind");
+    std::vector<double> raw((size_t)std::max<int64_t>(count, 0) * D->nb * SERIES_ROW);
+    int rc = lbm_get_series(D, first, count, raw.data());
+    if (rc) return rc;
+    for (int64_t r = 0; r < count * D->nb; ++r) {
+        const double *s = raw.data() + r * SERIES_ROW;
+        double *o = out + r * 6;
+        for (int k = 0; k < 6; ++k) {
+            if (kind == LBM_FT_STATIC) o[k] = s[k];
+            else if (kind == LBM_FT_LATTICE) o[k] = s[k] + s[6 + k];
+            else if (kind == LBM_FT_MOVING) o[k] = s[12 + k];
+            else o[k] = s[6 + k];
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_domain *D, double *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    const size_t n = (size_t)D->p.N * D->Q;
+    void *tmp = D->alloc(n * sizeof(double));
+    if (!tmp) return fail(LBM_ERR_OOM, "temporary export buffer");
+    cudaError_t e = launch_export(D->Q, D->prec, D->p, D->pop[D->t & 1], (double *)tmp, D->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(D->s);
+    if (e == cudaSuccess) e = cudaMemcpy(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost);
+    D->release(tmp);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("populations: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_get_solid(lbm_domain *D, int32_t *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    const size_t N = (size_t)D->p.N;
+    std::vector<uint16_t> o(N);
+    CK(cudaStreamSynchronize(D->s));
+    CK(cudaMemcpy(o.data(), D->owner[D->t & 1], N * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < N; ++k) out[k] = (int32_t)o[k] - 1;
+    return LBM_OK;
+}
+
+int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    std::memset(out, 0, sizeof(*out));
+    CK(cudaStreamSynchronize(D->s));
+    unsigned long long c[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(c, D->counters, sizeof(c), cudaMemcpyDeviceToHost));
+    out->step = D->t;
+    out->cells = D->p.N;
+    out->fallback_links = (int64_t)c[0];
+    out->covered = (int64_t)c[1];
+    out->uncovered = (int64_t)c[2];
+    out->device_bytes = (int64_t)D->bytes;
+    out->h2d_bytes = D->h2d;
+    out->d2h_bytes = D->d2h;
+    if (D->nb) {
+        std::vector<long long> lc(D->nb);
+        CK(cudaMemcpy(lc.data(), D->link_cnt[D->t & 1], sizeof(long long) * D->nb, cudaMemcpyDeviceToHost));
+        for (long long v : lc) out->links += v;
+    }
+    std::vector<int32_t> s((size_t)D->p.N);
+    int rc = lbm_get_solid(D, s.data());
+    if (rc) return rc;
+    for (int32_t v : s) out->fluid_cells += v < 0;
+    return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_domain *D) { return D ? D->t : -1; }
+
+int lbm_set_stream(lbm_domain *D, void *stream) {
+    if (!D) return fail(LBM_ERR_ARG, "null domain");
+    CK(cudaStreamSynchronize(D->s));
+    D->s = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_set_kernel_timing(lbm_domain *D, int enable) {
+    if (!D) return fail(LBM_ERR_ARG, "null domain");
+    CK(cudaStreamSynchronize(D->s));
+    D->timing = enable != 0;
+    D->ev_used = 0;
+    return LBM_OK;
+}
+
+int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
+    if (!D || !launches || !total_ms) return fail(LBM_ERR_ARG, "invalid arguments");
+    CK(cudaStreamSynchronize(D->s));
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < D->ev_used; k += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, D->ev[k], D->ev[k + 1]));
+        tot += ms;
+    }
+    *launches = (int64_t)(D->ev_used / 2);
+    *total_ms = tot;
+    D->ev_used = 0;
+    return LBM_OK;
+}
+
+int lbm_launches_per_step(const lbm_domain *D, int *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0);
+    return LBM_OK;
+}
+
+} // extern "C"

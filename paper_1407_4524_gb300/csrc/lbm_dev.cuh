@@ -1,0 +1,261 @@
+// lbm_dev.cuh -- device-side definitions shared by the kernels of liblbm.
+//
+// Lattice traits (D2Q9 / D3Q19 in the library's direction order), precision
+// policies, the POD parameter blocks passed to every kernel, and the FP64
+// geometry helpers (pose, minimum image, rigid-body velocity, fractional link
+// distance Delta of Sec. 2.1).
+//
+// Every translation unit of the library is compiled with --fmad=false: the
+// FP64 mode must reproduce the fixed operation order of each formula exactly,
+// so no multiply-add may be contracted behind our back.  The FP32 path asks
+// for fused multiply-adds explicitly with fmaf().
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace lbm {
+
+constexpr uint8_t FL_SOLID = 1; // node inside a body at time t
+constexpr uint8_t FL_MAC = 2;   // store rho,u of f(t+1) at this node
+
+constexpr int SERIES_ROW = 18;  // Fs Ts Fi Ti Fm Tm
+constexpr int ME_PER_LINK = 12; // Fs Ts Fm Tm contributions of one link
+constexpr int GEOM_THREADS = 256;
+constexpr int REGION_MARGIN = 4;
+
+// ---------------------------------------------------------------- lattices --
+template <int Q_> struct Lat;
+
+template <> struct Lat<9> {
+    static constexpr int Q = 9, D = 2;
+    __host__ __device__ static constexpr int cx(int i) {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+    }
+    template <class T> __host__ __device__ static constexpr T w(int i) {
+        return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
+    }
+};
+
+template <> struct Lat<19> {
+    static constexpr int Q = 19, D = 3;
+    // 0 rest; 1..6 +-x +-y +-z; 7..18 face diagonals in opposite pairs
+    __host__ __device__ static constexpr int cx(int i) {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+             : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+             : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+             : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : ((i % 2) == 1 ? i + 1 : i - 1);
+    }
+    template <class T> __host__ __device__ static constexpr T w(int i) {
+        return i == 0 ? T(1) / T(3) : (i <= 6 ? T(1) / T(18) : T(1) / T(36));
+    }
+};
+
+// run-time indexed copies of the tables (for kernels that walk link lists)
+struct LatTab {
+    int8_t c[19][3];
+    int8_t opp[19];
+    double w[19];
+};
+
+template <class L> __host__ __device__ inline LatTab make_tab() {
+    LatTab t{};
+    for (int i = 0; i < L::Q; ++i) {
+        t.c[i][0] = (int8_t)L::cx(i);
+        t.c[i][1] = (int8_t)L::cy(i);
+        t.c[i][2] = (int8_t)L::cz(i);
+        t.opp[i] = (int8_t)L::opp(i);
+        t.w[i] = L::template w<double>(i);
+    }
+    return t;
+}
+
+// ------------------------------------------------------- precision policies --
+struct PF64 { // FP64 arithmetic, FP64 storage of f (no shift)
+    using S = double;
+    using C = double;
+    static constexpr bool exact = true;
+};
+struct PF32 { // FP32 arithmetic, storage of f - w in FP32
+    using S = float;
+    using C = float;
+    static constexpr bool exact = false;
+};
+struct PF16 { // FP32 arithmetic, storage of f - w in FP16
+    using S = __half;
+    using C = float;
+    static constexpr bool exact = false;
+};
+
+__device__ __forceinline__ double ldS(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ldS(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldS(const __half *p) { return __half2float(__ldg(p)); }
+// plain loads for buffers written earlier in the same kernel's lifetime
+__device__ __forceinline__ double ldP(const double *p) { return *p; }
+__device__ __forceinline__ float ldP(const float *p) { return *p; }
+__device__ __forceinline__ float ldP(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void stS(double *p, double v) { *p = v; }
+__device__ __forceinline__ void stS(float *p, float v) { *p = v; }
+__device__ __forceinline__ void stS(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ float roundS(const __half *, float v) { return __half2float(__float2half_rn(v)); }
+__device__ __forceinline__ float roundS(const float *, float v) { return v; }
+__device__ __forceinline__ double roundS(const double *, double v) { return v; }
+
+// ------------------------------------------------------------ kernel params --
+struct Params {
+    int nx, ny, nz;
+    int per[3];  // periodic axes
+    int edge[6]; // x-lo x-hi y-lo y-hi z-lo z-hi
+    long long N; // nx*ny*nz
+    int eq;      // 0 quasi-incompressible, 1 standard
+    int inlet_parabolic;
+    int has_force;
+    int refill;
+    int nb;      // bodies
+    int nonper;  // 1 if any axis is non-periodic
+    long long series_cap;
+    double tau, omega, rho0, u_in;
+    double g[3];
+    float omegaf, rho0f, u_inf;
+    float gf[3];
+};
+
+struct BodyDev {
+    int shape;   // 0 cylinder (x-y disc), 1 sphere
+    int halfway; // Delta = 1/2 on every link
+    int moving;  // U or W non-zero
+    int nchunks; // geometry chunks of its region
+    double R;
+    double X0[3], U[3], W[3];
+    long long t0;
+    long long link_off, link_cap; // segment in the link arrays
+    long long apm_off, apm_cap;   // segment in the covered/uncovered list
+    int ext[3];                   // region extents (cells) per axis
+    int chunk_base;               // first geometry chunk of this body
+};
+
+// ------------------------------------------------------- FP64 geometry ------
+// These follow one fixed expression each; they are shared by all precision
+// modes so the solid set and link distances never depend on the mode.
+__device__ __forceinline__ double mimg(const Params &p, int a, double v) {
+    if (!p.per[a]) return v;
+    double L = (double)(a == 0 ? p.nx : (a == 1 ? p.ny : p.nz));
+    return v - L * floor(v / L + 0.5);
+}
+
+__device__ __forceinline__ void pose(const BodyDev &b, long long t, double X[3]) {
+    double dt = (double)(t - b.t0);
+    for (int k = 0; k < 3; ++k) X[k] = b.X0[k] + dt * b.U[k];
+}
+
+__device__ __forceinline__ void disp(const Params &p, const double X[3], int x, int y, int z, double r[3]) {
+    r[0] = mimg(p, 0, (double)x - X[0]);
+    r[1] = mimg(p, 1, (double)y - X[1]);
+    r[2] = mimg(p, 2, (double)z - X[2]);
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ void body_velocity(const BodyDev &b, const double r[3], double v[3]) {
+    double wr[3];
+    cross3(b.W, r, wr);
+    for (int k = 0; k < 3; ++k) v[k] = b.U[k] + wr[k];
+}
+
+__device__ __forceinline__ bool inside(const BodyDev &b, const double r[3]) {
+    double s = r[0] * r[0] + r[1] * r[1];
+    if (b.shape == 1) s = s + r[2] * r[2];
+    return s <= b.R * b.R;
+}
+
+// Delta of Sec. 2.1: root s in (0,1] of |d - s c|^2 = R^2 (x_F outside)
+__device__ __forceinline__ double link_delta(const BodyDev &b, const double d[3], int cxi, int cyi, int czi) {
+    if (b.halfway) return 0.5;
+    double cx = cxi, cy = cyi, cz = czi;
+    double a, bb, cc;
+    if (b.shape == 1) {
+        a = cx * cx + cy * cy + cz * cz;
+        bb = d[0] * cx + d[1] * cy + d[2] * cz;
+        cc = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - b.R * b.R;
+    } else {
+        a = cx * cx + cy * cy;
+        bb = d[0] * cx + d[1] * cy;
+        cc = (d[0] * d[0] + d[1] * d[1]) - b.R * b.R;
+    }
+    (void)a;
+    double disc = bb * bb - a * cc;
+    if (disc < 0.0) disc = 0.0;
+    double s = cc / (bb + sqrt(disc));
+    if (s > 1.0) s = 1.0;
+    if (s < 0.0) s = 0.0;
+    return s;
+}
+
+__device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ long long cell_of(const Params &p, int x, int y, int z) {
+    return ((long long)z * p.ny + y) * p.nx + x;
+}
+
+__device__ __forceinline__ void coords_of(const Params &p, long long c, int &x, int &y, int &z) {
+    long long row = c / p.nx;
+    x = (int)(c - row * p.nx);
+    z = (int)(row / p.ny);
+    y = (int)(row - (long long)z * p.ny);
+}
+
+// i-th coordinate of a region axis in ascending wrapped order: the region
+// covers `len` consecutive (unwrapped) coordinates starting at lo.
+// Returns -1 for a coordinate outside a non-periodic axis.
+__device__ __forceinline__ int region_axis(int k, int lo, int len, int n, int periodic) {
+    if (!periodic) {
+        int v = lo + k;
+        return (v < 0 || v >= n) ? -1 : v;
+    }
+    if (len >= n) return k < n ? k : -1;
+    int s0 = ((lo % n) + n) % n;
+    int wr = s0 + len - n;
+    if (wr > 0) return k < wr ? k : s0 + (k - wr);
+    return s0 + k;
+}
+
+// region of a body covering its poses at t and t+1, dilated by `margin`
+__device__ __forceinline__ void region_lo(const Params &p, const BodyDev &b, long long t, int margin, int lo[3]) {
+    double X0[3], X1[3];
+    pose(b, t, X0);
+    pose(b, t + 1, X1);
+    for (int a = 0; a < 3; ++a) {
+        int n = a == 0 ? p.nx : (a == 1 ? p.ny : p.nz);
+        bool full = (a == 2 && b.shape == 0) || b.ext[a] >= n;
+        if (full) {
+            lo[a] = 0;
+            continue;
+        }
+        double m = X0[a] < X1[a] ? X0[a] : X1[a];
+        lo[a] = (int)floor(m - b.R) - margin;
+    }
+}
+
+} // namespace lbm

@@ -1,0 +1,28 @@
+// lbm_fp64.cu -- FP64 mode: FP64 arithmetic and storage, every formula in the
+// fixed operation order of the FP64 CPU oracle (built with --fmad=false).
+#include "lbm_launch.cuh"
+
+namespace lbm {
+
+cudaError_t launch_init_p0(int Q, const Params &p, void *dst, void *mac, const uint8_t *flags, const double u0[3],
+                           cudaStream_t s) {
+    return Q == 9 ? init_t<Lat<9>, PF64>(p, dst, mac, flags, u0, s) : init_t<Lat<19>, PF64>(p, dst, mac, flags, u0, s);
+}
+cudaError_t launch_links_p0(int Q, const Params &p, const StepBufs &sb, int grid, cudaStream_t s) {
+    return Q == 9 ? links_t<Lat<9>, PF64>(p, sb, grid, s) : links_t<Lat<19>, PF64>(p, sb, grid, s);
+}
+cudaError_t launch_bulk_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    return Q == 9 ? bulk_t<Lat<9>, PF64>(p, sb, s) : bulk_t<Lat<19>, PF64>(p, sb, s);
+}
+cudaError_t launch_imp_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    return Q == 9 ? imp_t<Lat<9>, PF64>(p, sb, s) : imp_t<Lat<19>, PF64>(p, sb, s);
+}
+
+cudaError_t launch_reduce(int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    if (p.nb == 0) return cudaSuccess;
+    if (prec == 0) k_reduce<true><<<p.nb, RED_THREADS, 0, s>>>(p, sb);
+    else k_reduce<false><<<p.nb, RED_THREADS, 0, s>>>(p, sb);
+    return cudaGetLastError();
+}
+
+} // namespace lbm

@@ -1,0 +1,352 @@
+// lbm_geom.cu -- body geometry on the device (FP64, identical in every
+// precision mode): solid owner of each node, covered / uncovered node lists
+// A+ / A- between t and t+1 (Sec. 3.2.2), node flags, and the cut-link lists
+// (fluid node x_F, direction i with x_F - c_i inside the body, fractional
+// distance Delta of Sec. 2.1).
+//
+// Work is split into chunks of GEOM_THREADS consecutive cells of each body's
+// region (a box covering the body at t and t+1 plus a margin), enumerated in
+// ascending cell order even across periodic seams.  Lists are compacted with
+// block scans and per-chunk offsets, so every list is in cell order (then
+// direction order) whatever the launch configuration: the FP64 mode can then
+// sum link contributions in exactly the oracle's order.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// exclusive block scan of v over GEOM_THREADS threads; *total gets the sum
+__device__ __forceinline__ int block_excl_scan(int v, int *total) {
+    __shared__ int wsum[GEOM_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = warp_incl_scan(v);
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < GEOM_THREADS / 32 ? wsum[lane] : 0;
+        s = warp_incl_scan(s);
+        if (lane < GEOM_THREADS / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    int base = wid ? wsum[wid - 1] : 0;
+    *total = wsum[GEOM_THREADS / 32 - 1];
+    __syncthreads();
+    return base + inc - v;
+}
+
+// sum of the counts of the chunks [first, first + n) (block-wide)
+__device__ __forceinline__ long long block_sum_range(const int *cnt, int first, int n) {
+    __shared__ long long red[GEOM_THREADS];
+    long long s = 0;
+    for (int k = threadIdx.x; k < n; k += GEOM_THREADS) s += cnt[first + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = GEOM_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    long long r = red[0];
+    __syncthreads();
+    return r;
+}
+
+struct RegionCell {
+    bool valid;
+    int x, y, z;
+    long long cell;
+};
+
+__device__ __forceinline__ RegionCell region_cell(const Params &p, const BodyDev &B, const int lo[3], int chunk) {
+    RegionCell rc{false, 0, 0, 0, 0};
+    const long long vol = (long long)B.ext[0] * B.ext[1] * B.ext[2];
+    const long long k = (long long)chunk * GEOM_THREADS + threadIdx.x;
+    if (k >= vol) return rc;
+    const int kx = (int)(k % B.ext[0]);
+    const int ky = (int)((k / B.ext[0]) % B.ext[1]);
+    const int kz = (int)(k / ((long long)B.ext[0] * B.ext[1]));
+    rc.x = region_axis(kx, lo[0], B.ext[0], p.nx, p.per[0]);
+    rc.y = region_axis(ky, lo[1], B.ext[1], p.ny, p.per[1]);
+    rc.z = region_axis(kz, lo[2], B.ext[2], p.nz, p.per[2]);
+    if (rc.x < 0 || rc.y < 0 || rc.z < 0) return rc;
+    rc.valid = true;
+    rc.cell = cell_of(p, rc.x, rc.y, rc.z);
+    return rc;
+}
+
+// neighbour x - k c_i; -1 if it falls outside a non-periodic axis
+template <class L>
+__device__ __forceinline__ long long nbr(const Params &p, int x, int y, int z, int i, int k) {
+    int q[3] = {x - k * L::cx(i), y - k * L::cy(i), z - k * L::cz(i)};
+    const int n[3] = {p.nx, p.ny, p.nz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (q[a] >= 0 && q[a] < n[a]) continue;
+        if (!p.per[a]) return -1;
+        q[a] = ((q[a] % n[a]) + n[a]) % n[a];
+    }
+    return cell_of(p, q[0], q[1], q[2]);
+}
+
+__device__ __forceinline__ bool edge_node(const Params &p, int x, int y, int z) {
+    return (!p.per[0] && (x == 0 || x == p.nx - 1)) || (!p.per[1] && (y == 0 || y == p.ny - 1)) ||
+           (!p.per[2] && (z == 0 || z == p.nz - 1));
+}
+
+// store macros at x if x is fluid and within two hops of a solid node (the
+// fluid end of a cut link, or its u_G node), or on a non-periodic face
+template <class L>
+__device__ __forceinline__ uint8_t node_flags(const Params &p, const uint16_t *owner_t, const uint16_t *owner_m,
+                                              int x, int y, int z, long long cell) {
+    uint8_t f = owner_t[cell] ? FL_SOLID : 0;
+    bool mac = edge_node(p, x, y, z);
+    if (!mac && owner_m[cell] == 0) {
+        for (int i = 1; i < L::Q && !mac; ++i) {
+            long long a = nbr<L>(p, x, y, z, i, 1);
+            if (a >= 0 && owner_m[a]) mac = true;
+            long long b = nbr<L>(p, x, y, z, i, 2);
+            if (b >= 0 && owner_m[b]) mac = true;
+        }
+    }
+    if (owner_m[cell]) mac = false;
+    return f | (mac ? FL_MAC : 0);
+}
+
+__global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, uint16_t *owner, long long t_pose) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const BodyDev &B = g.bodies[cm.x];
+    int lo[3];
+    region_lo(p, B, t_pose, REGION_MARGIN, lo);
+    RegionCell rc = region_cell(p, B, lo, cm.y);
+    if (!rc.valid) return;
+    double X[3], r[3];
+    pose(B, t_pose, X);
+    disp(p, X, rc.x, rc.y, rc.z, r);
+    if (inside(B, r)) owner[rc.cell] = (uint16_t)(cm.x + 1);
+}
+
+// moving step, part a: owner at t+1 for this body's region; count A+/A-
+__global__ void __launch_bounds__(GEOM_THREADS) k_geom_a(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    int lo[3];
+    region_lo(p, B, g.t, REGION_MARGIN, lo);
+    RegionCell rc = region_cell(p, B, lo, cm.y);
+    int flag = 0;
+    if (rc.valid) {
+        const uint16_t me = (uint16_t)(b + 1);
+        const bool in_t = g.owner_t[rc.cell] == me;
+        double X1[3], r[3];
+        pose(B, g.t + 1, X1);
+        disp(p, X1, rc.x, rc.y, rc.z, r);
+        const bool in1 = inside(B, r);
+        if (in1) g.owner_t1[rc.cell] = me;
+        else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
+        flag = in_t != in1;
+    }
+    int total;
+    block_excl_scan(flag, &total);
+    if (threadIdx.x == 0) g.chunk_cnt_apm[blockIdx.x] = total;
+}
+
+// part b: A+/A- lists (moving step), node flags, link counts
+template <class L>
+__global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    const uint16_t me = (uint16_t)(b + 1);
+    const uint16_t *owner_L = g.owner_t1; // geometry of the links being built
+    int lo[3];
+    region_lo(p, B, g.t, REGION_MARGIN, lo);
+    RegionCell rc = region_cell(p, B, lo, cm.y);
+    const int first = blockIdx.x - cm.y; // first chunk of this body
+    if (g.do_apm) {
+        int flag = 0, sign = 0;
+        if (rc.valid) {
+            const bool in_t = g.owner_t[rc.cell] == me, in1 = g.owner_t1[rc.cell] == me;
+            flag = in_t != in1;
+            sign = in1 ? 1 : -1;
+        }
+        const long long before = block_sum_range(g.chunk_cnt_apm, first, cm.y);
+        int total;
+        const int pos = block_excl_scan(flag, &total);
+        if (flag) {
+            const long long at = B.apm_off + before + pos;
+            if (before + pos < B.apm_cap) {
+                g.apm_cell[at] = (uint32_t)rc.cell;
+                g.apm_sign[at] = (int8_t)sign;
+            }
+        }
+        if (cm.y == B.nchunks - 1 && threadIdx.x == 0) {
+            long long n = before + total;
+            g.apm_cnt[b] = n < B.apm_cap ? n : B.apm_cap;
+        }
+    }
+    int nl = 0;
+    if (rc.valid) {
+        if (g.do_flags) g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
+        if (owner_L[rc.cell] == 0) {
+            for (int i = 1; i < L::Q; ++i) {
+                long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                if (a >= 0 && owner_L[a] == me) nl++;
+            }
+        }
+    }
+    int total;
+    block_excl_scan(nl, &total);
+    if (threadIdx.x == 0) g.chunk_cnt_link[blockIdx.x] = total;
+}
+
+// part c: fill the cut-link list of the body (cell order, then direction)
+template <class L>
+__global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    const uint16_t me = (uint16_t)(b + 1);
+    const uint16_t *owner_L = g.owner_t1;
+    int lo[3];
+    region_lo(p, B, g.t, REGION_MARGIN, lo);
+    RegionCell rc = region_cell(p, B, lo, cm.y);
+    const int first = blockIdx.x - cm.y;
+    unsigned mask = 0;
+    int nl = 0;
+    if (rc.valid && owner_L[rc.cell] == 0) {
+        for (int i = 1; i < L::Q; ++i) {
+            long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+            if (a >= 0 && owner_L[a] == me) {
+                mask |= 1u << i;
+                nl++;
+            }
+        }
+    }
+    const long long before = block_sum_range(g.chunk_cnt_link, first, cm.y);
+    int total;
+    const int pos = block_excl_scan(nl, &total);
+    if (nl) {
+        double X[3], d[3];
+        pose(B, g.t_link, X);
+        disp(p, X, rc.x, rc.y, rc.z, d);
+        long long at = before + pos;
+        for (int i = 1; i < L::Q; ++i) {
+            if (!(mask & (1u << i))) continue;
+            if (at < B.link_cap) {
+                const long long j = B.link_off + at;
+                g.Lcell[j] = (uint32_t)rc.cell;
+                g.Ldir[j] = (uint8_t)i;
+                g.Ldelta[j] = link_delta(B, d, L::cx(i), L::cy(i), L::cz(i));
+            }
+            at++;
+        }
+    }
+    if (cm.y == B.nchunks - 1 && threadIdx.x == 0) {
+        long long n = before + total;
+        g.link_cnt[b] = n < B.link_cap ? n : B.link_cap;
+    }
+}
+
+template <class L>
+__global__ void k_flags_full(Params p, const uint16_t *owner, uint8_t *flags) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx) return;
+    const long long cell = cell_of(p, x, y, z);
+    flags[cell] = node_flags<L>(p, owner, owner, x, y, z, cell);
+}
+
+template <class L, class P>
+__global__ void k_export(Params p, const typename P::S *pop, double *out) {
+    const long long n = (long long)L::Q * p.N;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / p.N);
+        double v = (double)ldP(pop + k);
+        if constexpr (!P::exact) v += L::template w<double>(i);
+        out[k] = v;
+    }
+}
+
+template <class L, class P>
+__global__ void k_import(Params p, const double *in, typename P::S *pop) {
+    const long long n = (long long)L::Q * p.N;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / p.N);
+        double v = in[k];
+        if constexpr (!P::exact) v -= L::template w<double>(i);
+        stS(pop + k, (typename P::C)v);
+    }
+}
+
+} // namespace
+
+cudaError_t launch_raster(int, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,
+                          cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    k_raster<<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g, owner, t_pose);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom_a(int, const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    k_geom_a<<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom_b(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    if (Q == 9) k_geom_b<Lat<9>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    else k_geom_b<Lat<19>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom_c(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    if (Q == 9) k_geom_c<Lat<9>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    else k_geom_c<Lat<19>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flags_full(int Q, const Params &p, const uint16_t *owner, uint8_t *flags, cudaStream_t s) {
+    const int bx = p.nx >= 128 ? 128 : 32;
+    dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+    if (Q == 9) k_flags_full<Lat<9>><<<grid, bx, 0, s>>>(p, owner, flags);
+    else k_flags_full<Lat<19>><<<grid, bx, 0, s>>>(p, owner, flags);
+    return cudaGetLastError();
+}
+
+template <class L>
+static cudaError_t export_t(int prec, const Params &p, const void *pop, double *out, cudaStream_t s) {
+    const int grid = 4 * 152;
+    if (prec == 0) k_export<L, PF64><<<grid, 256, 0, s>>>(p, (const double *)pop, out);
+    else if (prec == 1) k_export<L, PF32><<<grid, 256, 0, s>>>(p, (const float *)pop, out);
+    else k_export<L, PF16><<<grid, 256, 0, s>>>(p, (const __half *)pop, out);
+    return cudaGetLastError();
+}
+
+template <class L>
+static cudaError_t import_t(int prec, const Params &p, const double *in, void *pop, cudaStream_t s) {
+    const int grid = 4 * 152;
+    if (prec == 0) k_import<L, PF64><<<grid, 256, 0, s>>>(p, in, (double *)pop);
+    else if (prec == 1) k_import<L, PF32><<<grid, 256, 0, s>>>(p, in, (float *)pop);
+    else k_import<L, PF16><<<grid, 256, 0, s>>>(p, in, (__half *)pop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s) {
+    return Q == 9 ? export_t<Lat<9>>(prec, p, pop, out, s) : export_t<Lat<19>>(prec, p, pop, out, s);
+}
+
+cudaError_t launch_import(int Q, int prec, const Params &p, const double *in, void *pop, cudaStream_t s) {
+    return Q == 9 ? import_t<Lat<9>>(prec, p, in, pop, s) : import_t<Lat<19>>(prec, p, in, pop, s);
+}
+
+} // namespace lbm

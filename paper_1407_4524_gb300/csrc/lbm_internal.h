@@ -1,0 +1,54 @@
+// lbm_internal.h -- host-side launcher interface between the C ABI
+// (lbm_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_dev.cuh"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+struct GeomArgs {
+    const BodyDev *bodies;
+    const int2 *chunk_map; // (body, chunk within the body's region)
+    int nchunks;
+    const uint16_t *owner_t;
+    uint16_t *owner_t1;
+    uint8_t *flags;
+    int *chunk_cnt_apm;
+    int *chunk_cnt_link;
+    uint32_t *apm_cell;
+    int8_t *apm_sign;
+    long long *apm_cnt;
+    uint32_t *Lcell;
+    uint8_t *Ldir;
+    double *Ldelta;
+    long long *link_cnt;
+    long long t;      // current step
+    long long t_link; // pose time of the links being built
+    int do_apm;       // covered/uncovered lists (moving step)
+    int do_flags;     // rewrite flags in the regions
+};
+
+// precision: 0 FP64, 1 FP32, 2 FP16; Q: 9 or 19
+cudaError_t launch_init(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
+                        const double u0[3], cudaStream_t s);
+cudaError_t launch_links(int Q, int prec, const Params &p, const StepBufs &sb, int grid, cudaStream_t s);
+cudaError_t launch_bulk(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_imp(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_reduce(int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+
+// geometry (all FP64, mode independent)
+cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,
+                          cudaStream_t s);
+cudaError_t launch_geom_a(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
+cudaError_t launch_geom_b(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
+cudaError_t launch_geom_c(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
+cudaError_t launch_flags_full(int Q, const Params &p, const uint16_t *owner, uint8_t *flags, cudaStream_t s);
+
+// population export: fhat as FP64 f (adds w back for the shifted modes)
+cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);
+cudaError_t launch_import(int Q, int prec, const Params &p, const double *in, void *pop, cudaStream_t s);
+
+} // namespace lbm

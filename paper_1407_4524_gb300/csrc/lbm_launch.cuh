@@ -1,0 +1,46 @@
+// lbm_launch.cuh -- typed launchers of the step kernels; included by the
+// precision translation units (lbm_fp64.cu, lbm_fp32.cu).
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+inline dim3 bulk_block(const Params &p) {
+    int bx = BULK_THREADS;
+    while (bx > 32 && bx / 2 >= p.nx) bx /= 2;
+    return dim3(bx, 1, 1);
+}
+
+inline dim3 bulk_grid(const Params &p) {
+    dim3 b = bulk_block(p);
+    return dim3((p.nx + b.x - 1) / b.x, p.ny, p.nz);
+}
+
+template <class L, class P>
+cudaError_t init_t(const Params &p, void *dst, void *mac, const uint8_t *flags, const double u0[3], cudaStream_t s) {
+    k_init<L, P><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, (typename P::S *)dst, (typename P::C *)mac, flags, u0[0],
+                                                         u0[1], u0[2]);
+    return cudaGetLastError();
+}
+
+template <class L, class P> cudaError_t links_t(const Params &p, const StepBufs &sb, int grid, cudaStream_t s) {
+    if (p.nb == 0 || grid <= 0) return cudaSuccess;
+    k_links<L, P><<<grid, LINK_THREADS, 0, s>>>(p, sb);
+    return cudaGetLastError();
+}
+
+template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
+    k_bulk<L, P><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, (const typename P::S *)sb.src, (typename P::S *)sb.dst,
+                                                         sb.flags, (const typename P::C *)sb.mac_t,
+                                                         (typename P::C *)sb.mac_t1);
+    return cudaGetLastError();
+}
+
+template <class L, class P> cudaError_t imp_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
+    if (sb.n_moving == 0) return cudaSuccess;
+    k_imp<L, P><<<sb.n_moving, IMP_THREADS, 0, s>>>(p, sb);
+    return cudaGetLastError();
+}
+
+} // namespace lbm

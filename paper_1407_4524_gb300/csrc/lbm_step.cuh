@@ -1,0 +1,653 @@
+// lbm_step.cuh -- the kernels of one time step t -> t+1 (templated on the
+// lattice L and the precision policy P; instantiated in lbm_fp64.cu and
+// lbm_fp32.cu).
+//
+// Storage convention: the population buffer of step t holds the
+// post-collision values fhat(x, t) (Eq. collision) at every fluid node.  One
+// step is, in launch order:
+//   k_links  : for every cut link (x_F fluid, x_A = x_F - c_i solid) compute
+//              the wall value fhat_i(x_A, t) of Eq. Fillipova_interpolation and
+//              store it in the (otherwise unused) slot i of the solid node x_A,
+//              and write the link's momentum-exchange contributions
+//              (Eqs. flow_force_2, flow_torque_2, ForceInMovementMovingFrame,
+//              TorqueInMovementMovingFrame), which by Eq. Equalities need
+//              exactly that wall value and fhat_ib(x_F, t);
+//   k_bulk   : pull-streaming f_i(x, t+1) = fhat_i(x - c_i, t) (Eq.
+//              streaming) -- at cut links the pull reads the wall value --,
+//              moments (Eqs. LBMmacroscopics_0/1), BGK collision, store;
+//   k_imp    : moving bodies only -- covered / uncovered nodes A+ / A-
+//              (Sec. 3.2.2): impulsive terms of Eqs. ForceInMovement /
+//              TorqueInMovement, refill of uncovered nodes;
+//   k_reduce : deterministic per-body sum of the link contributions into the
+//              force/torque series row of step t.
+//
+// P::exact (FP64 mode) evaluates every formula with the same fixed operation
+// order as the FP64 CPU oracle, so the FP64 mode reproduces it bit for bit.
+// The FP32/FP16 modes store f - w and evaluate the deviation form of the same
+// formulas with FP32 arithmetic; the momentum-exchange sums stay FP64.
+#pragma once
+
+#include "lbm_dev.cuh"
+
+namespace lbm {
+
+constexpr int BULK_THREADS = 128;
+constexpr int LINK_THREADS = 256;
+constexpr int RED_THREADS = 256;
+constexpr int IMP_THREADS = 128;
+
+struct StepBufs {
+    const void *src; // fhat(t)   (k_links also writes wall values into it)
+    void *dst;       // fhat(t+1)
+    const void *mac_t;
+    void *mac_t1;
+    const uint8_t *flags;
+    const uint16_t *owner_t;
+    const BodyDev *bodies;
+    const int *moving_ids;
+    int n_moving;
+    const long long *link_cnt; // per body, current link buffer
+    const uint32_t *Lcell;
+    const uint8_t *Ldir;
+    const double *Ldelta;
+    double *me;
+    const long long *apm_cnt;
+    const uint32_t *apm_cell;
+    const int8_t *apm_sign;
+    double *imp;
+    double *series;
+    unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered
+    long long t;
+};
+
+// =================================================================== exact ==
+// FP64, operation order of the oracle (one expression per formula).
+
+template <class L>
+__device__ __forceinline__ double feq_x(const Params &p, int i, double rho, const double u[3]) {
+    double cu = (double)L::cx(i) * u[0] + (double)L::cy(i) * u[1] + (double)L::cz(i) * u[2];
+    double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double w = L::template w<double>(i);
+    if (p.eq == 0) return w * (rho + p.rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+    return w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+}
+
+template <class L>
+__device__ __forceinline__ void moments_x(const Params &p, const double f[], double &rho, double u[3]) {
+    double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        r += f[i];
+        j0 += (double)L::cx(i) * f[i];
+        j1 += (double)L::cy(i) * f[i];
+        j2 += (double)L::cz(i) * f[i];
+    }
+    if (p.has_force) {
+        j0 += 0.5 * p.g[0];
+        j1 += 0.5 * p.g[1];
+        j2 += 0.5 * p.g[2];
+    }
+    double den = p.eq == 0 ? p.rho0 : r;
+    rho = r;
+    u[0] = j0 / den;
+    u[1] = j1 / den;
+    u[2] = j2 / den;
+}
+
+template <class L>
+__device__ __forceinline__ void collide_x(const Params &p, double f[], double rho, const double u[3]) {
+    const double omega = p.omega;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        double fi = f[i];
+        double v = fi - omega * (fi - feq_x<L>(p, i, rho, u));
+        if (p.has_force) {
+            double cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            double cg = cx * p.g[0] + cy * p.g[1] + cz * p.g[2];
+            double ug = u[0] * p.g[0] + u[1] * p.g[1] + u[2] * p.g[2];
+            double cu = cx * u[0] + cy * u[1] + cz * u[2];
+            v = v + (1.0 - 0.5 * omega) * L::template w<double>(i) * (3.0 * (cg - ug) + 9.0 * cu * cg);
+        }
+        f[i] = v;
+    }
+}
+
+// fictitious equilibrium g_ib of Eq. Fillipova_equilibrium
+__device__ __forceinline__ double geq_x(const Params &p, const LatTab &tb, int ib, double rhoF,
+                                        const double ubf[3], const double uF[3]) {
+    double c0 = tb.c[ib][0], c1 = tb.c[ib][1], c2 = tb.c[ib][2];
+    double cbu = c0 * ubf[0] + c1 * ubf[1] + c2 * ubf[2];
+    double cbF = c0 * uF[0] + c1 * uF[1] + c2 * uF[2];
+    double uFsq = uF[0] * uF[0] + uF[1] * uF[1] + uF[2] * uF[2];
+    if (p.eq == 0) return tb.w[ib] * (rhoF + p.rho0 * (3.0 * cbu + 4.5 * cbF * cbF - 1.5 * uFsq));
+    return tb.w[ib] * rhoF * (1.0 + 3.0 * cbu + 4.5 * cbF * cbF - 1.5 * uFsq);
+}
+
+// ==================================================================== fast ==
+// FP32, deviation form: d = f - w, drho = rho - 1.
+
+template <class L>
+__device__ __forceinline__ void moments_f(const Params &p, const float f[], float &drho, float u[3]) {
+    float r = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        r += f[i];
+        if (L::cx(i) == 1) j0 += f[i];
+        if (L::cx(i) == -1) j0 -= f[i];
+        if (L::cy(i) == 1) j1 += f[i];
+        if (L::cy(i) == -1) j1 -= f[i];
+        if (L::cz(i) == 1) j2 += f[i];
+        if (L::cz(i) == -1) j2 -= f[i];
+    }
+    if (p.has_force) {
+        j0 = fmaf(0.5f, p.gf[0], j0);
+        j1 = fmaf(0.5f, p.gf[1], j1);
+        j2 = fmaf(0.5f, p.gf[2], j2);
+    }
+    float den = p.eq == 0 ? p.rho0f : 1.0f + r;
+    float inv = 1.0f / den;
+    drho = r;
+    u[0] = j0 * inv;
+    u[1] = j1 * inv;
+    u[2] = j2 * inv;
+}
+
+// deviation of the equilibrium, f^eq_i - w_i
+template <class L>
+__device__ __forceinline__ float dfeq_f(const Params &p, int i, float drho, const float u[3], float usq15) {
+    float cu = (float)L::cx(i) * u[0] + (float)L::cy(i) * u[1] + (float)L::cz(i) * u[2];
+    float poly = fmaf(cu, fmaf(4.5f, cu, 3.0f), -usq15); // 3cu + 4.5cu^2 - 1.5u^2
+    float rr = p.eq == 0 ? p.rho0f : 1.0f + drho;
+    return L::template w<float>(i) * fmaf(rr, poly, drho);
+}
+
+template <class L>
+__device__ __forceinline__ void collide_f(const Params &p, float f[], float drho, const float u[3]) {
+    const float om = p.omegaf;
+    const float usq15 = 1.5f * fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        float fe = dfeq_f<L>(p, i, drho, u, usq15);
+        float v = fmaf(-om, f[i] - fe, f[i]);
+        if (p.has_force) {
+            float cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            float cg = cx * p.gf[0] + cy * p.gf[1] + cz * p.gf[2];
+            float ug = u[0] * p.gf[0] + u[1] * p.gf[1] + u[2] * p.gf[2];
+            float cu = cx * u[0] + cy * u[1] + cz * u[2];
+            v = fmaf((1.0f - 0.5f * om) * L::template w<float>(i), fmaf(9.0f * cu, cg, 3.0f * (cg - ug)), v);
+        }
+        f[i] = v;
+    }
+}
+
+__device__ __forceinline__ float dgeq_f(const Params &p, const LatTab &tb, int ib, float drhoF, const float ubf[3],
+                                        const float uF[3]) {
+    float c0 = tb.c[ib][0], c1 = tb.c[ib][1], c2 = tb.c[ib][2];
+    float cbu = c0 * ubf[0] + c1 * ubf[1] + c2 * ubf[2];
+    float cbF = c0 * uF[0] + c1 * uF[1] + c2 * uF[2];
+    float uFsq = uF[0] * uF[0] + uF[1] * uF[1] + uF[2] * uF[2];
+    float poly = 3.0f * cbu + 4.5f * cbF * cbF - 1.5f * uFsq;
+    float rr = p.eq == 0 ? p.rho0f : 1.0f + drhoF;
+    return (float)tb.w[ib] * fmaf(rr, poly, drhoF);
+}
+
+// ============================================================== streaming ==
+
+// inlet velocity at the wall point of an edge link (x_B = x_F - c_i / 2)
+__device__ __forceinline__ double inlet_u(const Params &p, int y, int cy) {
+    if (!p.inlet_parabolic) return p.u_in;
+    double ny = (double)p.ny;
+    double yb = (double)y - 0.5 * (double)cy;
+    return 4.0 * p.u_in * (yb + 0.5) * ((ny - 0.5) - yb) / (ny * ny);
+}
+
+// Pull of population i at a node on a non-periodic face.  Out-of-range
+// sources: wall / inlet links (Delta = 1/2: chi = 0, so the curved-wall rule
+// reduces to moving bounce-back with u_B = 0 / the inlet profile), outlet
+// copies the last interior column; a wall wins at corners.
+template <class L, class P>
+__device__ __noinline__ typename P::C pull_edge(const Params &p, const typename P::S *__restrict__ src,
+                                                const typename P::C *__restrict__ mac_t, int x, int y, int z,
+                                                long long cell, int i) {
+    using C = typename P::C;
+    int s[3] = {x - L::cx(i), y - L::cy(i), z - L::cz(i)};
+    const int n[3] = {p.nx, p.ny, p.nz};
+    bool wall = false, inlet = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int side = s[a] < 0 ? 0 : (s[a] >= n[a] ? 1 : -1);
+        if (side < 0) continue;
+        int e = p.edge[2 * a + side];
+        if (e == 0) s[a] += side == 0 ? n[a] : -n[a];
+        else if (e == 1) wall = true;
+        else if (e == 2) inlet = true;
+        else s[a] = n[a] - 1;
+    }
+    if (wall || inlet) {
+        const int ib = L::opp(i);
+        C fb = ldS(src + (long long)ib * p.N + cell);
+        double uB0 = inlet && !wall ? inlet_u(p, y, L::cy(i)) : 0.0;
+        if constexpr (P::exact) {
+            double uB[3] = {uB0, 0.0, 0.0};
+            double rhow = p.eq == 0 ? p.rho0 : mac_t[4 * cell];
+            double cuB = (double)L::cx(i) * uB[0] + (double)L::cy(i) * uB[1] + (double)L::cz(i) * uB[2];
+            return fb + 2.0 * L::template w<double>(i) * rhow * 3.0 * cuB;
+        } else {
+            float rhow = p.eq == 0 ? p.rho0f : 1.0f + mac_t[4 * cell];
+            float cuB = (float)L::cx(i) * (float)uB0;
+            return fmaf(6.0f * L::template w<float>(i) * rhow, cuB, fb);
+        }
+    }
+    return ldS(src + (long long)i * p.N + cell_of(p, s[0], s[1], s[2]));
+}
+
+__device__ __forceinline__ bool on_edge(const Params &p, int x, int y, int z) {
+    return (!p.per[0] && (x == 0 || x == p.nx - 1)) || (!p.per[1] && (y == 0 || y == p.ny - 1)) ||
+           (!p.per[2] && (z == 0 || z == p.nz - 1));
+}
+
+// f_i(x, t+1) for all i at node (x,y,z)
+template <class L, class P>
+__device__ __forceinline__ void pull_all(const Params &p, const typename P::S *__restrict__ src,
+                                         const typename P::C *__restrict__ mac_t, int x, int y, int z,
+                                         long long cell, typename P::C f[]) {
+    if (p.nonper && on_edge(p, x, y, z)) {
+        for (int i = 0; i < L::Q; ++i) f[i] = pull_edge<L, P>(p, src, mac_t, x, y, z, cell, i);
+        return;
+    }
+    const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
+        const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
+        const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
+        f[i] = ldS(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+    }
+}
+
+// ================================================================== kernels ==
+
+// f(x,0) = f^eq(1, u0); store fhat(x,0) and the moments of f(x,0)
+template <class L, class P>
+__global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *__restrict__ dst,
+                                                       typename P::C *__restrict__ mac,
+                                                       const uint8_t *__restrict__ flags, double u0x, double u0y,
+                                                       double u0z) {
+    using C = typename P::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx) return;
+    const long long cell = cell_of(p, x, y, z);
+    const bool mac_here = flags[cell] & FL_MAC;
+    C f[L::Q];
+    if constexpr (P::exact) {
+        double u0[3] = {u0x, u0y, u0z};
+        for (int i = 0; i < L::Q; ++i) f[i] = feq_x<L>(p, i, 1.0, u0);
+        double rho, u[3];
+        moments_x<L>(p, f, rho, u);
+        if (mac_here) {
+            mac[4 * cell] = rho;
+            mac[4 * cell + 1] = u[0];
+            mac[4 * cell + 2] = u[1];
+            mac[4 * cell + 3] = u[2];
+        }
+        collide_x<L>(p, f, rho, u);
+    } else {
+        float u0[3] = {(float)u0x, (float)u0y, (float)u0z};
+        const float usq15 = 1.5f * (u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+        for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, 0.0f, u0, usq15);
+        float drho, u[3];
+        moments_f<L>(p, f, drho, u);
+        if (mac_here) {
+            mac[4 * cell] = drho;
+            mac[4 * cell + 1] = u[0];
+            mac[4 * cell + 2] = u[1];
+            mac[4 * cell + 3] = u[2];
+        }
+        collide_f<L>(p, f, drho, u);
+    }
+    for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
+}
+
+// pull-stream + moments + BGK collision over every fluid node
+template <class L, class P>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename P::S *__restrict__ src,
+                                                       typename P::S *__restrict__ dst,
+                                                       const uint8_t *__restrict__ flags,
+                                                       const typename P::C *__restrict__ mac_t,
+                                                       typename P::C *__restrict__ mac_t1) {
+    using C = typename P::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx) return;
+    const long long cell = cell_of(p, x, y, z);
+    const uint8_t fl = __ldg(flags + cell);
+    if (fl & FL_SOLID) return;
+    C f[L::Q];
+    pull_all<L, P>(p, src, mac_t, x, y, z, cell, f);
+    if constexpr (P::exact) {
+        double rho, u[3];
+        moments_x<L>(p, f, rho, u);
+        if (fl & FL_MAC) {
+            mac_t1[4 * cell] = rho;
+            mac_t1[4 * cell + 1] = u[0];
+            mac_t1[4 * cell + 2] = u[1];
+            mac_t1[4 * cell + 3] = u[2];
+        }
+        collide_x<L>(p, f, rho, u);
+    } else {
+        float drho, u[3];
+        moments_f<L>(p, f, drho, u);
+        if (fl & FL_MAC) {
+            reinterpret_cast<float4 *>(mac_t1)[cell] = make_float4(drho, u[0], u[1], u[2]);
+        }
+        collide_f<L>(p, f, drho, u);
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
+}
+
+// wall values on cut links + per-link momentum-exchange contributions
+template <class L, class P>
+__global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
+    using S = typename P::S;
+    using C = typename P::C;
+    __shared__ LatTab tb;
+    if (threadIdx.x == 0) tb = make_tab<L>();
+    __syncthreads();
+    S *pop = (S *)sb.src;
+    const C *mac = (const C *)sb.mac_t;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gsz = (long long)gridDim.x * blockDim.x;
+    const long long N = p.N;
+    for (int b = 0; b < p.nb; ++b) {
+        const long long cnt = sb.link_cnt[b];
+        if (gtid >= cnt) continue;
+        const BodyDev &B = sb.bodies[b];
+        double X[3];
+        pose(B, sb.t, X);
+        for (long long k = gtid; k < cnt; k += gsz) {
+            const long long j = B.link_off + k;
+            const long long cell = sb.Lcell[j];
+            const int i = sb.Ldir[j];
+            const double delta = sb.Ldelta[j];
+            int x, y, z;
+            coords_of(p, cell, x, y, z);
+            const int cxi = tb.c[i][0], cyi = tb.c[i][1], czi = tb.c[i][2];
+            const int ib = tb.opp[i];
+            const long long A =
+                cell_of(p, wrap_axis(x - cxi, p.nx), wrap_axis(y - cyi, p.ny), wrap_axis(z - czi, p.nz));
+            double d[3], rB[3], uB[3];
+            disp(p, X, x, y, z, d);
+            rB[0] = d[0] - delta * cxi;
+            rB[1] = d[1] - delta * cyi;
+            rB[2] = d[2] - delta * czi;
+            body_velocity(B, rB, uB);
+            // u_G = u(x_F + c_i, t) for Delta < 1/2 (Sec. 2.1)
+            long long G = -1;
+            if (delta < 0.5) {
+                int g[3] = {x + cxi, y + cyi, z + czi};
+                const int n[3] = {p.nx, p.ny, p.nz};
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) {
+                    if (g[a] >= 0 && g[a] < n[a]) continue;
+                    if (!p.per[a]) ok = false;
+                    else g[a] += g[a] < 0 ? n[a] : -n[a];
+                }
+                if (ok) {
+                    G = cell_of(p, g[0], g[1], g[2]);
+                    if (sb.owner_t[G] != 0) G = -1;
+                }
+                if (G < 0) atomicAdd(&sb.counters[0], 1ull);
+            }
+            double fa, fb, ps[3], pm[3];
+            if constexpr (P::exact) {
+                fb = ldP(pop + (long long)ib * N + cell);
+                const double rhoF = mac[4 * cell];
+                const double uF[3] = {mac[4 * cell + 1], mac[4 * cell + 2], mac[4 * cell + 3]};
+                double ubf[3], chi;
+                if (delta < 0.5) {
+                    if (G >= 0) {
+                        for (int a = 0; a < 3; ++a) ubf[a] = mac[4 * G + 1 + a];
+                        chi = (2.0 * delta - 1.0) / (p.tau - 2.0);
+                    } else {
+                        for (int a = 0; a < 3; ++a) ubf[a] = uF[a];
+                        chi = 0.0;
+                    }
+                } else {
+                    double k3 = 3.0 / (2.0 * delta);
+                    for (int a = 0; a < 3; ++a) ubf[a] = uF[a] + k3 * (uB[a] - uF[a]);
+                    chi = (2.0 * delta - 1.0) / (p.tau + 0.5);
+                }
+                double g = geq_x(p, tb, ib, rhoF, ubf, uF);
+                double rhow = p.eq == 0 ? p.rho0 : rhoF;
+                double cuB = (double)cxi * uB[0] + (double)cyi * uB[1] + (double)czi * uB[2];
+                double bc = (1.0 - chi) * fb + chi * g + 2.0 * tb.w[i] * rhow * 3.0 * cuB;
+                stS(pop + (long long)i * N + A, bc);
+                fa = bc;
+                double sum = fa + fb;
+                ps[0] = -cxi * sum;
+                ps[1] = -cyi * sum;
+                ps[2] = -czi * sum;
+                const int cb[3] = {-cxi, -cyi, -czi};
+                const int cc[3] = {cxi, cyi, czi};
+                for (int a = 0; a < 3; ++a) pm[a] = -(cc[a] - uB[a]) * fa + (cb[a] - uB[a]) * fb;
+            } else {
+                const float fbf = ldP(pop + (long long)ib * N + cell);
+                const float4 mF = reinterpret_cast<const float4 *>(mac)[cell];
+                const float uF[3] = {mF.y, mF.z, mF.w};
+                float ubf[3], chi;
+                const float dl = (float)delta;
+                if (delta < 0.5) {
+                    if (G >= 0) {
+                        const float4 mG = reinterpret_cast<const float4 *>(mac)[G];
+                        ubf[0] = mG.y;
+                        ubf[1] = mG.z;
+                        ubf[2] = mG.w;
+                        chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
+                    } else {
+                        ubf[0] = uF[0];
+                        ubf[1] = uF[1];
+                        ubf[2] = uF[2];
+                        chi = 0.0f;
+                    }
+                } else {
+                    const float k3 = 3.0f / (2.0f * dl);
+                    for (int a = 0; a < 3; ++a) ubf[a] = fmaf(k3, (float)uB[a] - uF[a], uF[a]);
+                    chi = (2.0f * dl - 1.0f) / ((float)p.tau + 0.5f);
+                }
+                const float g = dgeq_f(p, tb, ib, mF.x, ubf, uF);
+                const float rhow = p.eq == 0 ? p.rho0f : 1.0f + mF.x;
+                const float cuB = (float)(cxi * uB[0] + cyi * uB[1] + czi * uB[2]);
+                const float bc = fmaf(6.0f * (float)tb.w[i] * rhow, cuB, fmaf(chi, g - fbf, fbf));
+                stS(pop + (long long)i * N + A, bc);
+                fa = (double)roundS(pop, bc);
+                fb = (double)fbf;
+                // deviation form: the constant parts -2 w_i c_i cancel over the
+                // closed link set of a body (N_i = N_ib on every lattice line)
+                double sum = fa + fb, dif = fa - fb;
+                ps[0] = -cxi * sum;
+                ps[1] = -cyi * sum;
+                ps[2] = -czi * sum;
+                for (int a = 0; a < 3; ++a) pm[a] = ps[a] + uB[a] * dif;
+            }
+            double ts[3], tm[3];
+            cross3(d, ps, ts);
+            cross3(d, pm, tm);
+            double *o = sb.me + j * ME_PER_LINK;
+            o[0] = ps[0];
+            o[1] = ps[1];
+            o[2] = ps[2];
+            o[3] = ts[0];
+            o[4] = ts[1];
+            o[5] = ts[2];
+            o[6] = pm[0];
+            o[7] = pm[1];
+            o[8] = pm[2];
+            o[9] = tm[0];
+            o[10] = tm[1];
+            o[11] = tm[2];
+        }
+    }
+}
+
+// covered (sign +1) and uncovered (sign -1) nodes of one moving body:
+// impulsive terms and refill (one CTA per moving body)
+template <class L, class P>
+__global__ void __launch_bounds__(IMP_THREADS) k_imp(Params p, StepBufs sb) {
+    using S = typename P::S;
+    using C = typename P::C;
+    __shared__ double part[IMP_THREADS][6];
+    __shared__ int sgn[IMP_THREADS];
+    const int b = sb.moving_ids[blockIdx.x];
+    const BodyDev &B = sb.bodies[b];
+    const long long cnt = sb.apm_cnt[b];
+    const S *src = (const S *)sb.src;
+    S *dst = (S *)sb.dst;
+    const C *mac_t = (const C *)sb.mac_t;
+    C *mac_t1 = (C *)sb.mac_t1;
+    double X[3], X1[3];
+    pose(B, sb.t, X);
+    pose(B, sb.t + 1, X1);
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long base = 0; base < cnt; base += IMP_THREADS) {
+        const long long e = base + threadIdx.x;
+        if (e < cnt) {
+            const long long A = sb.apm_cell[B.apm_off + e];
+            const int s = sb.apm_sign[B.apm_off + e];
+            int x, y, z;
+            coords_of(p, A, x, y, z);
+            double m[3] = {0.0, 0.0, 0.0};
+            if (s > 0) { // covered: the streamed values f_i(A, t+1)
+                C f[L::Q];
+                pull_all<L, P>(p, (const S *)src, mac_t, x, y, z, A, f);
+                for (int i = 0; i < L::Q; ++i) {
+                    m[0] += (double)L::cx(i) * (double)f[i];
+                    m[1] += (double)L::cy(i) * (double)f[i];
+                    m[2] += (double)L::cz(i) * (double)f[i];
+                }
+                atomicAdd(&sb.counters[1], 1ull);
+            } else { // uncovered: refill f(A, t+1) = f^eq(rho_bar, u_B or u_bar)
+                double r1[3], uB[3];
+                disp(p, X1, x, y, z, r1);
+                body_velocity(B, r1, uB);
+                double sum = 0.0, us[3] = {0.0, 0.0, 0.0};
+                int nn = 0;
+                for (int i = 1; i < L::Q; ++i) {
+                    int q[3] = {x + L::cx(i), y + L::cy(i), z + L::cz(i)};
+                    const int n[3] = {p.nx, p.ny, p.nz};
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a) {
+                        if (q[a] >= 0 && q[a] < n[a]) continue;
+                        if (!p.per[a]) ok = false;
+                        else q[a] += q[a] < 0 ? n[a] : -n[a];
+                    }
+                    if (!ok) continue;
+                    const long long nb = cell_of(p, q[0], q[1], q[2]);
+                    if (sb.owner_t[nb] != 0) continue;
+                    sum += (double)mac_t[4 * nb];
+                    for (int a = 0; a < 3; ++a) us[a] += (double)mac_t[4 * nb + 1 + a];
+                    nn++;
+                }
+                C f[L::Q];
+                if constexpr (P::exact) {
+                    double rbar = nn ? sum / (double)nn : p.rho0;
+                    double uf[3];
+                    for (int a = 0; a < 3; ++a) uf[a] = (p.refill == 1 && nn) ? us[a] / (double)nn : uB[a];
+                    for (int i = 0; i < L::Q; ++i) f[i] = feq_x<L>(p, i, rbar, uf);
+                    for (int i = 0; i < L::Q; ++i) {
+                        m[0] += (double)L::cx(i) * f[i];
+                        m[1] += (double)L::cy(i) * f[i];
+                        m[2] += (double)L::cz(i) * f[i];
+                    }
+                    double rho, u[3];
+                    moments_x<L>(p, f, rho, u);
+                    mac_t1[4 * A] = rho;
+                    mac_t1[4 * A + 1] = u[0];
+                    mac_t1[4 * A + 2] = u[1];
+                    mac_t1[4 * A + 3] = u[2];
+                    collide_x<L>(p, f, rho, u);
+                } else {
+                    float drb = nn ? (float)(sum / (double)nn) : 0.0f;
+                    float uf[3];
+                    for (int a = 0; a < 3; ++a) uf[a] = (float)((p.refill == 1 && nn) ? us[a] / (double)nn : uB[a]);
+                    const float usq15 = 1.5f * (uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+                    for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, drb, uf, usq15);
+                    for (int i = 0; i < L::Q; ++i) {
+                        m[0] += (double)L::cx(i) * (double)f[i];
+                        m[1] += (double)L::cy(i) * (double)f[i];
+                        m[2] += (double)L::cz(i) * (double)f[i];
+                    }
+                    float drho, u[3];
+                    moments_f<L>(p, f, drho, u);
+                    reinterpret_cast<float4 *>(mac_t1)[A] = make_float4(drho, u[0], u[1], u[2]);
+                    collide_f<L>(p, f, drho, u);
+                }
+                for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + A, f[i]);
+                atomicAdd(&sb.counters[2], 1ull);
+            }
+            double r[3], tq[3];
+            disp(p, X, x, y, z, r);
+            cross3(r, m, tq);
+            part[threadIdx.x][0] = m[0];
+            part[threadIdx.x][1] = m[1];
+            part[threadIdx.x][2] = m[2];
+            part[threadIdx.x][3] = tq[0];
+            part[threadIdx.x][4] = tq[1];
+            part[threadIdx.x][5] = tq[2];
+            sgn[threadIdx.x] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { // list order = cell order, as in the oracle
+            const long long m_ = cnt - base < IMP_THREADS ? cnt - base : IMP_THREADS;
+            for (int e2 = 0; e2 < m_; ++e2) {
+                if (sgn[e2] > 0)
+                    for (int a = 0; a < 6; ++a) acc[a] += part[e2][a];
+                else
+                    for (int a = 0; a < 6; ++a) acc[a] -= part[e2][a];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 6; ++a) sb.imp[b * 6 + a] = acc[a];
+}
+
+// per-body sum of the link contributions into the series row of step t
+template <bool EXACT>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(Params p, StepBufs sb) {
+    const int b = blockIdx.x;
+    const BodyDev &B = sb.bodies[b];
+    const long long cnt = sb.link_cnt[b];
+    const double *me = sb.me + B.link_off * ME_PER_LINK;
+    double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
+    if constexpr (EXACT) {
+        // sequential in link order (= cell, direction order of the oracle)
+        if (threadIdx.x < ME_PER_LINK) {
+            const int k = threadIdx.x;
+            double acc = 0.0;
+            for (long long j = 0; j < cnt; ++j) acc += me[j * ME_PER_LINK + k];
+            row[k < 6 ? k : k + 6] = acc;
+        }
+    } else {
+        __shared__ double sh[ME_PER_LINK][RED_THREADS];
+        double acc[ME_PER_LINK];
+        for (int k = 0; k < ME_PER_LINK; ++k) acc[k] = 0.0;
+        for (long long j = threadIdx.x; j < cnt; j += RED_THREADS)
+            for (int k = 0; k < ME_PER_LINK; ++k) acc[k] += me[j * ME_PER_LINK + k];
+        for (int k = 0; k < ME_PER_LINK; ++k) sh[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s)
+                for (int k = 0; k < ME_PER_LINK; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x < ME_PER_LINK) {
+            const int k = threadIdx.x;
+            row[k < 6 ? k : k + 6] = sh[k][0];
+        }
+    }
+    if (threadIdx.x < 6) row[6 + threadIdx.x] = B.moving ? sb.imp[b * 6 + threadIdx.x] : 0.0;
+}
+
+} // namespace lbm

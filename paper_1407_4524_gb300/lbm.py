@@ -1,0 +1,299 @@
+"""Thin Python binding of liblbm (include/lbm.h): argument marshalling only.
+
+Every step of the lattice-Boltzmann path runs in the CUDA kernels of
+liblbm.so; this module converts a problem-description dict (see
+``workloads``) into the C descriptor, optionally routes the library's device
+allocations through PyTorch's caching allocator and enqueues on a PyTorch
+stream.  There is no CPU fallback: if the library is missing or no GPU is
+present, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+LBM_OK = 0
+ERRORS = {1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_UNSTABLE",
+          5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
+EDGE = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
+SHAPE = {"cylinder": 0, "sphere": 1}
+FT_KIND = {"static": 0, "lattice": 1, "moving": 2, "impulsive": 3}
+SERIES_ROW = 18
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class lbm_domain_desc(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("precision", C.c_int), ("equilibrium", C.c_int), ("edge", C.c_int * 6),
+        ("inlet_profile", C.c_int), ("refill", C.c_int), ("has_force", C.c_int),
+        ("device", C.c_int), ("tau", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double),
+        ("force", C.c_double * 3), ("u0", C.c_double * 3), ("series_capacity", C.c_int64),
+        ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+    ]
+
+
+class lbm_body(C.Structure):
+    _fields_ = [
+        ("shape", C.c_int), ("halfway", C.c_int), ("reserved", C.c_int * 2), ("R", C.c_double),
+        ("X0", C.c_double * 3), ("U", C.c_double * 3), ("W", C.c_double * 3), ("t0", C.c_int64),
+    ]
+
+
+class lbm_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("step", "cells", "fluid_cells", "links", "fallback_links",
+                                          "covered", "uncovered", "device_bytes", "h2d_bytes", "d2h_bytes")]
+
+
+class LbmError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise LbmError(f"liblbm.so not found at {path}; run paper_1407_4524_gb300/build.py")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.lbm_last_error.restype = C.c_char_p
+    lib.lbm_version.restype = C.c_char_p
+    lib.lbm_lattice_table.argtypes = [C.c_int, P, P, P]
+    lib.lbm_create_domain.argtypes = [C.POINTER(lbm_domain_desc), C.POINTER(C.c_void_p)]
+    lib.lbm_destroy_domain.argtypes = [P]
+    lib.lbm_set_bodies.argtypes = [P, C.POINTER(lbm_body), C.c_int]
+    lib.lbm_update_bodies.argtypes = [P, C.POINTER(lbm_body), C.c_int]
+    lib.lbm_step.argtypes = [P, C.c_int]
+    lib.lbm_get_force_torque.argtypes = [P, C.c_int64, C.c_int64, C.c_int, P]
+    lib.lbm_get_series.argtypes = [P, C.c_int64, C.c_int64, P]
+    lib.lbm_get_populations.argtypes = [P, P]
+    lib.lbm_get_solid.argtypes = [P, P]
+    lib.lbm_get_stats.argtypes = [P, C.POINTER(lbm_stats)]
+    lib.lbm_time.restype = C.c_int64
+    lib.lbm_time.argtypes = [P]
+    lib.lbm_set_stream.argtypes = [P, P]
+    lib.lbm_set_kernel_timing.argtypes = [P, C.c_int]
+    lib.lbm_kernel_time.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+    lib.lbm_launches_per_step.argtypes = [P, C.POINTER(C.c_int)]
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != LBM_OK:
+        msg = _lib.lbm_last_error().decode(errors="replace")
+        raise LbmError(f"{ERRORS.get(rc, rc)}: {msg}")
+
+
+def lbm_lattice_table(q: int):
+    """(c[Q,3], w[Q], opp[Q]) in the library's direction order; needs no GPU."""
+    lib = load()
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q)
+    opp = np.zeros(q, dtype=np.int32)
+    _check(lib.lbm_lattice_table(q, c.ctypes.data, w.ctypes.data, opp.ctypes.data))
+    return c, w, opp
+
+
+def body_struct(b: dict) -> lbm_body:
+    s = lbm_body()
+    s.shape = SHAPE[b.get("shape", "sphere")]
+    s.halfway = int(bool(b.get("halfway", False)))
+    s.R = float(b["R"])
+    X0 = tuple(b["X0"]) + (0.0,) * (3 - len(b["X0"]))
+    U = tuple(b.get("U", (0.0, 0.0, 0.0)))
+    U = U + (0.0,) * (3 - len(U))
+    W = b.get("W", (0.0, 0.0, 0.0))
+    if np.isscalar(W):
+        W = (0.0, 0.0, float(W))
+    for k in range(3):
+        s.X0[k], s.U[k], s.W[k] = float(X0[k]), float(U[k]), float(W[k])
+    s.t0 = int(b.get("t0", 0))
+    return s
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self, device: int, stream_ptr: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream_ptr = stream_ptr
+
+        def _alloc(nbytes, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                              self.stream_ptr or None))
+            except Exception:  # OOM -> the library reports LBM_ERR_OOM
+                return None
+
+        def _free(ptr, ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class Domain:
+    """One lattice-Boltzmann domain on the GPU, built from a problem dict."""
+
+    def __init__(self, spec: dict, device: int = 0, stream=None, torch_allocator: bool = True,
+                 series_capacity: int = 0):
+        lib = load()
+        self.lib = lib
+        self.spec = spec
+        q = {"D2Q9": 9, "D3Q19": 19}[spec["lattice"]]
+        n = tuple(spec["n"]) + (1,) * (3 - len(spec["n"]))
+        d = lbm_domain_desc()
+        d.lattice, d.nx, d.ny, d.nz = q, n[0], n[1], n[2]
+        d.precision = PRECISION[spec.get("precision", "fp32")]
+        d.equilibrium = {"incomp": 0, "standard": 1}[spec.get("eq", "incomp")]
+        edges = spec.get("edges", {})
+        k = 0
+        for ax in "xyz":
+            e = edges.get(ax, "periodic")
+            lo, hi = (e, e) if isinstance(e, str) else e
+            d.edge[k], d.edge[k + 1] = EDGE[lo], EDGE[hi]
+            k += 2
+        inlet = spec.get("inlet", {})
+        d.inlet_profile = 1 if inlet.get("profile", "uniform") == "parabolic" else 0
+        d.u_in = float(inlet.get("u", 0.0))
+        d.refill = {"uB": 0, "ubar": 1}[spec.get("refill", "uB")]
+        g = spec.get("force")
+        d.has_force = int(g is not None)
+        for j in range(3):
+            d.force[j] = float(g[j]) if g is not None and j < len(g) else 0.0
+        u0 = tuple(spec.get("u0", (0.0, 0.0, 0.0)))
+        for j in range(3):
+            d.u0[j] = float(u0[j]) if j < len(u0) else 0.0
+        d.tau = float(spec["tau"])
+        d.rho0 = float(spec.get("rho0", 1.0))
+        d.device = int(device)
+        d.series_capacity = int(series_capacity or spec.get("series_capacity", 0) or 0)
+        self._alloc = None
+        self.stream = stream
+        stream_ptr = 0
+        try:
+            import torch
+            if torch.cuda.is_available():
+                if stream is None:
+                    stream = torch.cuda.current_stream(device)
+                    self.stream = stream
+                stream_ptr = int(stream.cuda_stream)
+                if torch_allocator:
+                    self._alloc = _TorchAllocator(device, stream_ptr)
+        except ImportError:
+            pass
+        d.stream = C.c_void_p(stream_ptr) if stream_ptr else None
+        if self._alloc is not None:
+            d.alloc, d.free = self._alloc.alloc, self._alloc.free
+        self._desc = d
+        h = C.c_void_p()
+        _check(lib.lbm_create_domain(C.byref(d), C.byref(h)))
+        self.h = h
+        self.q, self.shape = q, n
+        self.N = n[0] * n[1] * n[2]
+        self.bodies = list(spec.get("bodies", []))
+        if self.bodies:
+            self.set_bodies(self.bodies)
+
+    # ------------------------------------------------------------ lifecycle --
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_destroy_domain(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_bodies(self, bodies):
+        arr = (lbm_body * max(len(bodies), 1))(*[body_struct(b) for b in bodies])
+        _check(self.lib.lbm_set_bodies(self.h, arr, len(bodies)))
+        self.bodies = list(bodies)
+
+    def update_bodies(self, bodies):
+        arr = (lbm_body * len(bodies))(*[body_struct(b) for b in bodies])
+        _check(self.lib.lbm_update_bodies(self.h, arr, len(bodies)))
+        self.bodies = list(bodies)
+
+    def step(self, n: int = 1):
+        _check(self.lib.lbm_step(self.h, int(n)))
+
+    @property
+    def t(self) -> int:
+        return int(self.lib.lbm_time(self.h))
+
+    # -------------------------------------------------------------- results --
+    def series(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        nb = len(self.bodies)
+        if count is None:
+            count = self.t - first
+        out = np.zeros((count, max(nb, 1), SERIES_ROW))
+        if nb and count:
+            _check(self.lib.lbm_get_series(self.h, first, count, out.ctypes.data))
+        return out[:, :nb]
+
+    def force_torque(self, kind: str = "static", first: int = 0, count: int | None = None) -> np.ndarray:
+        nb = len(self.bodies)
+        if count is None:
+            count = self.t - first
+        out = np.zeros((count, max(nb, 1), 6))
+        if nb and count:
+            _check(self.lib.lbm_get_force_torque(self.h, first, count, FT_KIND[kind], out.ctypes.data))
+        return out[:, :nb]
+
+    def populations(self) -> np.ndarray:
+        """post-collision f-hat(t) as FP64 f, shape [Q, nz, ny, nx]"""
+        out = np.empty(self.q * self.N)
+        _check(self.lib.lbm_get_populations(self.h, out.ctypes.data))
+        nx, ny, nz = self.shape
+        return out.reshape(self.q, nz, ny, nx)
+
+    def solid(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int32)
+        _check(self.lib.lbm_get_solid(self.h, out.ctypes.data))
+        nx, ny, nz = self.shape
+        return out.reshape(nz, ny, nx)
+
+    def stats(self) -> dict:
+        s = lbm_stats()
+        _check(self.lib.lbm_get_stats(self.h, C.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in lbm_stats._fields_}
+
+    # --------------------------------------------------------------- timing --
+    def set_kernel_timing(self, enable: bool):
+        _check(self.lib.lbm_set_kernel_timing(self.h, int(bool(enable))))
+
+    def kernel_time(self):
+        n = C.c_int64()
+        ms = C.c_double()
+        _check(self.lib.lbm_kernel_time(self.h, C.byref(n), C.byref(ms)))
+        return int(n.value), float(ms.value)
+
+    def launches_per_step(self) -> int:
+        v = C.c_int()
+        _check(self.lib.lbm_launches_per_step(self.h, C.byref(v)))
+        return int(v.value)

@@ -1,0 +1,123 @@
+"""GPU path vs FP64 oracle, element by element on the same seeded inputs.
+
+Cases span several CUDA blocks and ragged tails (sizes not multiples of the
+block width), both lattices, every edge kind, static / translating /
+rotating bodies (including bodies that straddle a periodic seam), both
+equilibria, both refill rules and all three precision modes.  FP64 mode must
+reproduce the oracle to the benchmark spec's tolerance (it is built to be
+bit-identical); FP32 / FP16 modes to the stated reduced-precision tolerance.
+"""
+import numpy as np
+import pytest
+
+from parity_util import TOL_FP64_FT, TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP, ft_rel_error, pop_error
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_both(oracle_mod, spec, steps):
+    from paper_1407_4524_gb300 import lbm
+    dom = lbm.Domain(spec, device=0)
+    dom.step(steps)
+    ref = oracle_mod.Oracle(spec)
+    ref.step(steps)
+    return dom, ref
+
+
+def _compare(dom, ref, pop_tol, ft_tol, kinds=("static", "lattice", "moving")):
+    solid = ref.solid()
+    assert np.array_equal(dom.solid(), solid)
+    perr = pop_error(dom.populations(), ref.fhat(), solid)
+    assert perr <= pop_tol, f"populations differ by {perr:.3e}"
+    out = {"pop": perr}
+    if ref.bodies:
+        for kind in kinds:
+            e = ft_rel_error(dom.force_torque(kind), ref.force_torque(kind))
+            assert e <= ft_tol, f"{kind} force/torque rel error {e:.3e}"
+            out[kind] = e
+    return out
+
+
+CASES_2D = {
+    "channel_cylinder": dict(
+        lattice="D2Q9", n=(61, 29), tau=0.8, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+        inlet={"profile": "parabolic", "u": 0.05}, bodies=[dict(shape="cylinder", R=6.3, X0=(15.4, 14.2))]),
+    "moving_cylinders_periodic": dict(
+        lattice="D2Q9", n=(97, 66), tau=0.6,
+        bodies=[dict(shape="cylinder", R=8.2, X0=(6.3, 20.4), U=(0.06, -0.03)),  # crosses the seam
+                dict(shape="cylinder", R=7.0, X0=(60.0, 45.0), W=0.004)]),
+    "standard_eq_walls": dict(
+        lattice="D2Q9", n=(50, 40), tau=0.7, eq="standard", u0=(0.03, 0.0),
+        edges={"x": "periodic", "y": ("wall", "wall")},
+        bodies=[dict(shape="cylinder", R=5.1, X0=(20.5, 19.3), U=(0.04, 0.0), W=-0.003)]),
+    "refill_ubar": dict(
+        lattice="D2Q9", n=(45, 41), tau=0.9, refill="ubar", u0=(0.01, 0.02),
+        bodies=[dict(shape="cylinder", R=6.6, X0=(22.2, 20.1), U=(0.07, 0.05))]),
+    "halfway_body": dict(
+        lattice="D2Q9", n=(40, 33), tau=0.66, u0=(0.03, 0.01),
+        bodies=[dict(shape="cylinder", R=5.5, X0=(19.0, 16.5), halfway=True)]),
+    "poiseuille_1col": dict(
+        lattice="D2Q9", n=(1, 64), tau=0.8, edges={"x": "periodic", "y": ("wall", "wall")}, force=(1e-6, 0.0)),
+    "no_bodies_ragged": dict(lattice="D2Q9", n=(37, 23), tau=0.55, u0=(0.02, -0.01)),
+}
+
+CASES_3D = {
+    "channel_sphere": dict(
+        lattice="D3Q19", n=(42, 26, 22), tau=0.55, edges={"x": ("inlet", "outlet")},
+        inlet={"u": 0.04}, bodies=[dict(shape="sphere", R=5.3, X0=(12.4, 13.1, 10.6))]),
+    "moving_spheres_periodic": dict(
+        lattice="D3Q19", n=(40, 34, 30), tau=0.6,
+        bodies=[dict(shape="sphere", R=6.2, X0=(9.0, 10.0, 8.0)),
+                dict(shape="sphere", R=4.7, X0=(30.0, 24.5, 2.2), U=(0.05, -0.02, 0.04), W=(0.002, 0.0, -0.003)),
+                dict(shape="sphere", R=3.9, X0=(28.0, 7.0, 20.0), U=(-0.03, 0.04, 0.01))]),
+    "walled_box_cylinder3d": dict(
+        lattice="D3Q19", n=(30, 28, 9), tau=0.7, u0=(0.02, 0.01, 0.0),
+        edges={"x": ("wall", "wall"), "y": ("wall", "wall"), "z": "periodic"},
+        bodies=[dict(shape="cylinder", R=6.0, X0=(14.3, 13.6, 0.0), W=(0.0, 0.0, 0.003))]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES_2D))
+def test_fp64_parity_2d(oracle_mod, name):
+    spec = dict(CASES_2D[name], precision="fp64")
+    dom, ref = _run_both(oracle_mod, spec, 120)
+    _compare(dom, ref, TOL_FP64_POP, TOL_FP64_FT)
+    st = dom.stats()
+    assert st["fallback_links"] == ref.fallbacks
+
+
+@pytest.mark.parametrize("name", sorted(CASES_3D))
+def test_fp64_parity_3d(oracle_mod, name):
+    spec = dict(CASES_3D[name], precision="fp64")
+    dom, ref = _run_both(oracle_mod, spec, 40)
+    _compare(dom, ref, TOL_FP64_POP, TOL_FP64_FT)
+
+
+def test_fp64_is_bit_identical(oracle_mod):
+    """The FP64 mode evaluates every formula in the oracle's operation order."""
+    spec = dict(CASES_3D["moving_spheres_periodic"], precision="fp64")
+    dom, ref = _run_both(oracle_mod, spec, 25)
+    solid = ref.solid()
+    fl = solid < 0
+    assert np.array_equal(dom.populations()[:, fl], ref.fhat()[:, fl])
+    assert np.array_equal(dom.series(), ref.series())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("name", ["channel_cylinder", "moving_cylinders_periodic"])
+def test_reduced_precision_2d(oracle_mod, name, prec):
+    spec = dict(CASES_2D[name], precision=prec)
+    dom, ref = _run_both(oracle_mod, spec, 120)
+    pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
+    ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    _compare(dom, ref, pop_tol, ft_tol)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("name", ["channel_sphere", "moving_spheres_periodic"])
+def test_reduced_precision_3d(oracle_mod, name, prec):
+    spec = dict(CASES_3D[name], precision=prec)
+    dom, ref = _run_both(oracle_mod, spec, 40)
+    pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
+    ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    _compare(dom, ref, pop_tol, ft_tol)
