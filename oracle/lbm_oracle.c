@@ -144,12 +144,18 @@ static long cell(const or_dom *o, int x, int y, int z)
 
 static int periodic(const or_dom *o, int axis) { return o->d.edge[2 * axis] == OR_PERIODIC; }
 
-/* minimum-image displacement along a periodic axis */
-static double mimg(const or_dom *o, int axis, double v)
+/* minimum-image displacement x - X along one axis: on a periodic axis the
+ * pose is first brought into [0, L), then at most one period is added or
+ * removed (both of those steps are exact) */
+static double axis_disp(const or_dom *o, int axis, double x, double X)
 {
-    if (!periodic(o, axis)) return v;
+    if (!periodic(o, axis)) return x - X;
     double L = (double)o->n[axis];
-    return v - L * floor(v / L + 0.5);
+    double Xw = X - L * floor(X / L);
+    double v = x - Xw;
+    if (v > 0.5 * L) v = v - L;
+    else if (v < -0.5 * L) v = v + L;
+    return v;
 }
 
 /* prescribed pose: X(t) = X0 + (t - t0) U */
@@ -161,9 +167,9 @@ static void pose(const or_body *b, long long t, double X[3])
 
 static void disp(const or_dom *o, const double X[3], int x, int y, int z, double r[3])
 {
-    r[0] = mimg(o, 0, (double)x - X[0]);
-    r[1] = mimg(o, 1, (double)y - X[1]);
-    r[2] = mimg(o, 2, (double)z - X[2]);
+    r[0] = axis_disp(o, 0, (double)x, X[0]);
+    r[1] = axis_disp(o, 1, (double)y, X[1]);
+    r[2] = axis_disp(o, 2, (double)z, X[2]);
 }
 
 static void cross(const double a[3], const double b[3], double out[3])
