@@ -49,9 +49,11 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _workload(name: str, precision: str):
+def _workload(name: str, precision: str, n=None, bodies=None):
     from paper_1407_4524_gb300 import workloads as W
     if name == "sphere_swarm_3d":
+        if n is not None:
+            return W.sphere_swarm_3d(precision=precision, n=n, n_bodies=bodies if bodies is not None else 64)
         return W.sphere_swarm_3d(precision=precision)
     if name == "sphere_channel_3d":
         return W.sphere_channel_3d(precision=precision)
@@ -213,7 +215,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     from paper_1407_4524_gb300 import lbm
-    spec = _workload(args.workload, args.precision)
+    spec = _workload(args.workload, args.precision, args.n, args.bodies)
     stream = torch.cuda.Stream(dev)
     dom = lbm.Domain(spec, device=dev, stream=stream, series_capacity=max(8192, args.steps + args.warmup + 16))
     cells = dom.N
@@ -340,7 +342,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--print-kernel-rev", action="store_true")
+    ap.add_argument("--n", default=None, help="override the box size, e.g. 256,256,128 (profiling cases)")
+    ap.add_argument("--bodies", type=int, default=None)
     args = ap.parse_args()
+    if args.n:
+        args.n = tuple(int(v) for v in args.n.split(","))
     if args.print_kernel_rev:
         print(_kernel_rev())
         return

@@ -104,6 +104,9 @@ struct lbm_domain {
     double *imp = nullptr;
     double *series = nullptr;
     long long series_cap = 0;
+    double *poses = nullptr;
+    long long *link_pre = nullptr;
+    bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
     // timing of the bulk kernel
@@ -163,6 +166,9 @@ void free_body_buffers(lbm_domain *D) {
     D->apm_cnt = nullptr;
     D->imp = nullptr;
     D->series = nullptr;
+    D->poses = nullptr;
+    D->link_pre = nullptr;
+    D->prep_dirty = true;
     D->nb = D->n_moving = 0;
     D->nchunk_all = D->nchunk_mov = 0;
     D->link_cap_total = D->apm_cap_total = 0;
@@ -279,6 +285,8 @@ StepBufs step_bufs(lbm_domain *D) {
     sb.moving_ids = D->dmoving;
     sb.n_moving = D->n_moving;
     sb.link_cnt = D->link_cnt[cur];
+    sb.link_pre = D->link_pre;
+    sb.poses = D->poses;
     sb.Lcell = D->Lcell[cur];
     sb.Ldir = D->Ldir[cur];
     sb.Ldelta = D->Ldelta[cur];
@@ -297,6 +305,7 @@ GeomArgs geom_args(lbm_domain *D, bool moving_step) {
     const int cur = (int)(D->t & 1), nxt = cur ^ 1;
     GeomArgs g{};
     g.bodies = D->dbodies;
+    g.poses = D->poses;
     g.chunk_map = moving_step ? D->chunk_mov : D->chunk_all;
     g.nchunks = moving_step ? D->nchunk_mov : D->nchunk_all;
     g.owner_t = D->owner[cur];
@@ -357,6 +366,10 @@ int upload_bodies(lbm_domain *D) {
 
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
+    if (D->nb && (D->n_moving || D->prep_dirty)) {
+        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->poses, D->t, D->s));
+        D->prep_dirty = false;
+    }
     if (D->n_moving) {
         GeomArgs g = geom_args(D, true);
         CK(launch_geom_a(Q, D->p, g, D->s));
@@ -553,6 +566,8 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->apm_cnt, nbx, &T))) return rc;
     if ((rc = alloc_t(D, &D->imp, nbx * 6, &T))) return rc;
     if ((rc = alloc_t(D, &D->series, (size_t)D->series_cap * nbx * SERIES_ROW, &T))) return rc;
+    if ((rc = alloc_t(D, &D->poses, nbx * POSE_STRIDE, &T))) return rc;
+    if ((rc = alloc_t(D, &D->link_pre, nbx + 1, &T))) return rc;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
     D->links_grid = (int)std::min<long long>(4 * 152, (maxcnt + LINK_THREADS - 1) / LINK_THREADS);
@@ -561,6 +576,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     // solid owners at t = 0, flags, links (both buffers), initial state
     const size_t N = (size_t)D->p.N;
     CK(cudaMemsetAsync(D->owner[0], 0, N * sizeof(uint16_t), D->s));
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->poses, 0, D->s));
     GeomArgs g = geom_args(D, false);
     CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
     CK(cudaMemcpyAsync(D->owner[1], D->owner[0], N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
@@ -572,6 +588,8 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     CK(cudaMemcpyAsync(D->Ldir[1], D->Ldir[0], L, cudaMemcpyDeviceToDevice, D->s));
     CK(cudaMemcpyAsync(D->Ldelta[1], D->Ldelta[0], L * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
     CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice, D->s));
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->poses, 0, D->s));
+    D->prep_dirty = false;
     if ((rc = init_populations(D))) return rc;
     CK(cudaStreamSynchronize(D->s));
     return LBM_OK;
@@ -618,6 +636,7 @@ int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
             CK(cudaMemcpyAsync(D->owner[nxt], D->owner[cur], (size_t)D->p.N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
         }
     }
+    D->prep_dirty = true;
     if (maps_changed) return upload_bodies(D);
     return upload_body_array(D);
 }
@@ -752,7 +771,7 @@ int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
 
 int lbm_launches_per_step(const lbm_domain *D, int *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
-    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0);
+    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 5 : 0);
     return LBM_OK;
 }
 

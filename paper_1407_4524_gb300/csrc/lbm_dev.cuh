@@ -155,21 +155,59 @@ struct BodyDev {
 // ------------------------------------------------------- FP64 geometry ------
 // These follow one fixed expression each; they are shared by all precision
 // modes so the solid set and link distances never depend on the mode.
-__device__ __forceinline__ double mimg(const Params &p, int a, double v) {
-    if (!p.per[a]) return v;
-    double L = (double)(a == 0 ? p.nx : (a == 1 ? p.ny : p.nz));
-    return v - L * floor(v / L + 0.5);
-}
-
 __device__ __forceinline__ void pose(const BodyDev &b, long long t, double X[3]) {
     double dt = (double)(t - b.t0);
     for (int k = 0; k < 3; ++k) X[k] = b.X0[k] + dt * b.U[k];
 }
 
-__device__ __forceinline__ void disp(const Params &p, const double X[3], int x, int y, int z, double r[3]) {
-    r[0] = mimg(p, 0, (double)x - X[0]);
-    r[1] = mimg(p, 1, (double)y - X[1]);
-    r[2] = mimg(p, 2, (double)z - X[2]);
+__device__ __forceinline__ int axis_len(const Params &p, int a) { return a == 0 ? p.nx : (a == 1 ? p.ny : p.nz); }
+
+// pose brought into [0, L) on periodic axes (one division per body and step)
+__device__ __forceinline__ void wrap_pose(const Params &p, const double X[3], double Xw[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (!p.per[a]) {
+            Xw[a] = X[a];
+            continue;
+        }
+        double L = (double)axis_len(p, a);
+        Xw[a] = X[a] - L * floor(X[a] / L);
+    }
+}
+
+// minimum-image displacement x - X from the wrapped pose: at most one period
+// is added or removed, exactly
+__device__ __forceinline__ double axis_disp(const Params &p, int a, double x, double Xw) {
+    double v = x - Xw;
+    if (!p.per[a]) return v;
+    double L = (double)axis_len(p, a);
+    if (v > 0.5 * L) v = v - L;
+    else if (v < -0.5 * L) v = v + L;
+    return v;
+}
+
+__device__ __forceinline__ void disp(const Params &p, const double Xw[3], int x, int y, int z, double r[3]) {
+    r[0] = axis_disp(p, 0, (double)x, Xw[0]);
+    r[1] = axis_disp(p, 1, (double)y, Xw[1]);
+    r[2] = axis_disp(p, 2, (double)z, Xw[2]);
+}
+
+// FP32 estimate of the distance of a node from a body's centre (sphere) or
+// axis (cylinder); used only to skip nodes far from the surface, with margins
+// of at least half a cell
+__device__ __forceinline__ float approx_dist(const Params &p, int shape, const double Xw[3], int x, int y, int z) {
+    const int c[3] = {x, y, z};
+    float r2 = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && shape == 0) continue;
+        float v = (float)c[a] - (float)Xw[a];
+        if (p.per[a]) {
+            float L = (float)axis_len(p, a);
+            if (v > 0.5f * L) v -= L;
+            else if (v < -0.5f * L) v += L;
+        }
+        r2 += v * v;
+    }
+    return sqrtf(r2);
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
@@ -241,19 +279,19 @@ __device__ __forceinline__ int region_axis(int k, int lo, int len, int n, int pe
     return s0 + k;
 }
 
+// per body and step: X(t), Xw(t), X(t+1), Xw(t+1) (Xw wrapped into [0, L))
+constexpr int POSE_STRIDE = 12;
+
 // region of a body covering its poses at t and t+1, dilated by `margin`
-__device__ __forceinline__ void region_lo(const Params &p, const BodyDev &b, long long t, int margin, int lo[3]) {
-    double X0[3], X1[3];
-    pose(b, t, X0);
-    pose(b, t + 1, X1);
+__device__ __forceinline__ void region_lo(const Params &p, const BodyDev &b, const double *P, int margin, int lo[3]) {
     for (int a = 0; a < 3; ++a) {
-        int n = a == 0 ? p.nx : (a == 1 ? p.ny : p.nz);
+        int n = axis_len(p, a);
         bool full = (a == 2 && b.shape == 0) || b.ext[a] >= n;
         if (full) {
             lo[a] = 0;
             continue;
         }
-        double m = X0[a] < X1[a] ? X0[a] : X1[a];
+        double m = P[a] < P[6 + a] ? P[a] : P[6 + a];
         lo[a] = (int)floor(m - b.R) - margin;
     }
 }

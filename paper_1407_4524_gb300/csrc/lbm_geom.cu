@@ -121,45 +121,96 @@ __device__ __forceinline__ uint8_t node_flags(const Params &p, const uint16_t *o
     return f | (mac ? FL_MAC : 0);
 }
 
-__global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, uint16_t *owner, long long t_pose) {
+// wrapped poses at t and t+1 and the prefix of the link counts (one block)
+__global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, const long long *link_cnt,
+                                               long long *link_pre, double *poses, long long t) {
+    __shared__ long long ws[32];
+    __shared__ long long carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < p.nb; base += 1024) {
+        const int b = base + threadIdx.x;
+        long long v = b < p.nb ? link_cnt[b] : 0;
+        long long inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        if (lane == 31) ws[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            long long s = ws[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                long long n = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += n;
+            }
+            ws[lane] = s;
+        }
+        __syncthreads();
+        const long long before = carry + (wid ? ws[wid - 1] : 0);
+        if (b < p.nb) link_pre[b] = before + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += ws[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) link_pre[p.nb] = carry;
+    for (int b = threadIdx.x; b < p.nb; b += 1024) {
+        double *P = poses + (long long)b * POSE_STRIDE;
+        pose(bodies[b], t, P);
+        wrap_pose(p, P, P + 3);
+        pose(bodies[b], t + 1, P + 6);
+        wrap_pose(p, P + 6, P + 9);
+    }
+}
+
+__global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, uint16_t *owner, long long) {
     const int2 cm = g.chunk_map[blockIdx.x];
     const BodyDev &B = g.bodies[cm.x];
+    const double *P = g.poses + (long long)cm.x * POSE_STRIDE;
     int lo[3];
-    region_lo(p, B, t_pose, REGION_MARGIN, lo);
+    region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     if (!rc.valid) return;
-    double X[3], r[3];
-    pose(B, t_pose, X);
-    disp(p, X, rc.x, rc.y, rc.z, r);
+    double r[3];
+    disp(p, P + 3, rc.x, rc.y, rc.z, r);
     if (inside(B, r)) owner[rc.cell] = (uint16_t)(cm.x + 1);
 }
 
-// moving step, part a: owner at t+1 for this body's region; count A+/A-
+// moving step, part a: owner at t+1 for this body's region; count A+/A-.
+// Only the shell R-2 <= |x - X(t+1)| <= R+2 can change owner (the surface
+// moves less than half a cell per step).
 __global__ void __launch_bounds__(GEOM_THREADS) k_geom_a(Params p, GeomArgs g) {
     const int2 cm = g.chunk_map[blockIdx.x];
     const int b = cm.x;
     const BodyDev &B = g.bodies[b];
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
     int lo[3];
-    region_lo(p, B, g.t, REGION_MARGIN, lo);
+    region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     int flag = 0;
     if (rc.valid) {
-        const uint16_t me = (uint16_t)(b + 1);
-        const bool in_t = g.owner_t[rc.cell] == me;
-        double X1[3], r[3];
-        pose(B, g.t + 1, X1);
-        disp(p, X1, rc.x, rc.y, rc.z, r);
-        const bool in1 = inside(B, r);
-        if (in1) g.owner_t1[rc.cell] = me;
-        else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
-        flag = in_t != in1;
+        const float dist = approx_dist(p, B.shape, P + 9, rc.x, rc.y, rc.z);
+        const float R = (float)B.R;
+        if (dist >= R - 2.0f && dist <= R + 2.0f) {
+            const uint16_t me = (uint16_t)(b + 1);
+            const bool in_t = g.owner_t[rc.cell] == me;
+            double r[3];
+            disp(p, P + 9, rc.x, rc.y, rc.z, r);
+            const bool in1 = inside(B, r);
+            if (in1) g.owner_t1[rc.cell] = me;
+            else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
+            flag = in_t != in1;
+        }
     }
     int total;
     block_excl_scan(flag, &total);
     if (threadIdx.x == 0) g.chunk_cnt_apm[blockIdx.x] = total;
 }
 
-// part b: A+/A- lists (moving step), node flags, link counts
+// part b: A+/A- lists (moving step), node flags, link counts.  Nodes farther
+// than R+5 from the surface pose of the links, or deeper than R-2 inside,
+// keep their flags and carry no link.
 template <class L>
 __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     const int2 cm = g.chunk_map[blockIdx.x];
@@ -167,13 +218,21 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     const BodyDev &B = g.bodies[b];
     const uint16_t me = (uint16_t)(b + 1);
     const uint16_t *owner_L = g.owner_t1; // geometry of the links being built
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
+    const double *XL = P + (g.t_link == g.t ? 3 : 9);
     int lo[3];
-    region_lo(p, B, g.t, REGION_MARGIN, lo);
+    region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y; // first chunk of this body
+    bool near = false;
+    if (rc.valid) {
+        const float dist = approx_dist(p, B.shape, XL, rc.x, rc.y, rc.z);
+        const float R = (float)B.R;
+        near = dist >= R - 2.0f && dist <= R + 5.5f;
+    }
     if (g.do_apm) {
         int flag = 0, sign = 0;
-        if (rc.valid) {
+        if (near) {
             const bool in_t = g.owner_t[rc.cell] == me, in1 = g.owner_t1[rc.cell] == me;
             flag = in_t != in1;
             sign = in1 ? 1 : -1;
@@ -194,7 +253,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
         }
     }
     int nl = 0;
-    if (rc.valid) {
+    if (near) {
         if (g.do_flags) g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
         if (owner_L[rc.cell] == 0) {
             for (int i = 1; i < L::Q; ++i) {
@@ -216,18 +275,24 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
     const BodyDev &B = g.bodies[b];
     const uint16_t me = (uint16_t)(b + 1);
     const uint16_t *owner_L = g.owner_t1;
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
+    const double *XL = P + (g.t_link == g.t ? 3 : 9);
     int lo[3];
-    region_lo(p, B, g.t, REGION_MARGIN, lo);
+    region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y;
     unsigned mask = 0;
     int nl = 0;
-    if (rc.valid && owner_L[rc.cell] == 0) {
-        for (int i = 1; i < L::Q; ++i) {
-            long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-            if (a >= 0 && owner_L[a] == me) {
-                mask |= 1u << i;
-                nl++;
+    if (rc.valid) {
+        const float dist = approx_dist(p, B.shape, XL, rc.x, rc.y, rc.z);
+        const float R = (float)B.R;
+        if (dist >= R - 2.0f && dist <= R + 5.5f && owner_L[rc.cell] == 0) {
+            for (int i = 1; i < L::Q; ++i) {
+                long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                if (a >= 0 && owner_L[a] == me) {
+                    mask |= 1u << i;
+                    nl++;
+                }
             }
         }
     }
@@ -235,9 +300,8 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
     int total;
     const int pos = block_excl_scan(nl, &total);
     if (nl) {
-        double X[3], d[3];
-        pose(B, g.t_link, X);
-        disp(p, X, rc.x, rc.y, rc.z, d);
+        double d[3];
+        disp(p, XL, rc.x, rc.y, rc.z, d);
         long long at = before + pos;
         for (int i = 1; i < L::Q; ++i) {
             if (!(mask & (1u << i))) continue;
@@ -287,6 +351,12 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
 }
 
 } // namespace
+
+cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
+                        double *poses, long long t, cudaStream_t s) {
+    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, poses, t);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_raster(int, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,
                           cudaStream_t s) {

@@ -11,6 +11,7 @@ namespace lbm {
 
 struct GeomArgs {
     const BodyDev *bodies;
+    const double *poses; // POSE_STRIDE doubles per body: X(t), Xw(t), X(t+1), Xw(t+1)
     const int2 *chunk_map; // (body, chunk within the body's region)
     int nchunks;
     const uint16_t *owner_t;
@@ -38,6 +39,10 @@ cudaError_t launch_links(int Q, int prec, const Params &p, const StepBufs &sb, i
 cudaError_t launch_bulk(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
 cudaError_t launch_imp(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
 cudaError_t launch_reduce(int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+
+// per step: wrapped poses at t and t+1 and the prefix of the link counts
+cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
+                        double *poses, long long t, cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,

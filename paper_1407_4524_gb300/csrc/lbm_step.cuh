@@ -47,6 +47,8 @@ struct StepBufs {
     const int *moving_ids;
     int n_moving;
     const long long *link_cnt; // per body, current link buffer
+    const long long *link_pre; // prefix of link_cnt over bodies (nb + 1 entries)
+    const double *poses;       // POSE_STRIDE doubles per body
     const uint32_t *Lcell;
     const uint8_t *Ldir;
     const double *Ldelta;
@@ -360,14 +362,22 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gsz = (long long)gridDim.x * blockDim.x;
     const long long N = p.N;
-    for (int b = 0; b < p.nb; ++b) {
-        const long long cnt = sb.link_cnt[b];
-        if (gtid >= cnt) continue;
+    const long long total = sb.link_pre[p.nb];
+    // one global index over the links of every body (load balanced)
+    for (long long k = gtid; k < total; k += gsz) {
+        int b = 0;
+        {
+            int hi = p.nb;
+            while (hi - b > 1) {
+                const int mid = (b + hi) >> 1;
+                if (sb.link_pre[mid] <= k) b = mid;
+                else hi = mid;
+            }
+        }
         const BodyDev &B = sb.bodies[b];
-        double X[3];
-        pose(B, sb.t, X);
-        for (long long k = gtid; k < cnt; k += gsz) {
-            const long long j = B.link_off + k;
+        const double *X = sb.poses + (long long)b * POSE_STRIDE + 3; // wrapped pose at t
+        {
+            const long long j = B.link_off + (k - sb.link_pre[b]);
             const long long cell = sb.Lcell[j];
             const int i = sb.Ldir[j];
             const double delta = sb.Ldelta[j];
@@ -506,9 +516,8 @@ __global__ void __launch_bounds__(IMP_THREADS) k_imp(Params p, StepBufs sb) {
     S *dst = (S *)sb.dst;
     const C *mac_t = (const C *)sb.mac_t;
     C *mac_t1 = (C *)sb.mac_t1;
-    double X[3], X1[3];
-    pose(B, sb.t, X);
-    pose(B, sb.t + 1, X1);
+    const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;  // wrapped pose at t
+    const double *X1 = sb.poses + (long long)b * POSE_STRIDE + 9; // wrapped pose at t+1
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long base = 0; base < cnt; base += IMP_THREADS) {
         const long long e = base + threadIdx.x;

@@ -34,3 +34,19 @@ def ft_rel_error(ft, ref):
 def pop_error(f_gpu, f_ref, solid):
     fluid = solid < 0
     return float(np.abs(f_gpu[:, fluid] - f_ref[:, fluid]).max())
+
+
+def report(key, value):
+    """append a measured error to the JSON file named by $LBM_PARITY_REPORT"""
+    import json
+    import os
+    path = os.environ.get("LBM_PARITY_REPORT")
+    if not path:
+        return
+    data = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            data = json.load(fh)
+    data[key] = value
+    with open(path, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)

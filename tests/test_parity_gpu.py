@@ -10,7 +10,7 @@ bit-identical); FP32 / FP16 modes to the stated reduced-precision tolerance.
 import numpy as np
 import pytest
 
-from parity_util import TOL_FP64_FT, TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP, ft_rel_error, pop_error
+from parity_util import TOL_FP64_FT, TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP, ft_rel_error, pop_error, report
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,13 @@ CASES_2D = {
     "poiseuille_1col": dict(
         lattice="D2Q9", n=(1, 64), tau=0.8, edges={"x": "periodic", "y": ("wall", "wall")}, force=(1e-6, 0.0)),
     "no_bodies_ragged": dict(lattice="D2Q9", n=(37, 23), tau=0.55, u0=(0.02, -0.01)),
+    "node_on_surface": dict(  # integer centre and radius: nodes exactly on the surface, Delta = 1 links
+        lattice="D2Q9", n=(40, 40), tau=0.7, u0=(0.04, 0.01),
+        bodies=[dict(shape="cylinder", R=5.0, X0=(20.0, 20.0))]),
+    "two_bodies_close": dict(  # 2-cell surface gap: fluid nodes with links to both bodies
+        lattice="D2Q9", n=(48, 36), tau=0.75, u0=(0.03, 0.0),
+        bodies=[dict(shape="cylinder", R=6.0, X0=(15.0, 18.0)),
+                dict(shape="cylinder", R=6.0, X0=(29.2, 18.4), U=(0.0, 0.03))]),
 }
 
 CASES_3D = {
@@ -70,6 +77,7 @@ CASES_3D = {
         bodies=[dict(shape="sphere", R=6.2, X0=(9.0, 10.0, 8.0)),
                 dict(shape="sphere", R=4.7, X0=(30.0, 24.5, 2.2), U=(0.05, -0.02, 0.04), W=(0.002, 0.0, -0.003)),
                 dict(shape="sphere", R=3.9, X0=(28.0, 7.0, 20.0), U=(-0.03, 0.04, 0.01))]),
+    "single_cell_box": dict(lattice="D3Q19", n=(1, 1, 1), tau=0.8, u0=(0.01, 0.02, -0.03)),
     "walled_box_cylinder3d": dict(
         lattice="D3Q19", n=(30, 28, 9), tau=0.7, u0=(0.02, 0.01, 0.0),
         edges={"x": ("wall", "wall"), "y": ("wall", "wall"), "z": "periodic"},
@@ -110,6 +118,7 @@ def test_reduced_precision_2d(oracle_mod, name, prec):
     dom, ref = _run_both(oracle_mod, spec, 120)
     pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
     ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    report(f"{name}_{prec}_120", _compare(dom, ref, 1e9, 1e9))
     _compare(dom, ref, pop_tol, ft_tol)
 
 
@@ -120,4 +129,39 @@ def test_reduced_precision_3d(oracle_mod, name, prec):
     dom, ref = _run_both(oracle_mod, spec, 40)
     pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
     ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    report(f"{name}_{prec}_40", _compare(dom, ref, 1e9, 1e9))
     _compare(dom, ref, pop_tol, ft_tol)
+
+
+def test_zero_steps_and_empty_reads(oracle_mod):
+    from paper_1407_4524_gb300 import lbm
+    spec = dict(CASES_2D["channel_cylinder"], precision="fp64")
+    dom = lbm.Domain(spec, device=0)
+    dom.step(0)
+    assert dom.t == 0
+    assert dom.force_torque("static").shape == (0, 1, 6)
+    ref = oracle_mod.Oracle(spec)
+    fl = ref.solid() < 0
+    assert np.array_equal(dom.populations()[:, fl], ref.fhat()[:, fl])
+
+
+def test_invalid_bodies_rejected():
+    from paper_1407_4524_gb300 import lbm
+    base = dict(lattice="D2Q9", n=(40, 30), tau=0.7, precision="fp32",
+                edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")})
+    bad = [
+        [dict(shape="cylinder", R=5.0, X0=(3.0, 15.0))],                      # touches the inlet face
+        [dict(shape="cylinder", R=5.0, X0=(12.0, 15.0)),
+         dict(shape="cylinder", R=5.0, X0=(22.5, 15.0))],                     # surface gap < 2
+        [dict(shape="sphere", R=4.0, X0=(20.0, 15.0))],                       # sphere on D2Q9
+        [dict(shape="cylinder", R=4.0, X0=(20.0, 15.0), U=(0.01, 0.0))],       # translating along a non-periodic axis
+    ]
+    for bodies in bad:
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+            lbm.Domain(dict(base, bodies=bodies), device=0)
+    dom = lbm.Domain(dict(base, bodies=[dict(shape="cylinder", R=4.0, X0=(20.0, 15.0))]), device=0)
+    dom.step(1)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        dom.set_bodies([dict(shape="cylinder", R=4.0, X0=(20.0, 15.0))])
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
+        dom.force_torque("static", first=0, count=5)
