@@ -245,6 +245,9 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
             if (D->p.per[a]) {
                 if (2.0 * B.R + 4.0 >= nn[a])
                     return fail(LBM_ERR_ARG, "body " + std::to_string(k) + " is too large for the periodic axis");
+                if (is_moving(B) && 2.0 * B.R + 14.0 >= nn[a])
+                    return fail(LBM_ERR_ARG, "moving body " + std::to_string(k) +
+                                                 " needs 2R + 14 cells along each periodic axis");
             } else {
                 if (B.X0[a] - B.R < 3.0 || B.X0[a] + B.R > nn[a] - 4.0)
                     return fail(LBM_ERR_ARG, "body " + std::to_string(k) +
@@ -466,6 +469,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     for (int a = 0; a < 3; ++a) p.per[a] = d.edge[2 * a] == LBM_EDGE_PERIODIC;
     for (int k = 0; k < 6; ++k) p.edge[k] = d.edge[k];
     p.nonper = !(p.per[0] && p.per[1] && p.per[2]);
+    p.exact = d.precision == LBM_FP64;
     p.eq = d.equilibrium;
     p.inlet_parabolic = d.inlet_profile == LBM_INLET_PARABOLIC;
     p.has_force = d.has_force ? 1 : 0;
@@ -546,6 +550,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     }
     D->link_cap_total = loff;
     D->apm_cap_total = aoff;
+    D->p.me_stride = std::max<long long>(loff, 1);
     auto &T = D->body_allocs;
     const size_t nbx = (size_t)std::max(n, 1);
     if ((rc = alloc_t(D, &D->dbodies, nbx, &T))) return rc;

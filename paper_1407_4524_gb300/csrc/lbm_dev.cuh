@@ -23,7 +23,7 @@ constexpr uint8_t FL_MAC = 2;   // store rho,u of f(t+1) at this node
 
 constexpr int SERIES_ROW = 18;  // Fs Ts Fi Ti Fm Tm
 constexpr int ME_PER_LINK = 12; // Fs Ts Fm Tm contributions of one link
-constexpr int GEOM_THREADS = 256;
+constexpr int GEOM_THREADS = 1024;
 constexpr int REGION_MARGIN = 4;
 
 // ---------------------------------------------------------------- lattices --
@@ -131,7 +131,9 @@ struct Params {
     int refill;
     int nb;      // bodies
     int nonper;  // 1 if any axis is non-periodic
+    int exact;   // FP64 mode: link geometry in FP64 (else FP32)
     long long series_cap;
+    long long me_stride; // ME contribution arrays are [ME_PER_LINK][me_stride]
     double tau, omega, rho0, u_in;
     double g[3];
     float omegaf, rho0f, u_inf;
@@ -191,25 +193,6 @@ __device__ __forceinline__ void disp(const Params &p, const double Xw[3], int x,
     r[2] = axis_disp(p, 2, (double)z, Xw[2]);
 }
 
-// FP32 estimate of the distance of a node from a body's centre (sphere) or
-// axis (cylinder); used only to skip nodes far from the surface, with margins
-// of at least half a cell
-__device__ __forceinline__ float approx_dist(const Params &p, int shape, const double Xw[3], int x, int y, int z) {
-    const int c[3] = {x, y, z};
-    float r2 = 0.f;
-    for (int a = 0; a < 3; ++a) {
-        if (a == 2 && shape == 0) continue;
-        float v = (float)c[a] - (float)Xw[a];
-        if (p.per[a]) {
-            float L = (float)axis_len(p, a);
-            if (v > 0.5f * L) v -= L;
-            else if (v < -0.5f * L) v += L;
-        }
-        r2 += v * v;
-    }
-    return sqrtf(r2);
-}
-
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
@@ -251,6 +234,76 @@ __device__ __forceinline__ double link_delta(const BodyDev &b, const double d[3]
     return s;
 }
 
+// FP32 link distance (reduced-precision modes): same formula as link_delta
+__device__ __forceinline__ float link_delta_f(const BodyDev &b, const float d[3], int cxi, int cyi, int czi) {
+    if (b.halfway) return 0.5f;
+    float cx = cxi, cy = cyi, cz = czi;
+    float a, bb, cc;
+    const float R = (float)b.R;
+    if (b.shape == 1) {
+        a = cx * cx + cy * cy + cz * cz;
+        bb = d[0] * cx + d[1] * cy + d[2] * cz;
+        cc = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - R * R;
+    } else {
+        a = cx * cx + cy * cy;
+        bb = d[0] * cx + d[1] * cy;
+        cc = (d[0] * d[0] + d[1] * d[1]) - R * R;
+    }
+    float disc = bb * bb - a * cc;
+    if (disc < 0.0f) disc = 0.0f;
+    float sres = cc / (bb + sqrtf(disc));
+    return fminf(fmaxf(sres, 0.0f), 1.0f);
+}
+
+// Body frame of one step for fast node classification: integer part and FP32
+// fraction of the wrapped pose.  Node displacements are k - fr with k an
+// integer (minimum image taken on k), accurate to ~1e-6 cells.
+struct Frame {
+    int xi[3];
+    float fr[3];
+    double Xw[3];
+};
+
+__device__ __forceinline__ void make_frame(const double Xw[3], Frame &f) {
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(Xw[a]);
+        f.xi[a] = (int)fl;
+        f.fr[a] = (float)(Xw[a] - fl);
+        f.Xw[a] = Xw[a];
+    }
+}
+
+__device__ __forceinline__ void frame_disp_f(const Params &p, const Frame &f, int x, int y, int z, float d[3]) {
+    const int c[3] = {x, y, z};
+    for (int a = 0; a < 3; ++a) {
+        int k = c[a] - f.xi[a];
+        if (p.per[a]) {
+            const int n = a == 0 ? p.nx : (a == 1 ? p.ny : p.nz);
+            if (2 * k > n) k -= n;
+            else if (2 * k < -n) k += n;
+        }
+        d[a] = (float)k - f.fr[a];
+    }
+}
+
+// Inside test with the exact FP64 decision: FP32 decides unless the node is
+// within a thin band around the surface, where the FP64 test of `inside`
+// (the one the oracle uses) is evaluated.
+__device__ __forceinline__ bool inside_screened(const Params &p, const BodyDev &B, const Frame &f, int x, int y,
+                                                int z) {
+    float d[3];
+    frame_disp_f(p, f, x, y, z, d);
+    float s = d[0] * d[0] + d[1] * d[1];
+    if (B.shape == 1) s += d[2] * d[2];
+    const float R2 = (float)(B.R * B.R);
+    const float band = 1e-4f * R2 + 0.05f;
+    if (s < R2 - band) return true;
+    if (s > R2 + band) return false;
+    double r[3];
+    disp(p, f.Xw, x, y, z, r);
+    return inside(B, r);
+}
+
 __device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 __device__ __forceinline__ long long cell_of(const Params &p, int x, int y, int z) {
@@ -279,8 +332,9 @@ __device__ __forceinline__ int region_axis(int k, int lo, int len, int n, int pe
     return s0 + k;
 }
 
-// per body and step: X(t), Xw(t), X(t+1), Xw(t+1) (Xw wrapped into [0, L))
-constexpr int POSE_STRIDE = 12;
+// per body and step: X(t), Xw(t), X(t+1), Xw(t+1) (Xw wrapped into [0, L)),
+// floor(Xw(t)) and Xw(t) - floor(Xw(t))
+constexpr int POSE_STRIDE = 18;
 
 // region of a body covering its poses at t and t+1, dilated by `margin`
 __device__ __forceinline__ void region_lo(const Params &p, const BodyDev &b, const double *P, int margin, int lo[3]) {

@@ -161,6 +161,10 @@ __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, 
         wrap_pose(p, P, P + 3);
         pose(bodies[b], t + 1, P + 6);
         wrap_pose(p, P + 6, P + 9);
+        for (int a = 0; a < 3; ++a) {
+            P[12 + a] = floor(P[3 + a]);
+            P[15 + a] = P[3 + a] - P[12 + a];
+        }
     }
 }
 
@@ -168,13 +172,14 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, u
     const int2 cm = g.chunk_map[blockIdx.x];
     const BodyDev &B = g.bodies[cm.x];
     const double *P = g.poses + (long long)cm.x * POSE_STRIDE;
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(P + 3, F);
+    __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     if (!rc.valid) return;
-    double r[3];
-    disp(p, P + 3, rc.x, rc.y, rc.z, r);
-    if (inside(B, r)) owner[rc.cell] = (uint16_t)(cm.x + 1);
+    if (inside_screened(p, B, F, rc.x, rc.y, rc.z)) owner[rc.cell] = (uint16_t)(cm.x + 1);
 }
 
 // moving step, part a: owner at t+1 for this body's region; count A+/A-.
@@ -185,19 +190,22 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_a(Params p, GeomArgs g) {
     const int b = cm.x;
     const BodyDev &B = g.bodies[b];
     const double *P = g.poses + (long long)b * POSE_STRIDE;
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(P + 9, F);
+    __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     int flag = 0;
     if (rc.valid) {
-        const float dist = approx_dist(p, B.shape, P + 9, rc.x, rc.y, rc.z);
+        float d[3];
+        frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
+        const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
         const float R = (float)B.R;
         if (dist >= R - 2.0f && dist <= R + 2.0f) {
             const uint16_t me = (uint16_t)(b + 1);
             const bool in_t = g.owner_t[rc.cell] == me;
-            double r[3];
-            disp(p, P + 9, rc.x, rc.y, rc.z, r);
-            const bool in1 = inside(B, r);
+            const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
             if (in1) g.owner_t1[rc.cell] = me;
             else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
             flag = in_t != in1;
@@ -220,13 +228,18 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     const uint16_t *owner_L = g.owner_t1; // geometry of the links being built
     const double *P = g.poses + (long long)b * POSE_STRIDE;
     const double *XL = P + (g.t_link == g.t ? 3 : 9);
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(XL, F);
+    __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y; // first chunk of this body
     bool near = false;
     if (rc.valid) {
-        const float dist = approx_dist(p, B.shape, XL, rc.x, rc.y, rc.z);
+        float d[3];
+        frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
+        const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
         const float R = (float)B.R;
         near = dist >= R - 2.0f && dist <= R + 5.5f;
     }
@@ -277,16 +290,21 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
     const uint16_t *owner_L = g.owner_t1;
     const double *P = g.poses + (long long)b * POSE_STRIDE;
     const double *XL = P + (g.t_link == g.t ? 3 : 9);
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(XL, F);
+    __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y;
     unsigned mask = 0;
     int nl = 0;
+    float df[3] = {0.f, 0.f, 0.f};
     if (rc.valid) {
-        const float dist = approx_dist(p, B.shape, XL, rc.x, rc.y, rc.z);
+        frame_disp_f(p, F, rc.x, rc.y, rc.z, df);
+        const float dist = sqrtf(df[0] * df[0] + df[1] * df[1] + (B.shape == 1 ? df[2] * df[2] : 0.0f));
         const float R = (float)B.R;
-        if (dist >= R - 2.0f && dist <= R + 5.5f && owner_L[rc.cell] == 0) {
+        if (dist >= R - 2.0f && dist <= R + 2.5f && owner_L[rc.cell] == 0) {
             for (int i = 1; i < L::Q; ++i) {
                 long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
                 if (a >= 0 && owner_L[a] == me) {
@@ -301,7 +319,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
     const int pos = block_excl_scan(nl, &total);
     if (nl) {
         double d[3];
-        disp(p, XL, rc.x, rc.y, rc.z, d);
+        if (p.exact) disp(p, XL, rc.x, rc.y, rc.z, d);
         long long at = before + pos;
         for (int i = 1; i < L::Q; ++i) {
             if (!(mask & (1u << i))) continue;
@@ -309,7 +327,8 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
                 const long long j = B.link_off + at;
                 g.Lcell[j] = (uint32_t)rc.cell;
                 g.Ldir[j] = (uint8_t)i;
-                g.Ldelta[j] = link_delta(B, d, L::cx(i), L::cy(i), L::cz(i));
+                g.Ldelta[j] = p.exact ? link_delta(B, d, L::cx(i), L::cy(i), L::cz(i))
+                                      : (double)link_delta_f(B, df, L::cx(i), L::cy(i), L::cz(i));
             }
             at++;
         }

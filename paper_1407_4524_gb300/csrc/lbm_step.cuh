@@ -387,12 +387,39 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
             const int ib = tb.opp[i];
             const long long A =
                 cell_of(p, wrap_axis(x - cxi, p.nx), wrap_axis(y - cyi, p.ny), wrap_axis(z - czi, p.nz));
-            double d[3], rB[3], uB[3];
-            disp(p, X, x, y, z, d);
-            rB[0] = d[0] - delta * cxi;
-            rB[1] = d[1] - delta * cyi;
-            rB[2] = d[2] - delta * czi;
-            body_velocity(B, rB, uB);
+            double d[3], uB[3];
+            if constexpr (P::exact) {
+                double rB[3];
+                disp(p, X, x, y, z, d);
+                rB[0] = d[0] - delta * cxi;
+                rB[1] = d[1] - delta * cyi;
+                rB[2] = d[2] - delta * czi;
+                body_velocity(B, rB, uB);
+            } else { // FP32 link geometry (reduced-precision modes)
+                const double *Pf = X + 9; // floor(Xw), frac(Xw)
+                const int c3[3] = {x, y, z};
+                float df[3], rb[3];
+                for (int a = 0; a < 3; ++a) {
+                    int kk = c3[a] - (int)Pf[a];
+                    if (p.per[a]) {
+                        const int n = axis_len(p, a);
+                        if (2 * kk > n) kk -= n;
+                        else if (2 * kk < -n) kk += n;
+                    }
+                    df[a] = (float)kk - (float)Pf[3 + a];
+                }
+                const float dl = (float)delta;
+                rb[0] = df[0] - dl * cxi;
+                rb[1] = df[1] - dl * cyi;
+                rb[2] = df[2] - dl * czi;
+                const float W0 = (float)B.W[0], W1 = (float)B.W[1], W2 = (float)B.W[2];
+                uB[0] = (float)B.U[0] + (W1 * rb[2] - W2 * rb[1]);
+                uB[1] = (float)B.U[1] + (W2 * rb[0] - W0 * rb[2]);
+                uB[2] = (float)B.U[2] + (W0 * rb[1] - W1 * rb[0]);
+                d[0] = df[0];
+                d[1] = df[1];
+                d[2] = df[2];
+            }
             // u_G = u(x_F + c_i, t) for Delta < 1/2 (Sec. 2.1)
             long long G = -1;
             if (delta < 0.5) {
@@ -474,29 +501,46 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
                 fa = (double)roundS(pop, bc);
                 fb = (double)fbf;
                 // deviation form: the constant parts -2 w_i c_i cancel over the
-                // closed link set of a body (N_i = N_ib on every lattice line)
-                double sum = fa + fb, dif = fa - fb;
-                ps[0] = -cxi * sum;
-                ps[1] = -cyi * sum;
-                ps[2] = -czi * sum;
-                for (int a = 0; a < 3; ++a) pm[a] = ps[a] + uB[a] * dif;
+                // closed link set of a body (N_i = N_ib on every lattice line);
+                // per-link products in FP32, the per-body sums in FP64
+                const float sum = (float)fa + fbf, dif = (float)fa - fbf;
+                const float d0 = (float)d[0], d1 = (float)d[1], d2 = (float)d[2];
+                const float s0 = -cxi * sum, s1 = -cyi * sum, s2 = -czi * sum;
+                const float m0 = fmaf((float)uB[0], dif, s0), m1 = fmaf((float)uB[1], dif, s1),
+                            m2 = fmaf((float)uB[2], dif, s2);
+                const long long st = p.me_stride;
+                double *o = sb.me + j;
+                o[0 * st] = s0;
+                o[1 * st] = s1;
+                o[2 * st] = s2;
+                o[3 * st] = d1 * s2 - d2 * s1;
+                o[4 * st] = d2 * s0 - d0 * s2;
+                o[5 * st] = d0 * s1 - d1 * s0;
+                o[6 * st] = m0;
+                o[7 * st] = m1;
+                o[8 * st] = m2;
+                o[9 * st] = d1 * m2 - d2 * m1;
+                o[10 * st] = d2 * m0 - d0 * m2;
+                o[11 * st] = d0 * m1 - d1 * m0;
+                continue;
             }
             double ts[3], tm[3];
             cross3(d, ps, ts);
             cross3(d, pm, tm);
-            double *o = sb.me + j * ME_PER_LINK;
-            o[0] = ps[0];
-            o[1] = ps[1];
-            o[2] = ps[2];
-            o[3] = ts[0];
-            o[4] = ts[1];
-            o[5] = ts[2];
-            o[6] = pm[0];
-            o[7] = pm[1];
-            o[8] = pm[2];
-            o[9] = tm[0];
-            o[10] = tm[1];
-            o[11] = tm[2];
+            const long long st = p.me_stride;
+            double *o = sb.me + j;
+            o[0 * st] = ps[0];
+            o[1 * st] = ps[1];
+            o[2 * st] = ps[2];
+            o[3 * st] = ts[0];
+            o[4 * st] = ts[1];
+            o[5 * st] = ts[2];
+            o[6 * st] = pm[0];
+            o[7 * st] = pm[1];
+            o[8 * st] = pm[2];
+            o[9 * st] = tm[0];
+            o[10 * st] = tm[1];
+            o[11 * st] = tm[2];
         }
     }
 }
@@ -628,14 +672,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Params p, StepBufs sb) {
     const int b = blockIdx.x;
     const BodyDev &B = sb.bodies[b];
     const long long cnt = sb.link_cnt[b];
-    const double *me = sb.me + B.link_off * ME_PER_LINK;
+    const double *me = sb.me + B.link_off;
+    const long long st = p.me_stride;
     double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
     if constexpr (EXACT) {
         // sequential in link order (= cell, direction order of the oracle)
         if (threadIdx.x < ME_PER_LINK) {
             const int k = threadIdx.x;
+            const double *mk = me + k * st;
             double acc = 0.0;
-            for (long long j = 0; j < cnt; ++j) acc += me[j * ME_PER_LINK + k];
+            for (long long j = 0; j < cnt; ++j) acc += mk[j];
             row[k < 6 ? k : k + 6] = acc;
         }
     } else {
@@ -643,7 +689,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Params p, StepBufs sb) {
         double acc[ME_PER_LINK];
         for (int k = 0; k < ME_PER_LINK; ++k) acc[k] = 0.0;
         for (long long j = threadIdx.x; j < cnt; j += RED_THREADS)
-            for (int k = 0; k < ME_PER_LINK; ++k) acc[k] += me[j * ME_PER_LINK + k];
+            for (int k = 0; k < ME_PER_LINK; ++k) acc[k] += me[k * st + j];
         for (int k = 0; k < ME_PER_LINK; ++k) sh[k][threadIdx.x] = acc[k];
         __syncthreads();
         for (int s = RED_THREADS / 2; s > 0; s >>= 1) {

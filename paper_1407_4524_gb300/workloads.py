@@ -63,11 +63,12 @@ def moving_cylinders_2d(precision: str = "fp32") -> dict:
 
 def sphere_channel_3d(precision: str = "fp32") -> dict:
     """D3Q19 channel 256x128x128, tau 0.55, uniform inflow 0.04, zero-gradient
-    outflow, periodic cross-section, static sphere R=12 at (64,64,64)."""
+    outflow, periodic cross-section, static sphere R=12 at (64,64,64); the
+    fluid starts as the uniform inflow stream (impulsive start)."""
     return dict(
         name="sphere_channel_3d", lattice="D3Q19", n=(256, 128, 128), tau=0.55,
         edges={"x": ("inlet", "outlet"), "y": "periodic", "z": "periodic"},
-        inlet={"profile": "uniform", "u": 0.04},
+        inlet={"profile": "uniform", "u": 0.04}, u0=(0.04, 0.0, 0.0),
         bodies=[dict(shape="sphere", R=12.0, X0=(64.0, 64.0, 64.0))],
         precision=precision, steps=10000,
     )

@@ -50,7 +50,7 @@ def test_channel_cylinder_full_5000_steps_fp64(oracle_mod):
     assert np.array_equal(dom.populations()[:, fl], ref.fhat()[:, fl])
     s_gpu, s_ref = dom.series(), ref.series()
     assert np.array_equal(s_gpu, s_ref)
-    e = ft_rel_error(dom.force_torque("static"), ref.force_torque("static"))
+    e = ft_rel_error(dom.force_torque("static"), ref.force_torque("static"), spec)
     assert e <= TOL_FP64_FT
     drag = s_ref[-1, 0, 0]
     _report("channel_cylinder_2d_fp64_5000", {"bitwise": True, "ft_rel": e, "drag_final": float(drag),
@@ -67,7 +67,7 @@ def test_moving_cylinders_full_size(oracle_mod, prec):
     solid, fhat, ft, series = _oracle_run(oracle_mod, spec, steps)
     assert np.array_equal(dom.solid(), solid)
     perr = pop_error(dom.populations(), fhat, solid)
-    errs = {k: ft_rel_error(dom.force_torque(k), ft[k]) for k in ("static", "lattice", "moving")}
+    errs = {k: ft_rel_error(dom.force_torque(k), ft[k], spec) for k in ("static", "lattice", "moving")}
     _report(f"moving_cylinders_2d_{prec}_300", {"pop_abs": perr, **errs})
     if prec == "fp64":
         assert np.array_equal(dom.series(), series)
@@ -88,7 +88,7 @@ def test_sphere_channel_full_size(oracle_mod, prec):
     solid, fhat, ft, series = _oracle_run(oracle_mod, spec, steps)
     assert np.array_equal(dom.solid(), solid)
     perr = pop_error(dom.populations(), fhat, solid)
-    e = ft_rel_error(dom.force_torque("static"), ft["static"])
+    e = ft_rel_error(dom.force_torque("static"), ft["static"], spec)
     _report(f"sphere_channel_3d_{prec}_3", {"pop_abs": perr, "static": e})
     if prec == "fp64":
         assert np.array_equal(dom.series(), series)
@@ -144,7 +144,7 @@ def test_sphere_swarm_full_size_sampled(oracle_mod):
         for kind in ("static", "lattice", "moving"):
             g = dom.force_torque(kind)[:, i:i + 1]
             r = ref.force_torque(kind)
-            errs[kind] = ft_rel_error(g, r)
+            errs[kind] = ft_rel_error(g, r, spec, bodies=[i])
         out[str(i)] = errs
         assert max(errs.values()) <= TOL_RED_FT, (i, errs)
     _report("sphere_swarm_3d_fp32_sampled_4", out)

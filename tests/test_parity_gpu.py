@@ -24,7 +24,7 @@ def _run_both(oracle_mod, spec, steps):
     return dom, ref
 
 
-def _compare(dom, ref, pop_tol, ft_tol, kinds=("static", "lattice", "moving")):
+def _compare(dom, ref, pop_tol, ft_tol, kinds=("static", "lattice", "moving"), spec=None):
     solid = ref.solid()
     assert np.array_equal(dom.solid(), solid)
     perr = pop_error(dom.populations(), ref.fhat(), solid)
@@ -32,7 +32,7 @@ def _compare(dom, ref, pop_tol, ft_tol, kinds=("static", "lattice", "moving")):
     out = {"pop": perr}
     if ref.bodies:
         for kind in kinds:
-            e = ft_rel_error(dom.force_torque(kind), ref.force_torque(kind))
+            e = ft_rel_error(dom.force_torque(kind), ref.force_torque(kind), spec=spec or dom.spec)
             assert e <= ft_tol, f"{kind} force/torque rel error {e:.3e}"
             out[kind] = e
     return out
