@@ -5,10 +5,10 @@
 // arrays (solid owner at t and t+1), two cut-link buffers (t and t+1), the
 // per-link momentum-exchange contributions, the covered/uncovered lists and
 // the force/torque ring.  lbm_step enqueues, per step:
-//   moving bodies only: k_geom_a, k_geom_b, k_geom_c  (geometry of t+1)
+//   moving bodies only: k_prep (poses, link prefixes),
+//                       k_geom_a, k_geom_b, k_geom_c  (geometry of t+1)
 //   k_links (wall values + ME per link), k_bulk (stream-collide),
-//   moving bodies only: k_imp (A+/A- impulsive terms, refill),
-//   k_reduce (per-body series row).
+//   k_finish (per-body series row; A+/A- impulsive terms and refill).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -24,12 +24,12 @@ cudaError_t launch_init_p0(int Q, const Params &p, void *dst, void *mac, const u
                            cudaStream_t s);
 cudaError_t launch_links_p0(int Q, const Params &p, const StepBufs &sb, int grid, cudaStream_t s);
 cudaError_t launch_bulk_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s);
-cudaError_t launch_imp_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_finish_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s);
 cudaError_t launch_init_p12(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
                             const double u0[3], cudaStream_t s);
 cudaError_t launch_links_p12(int Q, int prec, const Params &p, const StepBufs &sb, int grid, cudaStream_t s);
 cudaError_t launch_bulk_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
-cudaError_t launch_imp_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_finish_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
 
 cudaError_t launch_init(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
                         const double u0[3], cudaStream_t s) {
@@ -41,8 +41,8 @@ cudaError_t launch_links(int Q, int prec, const Params &p, const StepBufs &sb, i
 cudaError_t launch_bulk(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
     return prec == 0 ? launch_bulk_p0(Q, p, sb, s) : launch_bulk_p12(Q, prec, p, sb, s);
 }
-cudaError_t launch_imp(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
-    return prec == 0 ? launch_imp_p0(Q, p, sb, s) : launch_imp_p12(Q, prec, p, sb, s);
+cudaError_t launch_finish(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    return prec == 0 ? launch_finish_p0(Q, p, sb, s) : launch_finish_p12(Q, prec, p, sb, s);
 }
 } // namespace lbm
 
@@ -101,11 +101,12 @@ struct lbm_domain {
     int8_t *apm_sign = nullptr;
     long long *apm_cnt = nullptr;
     long long apm_cap_total = 0;
-    double *imp = nullptr;
     double *series = nullptr;
     long long series_cap = 0;
     double *poses = nullptr;
     long long *link_pre = nullptr;
+    long long *tile_pre = nullptr;
+    double *tile_part = nullptr;
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -164,10 +165,11 @@ void free_body_buffers(lbm_domain *D) {
     D->apm_cell = nullptr;
     D->apm_sign = nullptr;
     D->apm_cnt = nullptr;
-    D->imp = nullptr;
     D->series = nullptr;
     D->poses = nullptr;
     D->link_pre = nullptr;
+    D->tile_pre = nullptr;
+    D->tile_part = nullptr;
     D->prep_dirty = true;
     D->nb = D->n_moving = 0;
     D->nchunk_all = D->nchunk_mov = 0;
@@ -289,6 +291,8 @@ StepBufs step_bufs(lbm_domain *D) {
     sb.n_moving = D->n_moving;
     sb.link_cnt = D->link_cnt[cur];
     sb.link_pre = D->link_pre;
+    sb.tile_pre = D->tile_pre;
+    sb.tile_part = D->tile_part;
     sb.poses = D->poses;
     sb.Lcell = D->Lcell[cur];
     sb.Ldir = D->Ldir[cur];
@@ -297,7 +301,6 @@ StepBufs step_bufs(lbm_domain *D) {
     sb.apm_cnt = D->apm_cnt;
     sb.apm_cell = D->apm_cell;
     sb.apm_sign = D->apm_sign;
-    sb.imp = D->imp;
     sb.series = D->series;
     sb.counters = D->counters;
     sb.t = D->t;
@@ -370,7 +373,7 @@ int upload_bodies(lbm_domain *D) {
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     if (D->nb && (D->n_moving || D->prep_dirty)) {
-        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->poses, D->t, D->s));
+        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t, D->s));
         D->prep_dirty = false;
     }
     if (D->n_moving) {
@@ -396,8 +399,7 @@ int do_step(lbm_domain *D) {
         CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
         D->ev_used += 2;
     }
-    if (D->n_moving) CK(launch_imp(Q, prec, D->p, sb, D->s));
-    if (D->nb) CK(launch_reduce(prec, D->p, sb, D->s));
+    if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
     D->t += 1;
     return LBM_OK;
 }
@@ -550,6 +552,8 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     }
     D->link_cap_total = loff;
     D->apm_cap_total = aoff;
+    long long tiles_cap = 0;
+    for (int b = 0; b < n; ++b) tiles_cap += (D->hbd[b].link_cap + LINK_THREADS - 1) / LINK_THREADS;
     D->p.me_stride = std::max<long long>(loff, 1);
     auto &T = D->body_allocs;
     const size_t nbx = (size_t)std::max(n, 1);
@@ -569,19 +573,21 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->apm_cell, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_sign, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_cnt, nbx, &T))) return rc;
-    if ((rc = alloc_t(D, &D->imp, nbx * 6, &T))) return rc;
     if ((rc = alloc_t(D, &D->series, (size_t)D->series_cap * nbx * SERIES_ROW, &T))) return rc;
     if ((rc = alloc_t(D, &D->poses, nbx * POSE_STRIDE, &T))) return rc;
     if ((rc = alloc_t(D, &D->link_pre, nbx + 1, &T))) return rc;
+    if ((rc = alloc_t(D, &D->tile_pre, nbx + 1, &T))) return rc;
+    if ((rc = alloc_t(D, &D->tile_part, (size_t)(tiles_cap + 1) * ME_PER_LINK, &T))) return rc;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
-    D->links_grid = (int)std::min<long long>(4 * 152, (maxcnt + LINK_THREADS - 1) / LINK_THREADS);
+    (void)maxcnt;
+    D->links_grid = (int)std::max<long long>(1, std::min<long long>(4 * 152, tiles_cap));
     if ((rc = upload_bodies(D))) return rc;
 
     // solid owners at t = 0, flags, links (both buffers), initial state
     const size_t N = (size_t)D->p.N;
     CK(cudaMemsetAsync(D->owner[0], 0, N * sizeof(uint16_t), D->s));
-    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->poses, 0, D->s));
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, D->s));
     GeomArgs g = geom_args(D, false);
     CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
     CK(cudaMemcpyAsync(D->owner[1], D->owner[0], N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
@@ -593,7 +599,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     CK(cudaMemcpyAsync(D->Ldir[1], D->Ldir[0], L, cudaMemcpyDeviceToDevice, D->s));
     CK(cudaMemcpyAsync(D->Ldelta[1], D->Ldelta[0], L * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
     CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice, D->s));
-    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->poses, 0, D->s));
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, D->s));
     D->prep_dirty = false;
     if ((rc = init_populations(D))) return rc;
     CK(cudaStreamSynchronize(D->s));
@@ -776,7 +782,7 @@ int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
 
 int lbm_launches_per_step(const lbm_domain *D, int *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
-    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 5 : 0);
+    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0);
     return LBM_OK;
 }
 

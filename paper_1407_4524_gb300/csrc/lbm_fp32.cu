@@ -18,9 +18,9 @@ cudaError_t launch_bulk_p12(int Q, int prec, const Params &p, const StepBufs &sb
     if (prec == 1) return Q == 9 ? bulk_t<Lat<9>, PF32>(p, sb, s) : bulk_t<Lat<19>, PF32>(p, sb, s);
     return Q == 9 ? bulk_t<Lat<9>, PF16>(p, sb, s) : bulk_t<Lat<19>, PF16>(p, sb, s);
 }
-cudaError_t launch_imp_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
-    if (prec == 1) return Q == 9 ? imp_t<Lat<9>, PF32>(p, sb, s) : imp_t<Lat<19>, PF32>(p, sb, s);
-    return Q == 9 ? imp_t<Lat<9>, PF16>(p, sb, s) : imp_t<Lat<19>, PF16>(p, sb, s);
+cudaError_t launch_finish_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    if (prec == 1) return Q == 9 ? finish_t<Lat<9>, PF32>(p, sb, s) : finish_t<Lat<19>, PF32>(p, sb, s);
+    return Q == 9 ? finish_t<Lat<9>, PF16>(p, sb, s) : finish_t<Lat<19>, PF16>(p, sb, s);
 }
 
 } // namespace lbm

@@ -14,15 +14,8 @@ cudaError_t launch_links_p0(int Q, const Params &p, const StepBufs &sb, int grid
 cudaError_t launch_bulk_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s) {
     return Q == 9 ? bulk_t<Lat<9>, PF64>(p, sb, s) : bulk_t<Lat<19>, PF64>(p, sb, s);
 }
-cudaError_t launch_imp_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s) {
-    return Q == 9 ? imp_t<Lat<9>, PF64>(p, sb, s) : imp_t<Lat<19>, PF64>(p, sb, s);
-}
-
-cudaError_t launch_reduce(int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
-    if (p.nb == 0) return cudaSuccess;
-    if (prec == 0) k_reduce<true><<<p.nb, RED_THREADS, 0, s>>>(p, sb);
-    else k_reduce<false><<<p.nb, RED_THREADS, 0, s>>>(p, sb);
-    return cudaGetLastError();
+cudaError_t launch_finish_p0(int Q, const Params &p, const StepBufs &sb, cudaStream_t s) {
+    return Q == 9 ? finish_t<Lat<9>, PF64>(p, sb, s) : finish_t<Lat<19>, PF64>(p, sb, s);
 }
 
 } // namespace lbm

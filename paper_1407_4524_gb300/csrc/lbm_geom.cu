@@ -68,14 +68,16 @@ struct RegionCell {
 
 __device__ __forceinline__ RegionCell region_cell(const Params &p, const BodyDev &B, const int lo[3], int chunk) {
     RegionCell rc{false, 0, 0, 0, 0};
-    const long long vol = (long long)B.ext[0] * B.ext[1] * B.ext[2];
-    const long long k = (long long)chunk * GEOM_THREADS + threadIdx.x;
+    const int e0 = B.ext[0], e1 = B.ext[1];
+    const int vol = e0 * e1 * B.ext[2];
+    const int k = chunk * GEOM_THREADS + (int)threadIdx.x;
     if (k >= vol) return rc;
-    const int kx = (int)(k % B.ext[0]);
-    const int ky = (int)((k / B.ext[0]) % B.ext[1]);
-    const int kz = (int)(k / ((long long)B.ext[0] * B.ext[1]));
-    rc.x = region_axis(kx, lo[0], B.ext[0], p.nx, p.per[0]);
-    rc.y = region_axis(ky, lo[1], B.ext[1], p.ny, p.per[1]);
+    const int kz = k / (e0 * e1);
+    const int rem = k - kz * e0 * e1;
+    const int ky = rem / e0;
+    const int kx = rem - ky * e0;
+    rc.x = region_axis(kx, lo[0], e0, p.nx, p.per[0]);
+    rc.y = region_axis(ky, lo[1], e1, p.ny, p.per[1]);
     rc.z = region_axis(kz, lo[2], B.ext[2], p.nz, p.per[2]);
     if (rc.x < 0 || rc.y < 0 || rc.z < 0) return rc;
     rc.valid = true;
@@ -107,23 +109,24 @@ __device__ __forceinline__ bool edge_node(const Params &p, int x, int y, int z) 
 template <class L>
 __device__ __forceinline__ uint8_t node_flags(const Params &p, const uint16_t *owner_t, const uint16_t *owner_m,
                                               int x, int y, int z, long long cell) {
-    uint8_t f = owner_t[cell] ? FL_SOLID : 0;
-    bool mac = edge_node(p, x, y, z);
-    if (!mac && owner_m[cell] == 0) {
-        for (int i = 1; i < L::Q && !mac; ++i) {
-            long long a = nbr<L>(p, x, y, z, i, 1);
-            if (a >= 0 && owner_m[a]) mac = true;
-            long long b = nbr<L>(p, x, y, z, i, 2);
-            if (b >= 0 && owner_m[b]) mac = true;
-        }
+    const uint8_t f = owner_t[cell] ? FL_SOLID : 0;
+    if (owner_m[cell]) return f;
+    if (edge_node(p, x, y, z)) return f | FL_MAC;
+    // all neighbour loads are independent (no early exit), so they overlap
+    unsigned any = 0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const long long a = nbr<L>(p, x, y, z, i, 1);
+        const long long b = nbr<L>(p, x, y, z, i, 2);
+        any |= (a >= 0 ? owner_m[a] : 0u) | (b >= 0 ? owner_m[b] : 0u);
     }
-    if (owner_m[cell]) mac = false;
-    return f | (mac ? FL_MAC : 0);
+    return f | (any ? FL_MAC : 0);
 }
 
-// wrapped poses at t and t+1 and the prefix of the link counts (one block)
-__global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, const long long *link_cnt,
-                                               long long *link_pre, double *poses, long long t) {
+// exclusive prefix over bodies of v(b) = link_cnt[b] (tiles = 0) or of the
+// number of LINK_THREADS-link tiles of each body (tiles = 1); one block of
+// 1024 threads, out has nb + 1 entries
+__device__ void prefix_over_bodies(const Params &p, const long long *link_cnt, long long *out, int tiles) {
     __shared__ long long ws[32];
     __shared__ long long carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -132,6 +135,7 @@ __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, 
     for (int base = 0; base < p.nb; base += 1024) {
         const int b = base + threadIdx.x;
         long long v = b < p.nb ? link_cnt[b] : 0;
+        if (tiles) v = (v + LINK_THREADS - 1) / LINK_THREADS;
         long long inc = v;
         for (int o = 1; o < 32; o <<= 1) {
             long long n = __shfl_up_sync(0xffffffffu, inc, o);
@@ -149,12 +153,20 @@ __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, 
         }
         __syncthreads();
         const long long before = carry + (wid ? ws[wid - 1] : 0);
-        if (b < p.nb) link_pre[b] = before + inc - v;
+        if (b < p.nb) out[b] = before + inc - v;
         __syncthreads();
         if (threadIdx.x == 0) carry += ws[31];
         __syncthreads();
     }
-    if (threadIdx.x == 0) link_pre[p.nb] = carry;
+    if (threadIdx.x == 0) out[p.nb] = carry;
+    __syncthreads();
+}
+
+// wrapped poses at t and t+1, prefixes of link counts and link tiles
+__global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, const long long *link_cnt,
+                                               long long *link_pre, long long *tile_pre, double *poses, long long t) {
+    prefix_over_bodies(p, link_cnt, link_pre, 0);
+    prefix_over_bodies(p, link_cnt, tile_pre, 1);
     for (int b = threadIdx.x; b < p.nb; b += 1024) {
         double *P = poses + (long long)b * POSE_STRIDE;
         pose(bodies[b], t, P);
@@ -269,9 +281,10 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     if (near) {
         if (g.do_flags) g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
         if (owner_L[rc.cell] == 0) {
+#pragma unroll
             for (int i = 1; i < L::Q; ++i) {
-                long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                if (a >= 0 && owner_L[a] == me) nl++;
+                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                nl += (a >= 0 ? owner_L[a] : (uint16_t)0) == me;
             }
         }
     }
@@ -305,13 +318,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
         const float dist = sqrtf(df[0] * df[0] + df[1] * df[1] + (B.shape == 1 ? df[2] * df[2] : 0.0f));
         const float R = (float)B.R;
         if (dist >= R - 2.0f && dist <= R + 2.5f && owner_L[rc.cell] == 0) {
+#pragma unroll
             for (int i = 1; i < L::Q; ++i) {
-                long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                if (a >= 0 && owner_L[a] == me) {
-                    mask |= 1u << i;
-                    nl++;
-                }
+                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                if ((a >= 0 ? owner_L[a] : (uint16_t)0) == me) mask |= 1u << i;
             }
+            nl = __popc(mask);
         }
     }
     const long long before = block_sum_range(g.chunk_cnt_link, first, cm.y);
@@ -372,8 +384,8 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
 } // namespace
 
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
-                        double *poses, long long t, cudaStream_t s) {
-    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, poses, t);
+                        long long *tile_pre, double *poses, long long t, cudaStream_t s) {
+    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, tile_pre, poses, t);
     return cudaGetLastError();
 }
 

@@ -37,12 +37,11 @@ cudaError_t launch_init(int Q, int prec, const Params &p, void *dst, void *mac, 
                         const double u0[3], cudaStream_t s);
 cudaError_t launch_links(int Q, int prec, const Params &p, const StepBufs &sb, int grid, cudaStream_t s);
 cudaError_t launch_bulk(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
-cudaError_t launch_imp(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
-cudaError_t launch_reduce(int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_finish(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
 
 // per step: wrapped poses at t and t+1 and the prefix of the link counts
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
-                        double *poses, long long t, cudaStream_t s);
+                        long long *tile_pre, double *poses, long long t, cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,

@@ -37,9 +37,10 @@ template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &
     return cudaGetLastError();
 }
 
-template <class L, class P> cudaError_t imp_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
-    if (sb.n_moving == 0) return cudaSuccess;
-    k_imp<L, P><<<sb.n_moving, IMP_THREADS, 0, s>>>(p, sb);
+template <class L, class P> cudaError_t finish_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
+    const int grid = p.nb + sb.n_moving;
+    if (grid == 0) return cudaSuccess;
+    k_finish<L, P><<<grid, IMP_THREADS, 0, s>>>(p, sb);
     return cudaGetLastError();
 }
 

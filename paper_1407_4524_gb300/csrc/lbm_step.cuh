@@ -33,7 +33,6 @@ namespace lbm {
 
 constexpr int BULK_THREADS = 128;
 constexpr int LINK_THREADS = 256;
-constexpr int RED_THREADS = 256;
 constexpr int IMP_THREADS = 128;
 
 struct StepBufs {
@@ -48,6 +47,8 @@ struct StepBufs {
     int n_moving;
     const long long *link_cnt; // per body, current link buffer
     const long long *link_pre; // prefix of link_cnt over bodies (nb + 1 entries)
+    const long long *tile_pre; // prefix of per-body link tiles (LINK_THREADS links each)
+    double *tile_part;         // per tile: ME_PER_LINK partial sums (reduced-precision modes)
     const double *poses;       // POSE_STRIDE doubles per body
     const uint32_t *Lcell;
     const uint8_t *Ldir;
@@ -349,198 +350,241 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename 
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
 }
 
-// wall values on cut links + per-link momentum-exchange contributions
+// Work of one cut link j of body b: the wall value fhat_i(x_A, t) of Eq.
+// Fillipova_interpolation is stored in slot i of the solid node x_A (so the
+// pull of k_bulk reads it), and the link's momentum-exchange contributions
+// are returned in out[12]: static force, static torque (Eqs. flow_force_2,
+// flow_torque_2), moving-frame force and torque (Eqs.
+// ForceInMovementMovingFrame / TorqueInMovementMovingFrame); by Eq.
+// Equalities they need exactly the wall value and fhat_ib(x_F, t).
 template <class L, class P>
-__global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
+__device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, const LatTab &tb,
+                                          const BodyDev &B, const double *X, long long j, double out[ME_PER_LINK]) {
     using S = typename P::S;
     using C = typename P::C;
+    S *pop = (S *)sb.src;
+    const C *mac = (const C *)sb.mac_t;
+    const long long N = p.N;
+    const long long cell = sb.Lcell[j];
+    const int i = sb.Ldir[j];
+    const double delta = sb.Ldelta[j];
+    int x, y, z;
+    coords_of(p, cell, x, y, z);
+    const int cxi = tb.c[i][0], cyi = tb.c[i][1], czi = tb.c[i][2];
+    const int ib = tb.opp[i];
+    const long long A =
+        cell_of(p, wrap_axis(x - cxi, p.nx), wrap_axis(y - cyi, p.ny), wrap_axis(z - czi, p.nz));
+    double d[3], uB[3];
+    if constexpr (P::exact) {
+        double rB[3];
+        disp(p, X, x, y, z, d);
+        rB[0] = d[0] - delta * cxi;
+        rB[1] = d[1] - delta * cyi;
+        rB[2] = d[2] - delta * czi;
+        body_velocity(B, rB, uB);
+    } else { // FP32 link geometry (reduced-precision modes)
+        const double *Pf = X + 9; // floor(Xw), frac(Xw)
+        const int c3[3] = {x, y, z};
+        float df[3], rb[3];
+        for (int a = 0; a < 3; ++a) {
+            int kk = c3[a] - (int)Pf[a];
+            if (p.per[a]) {
+                const int n = axis_len(p, a);
+                if (2 * kk > n) kk -= n;
+                else if (2 * kk < -n) kk += n;
+            }
+            df[a] = (float)kk - (float)Pf[3 + a];
+        }
+        const float dl = (float)delta;
+        rb[0] = df[0] - dl * cxi;
+        rb[1] = df[1] - dl * cyi;
+        rb[2] = df[2] - dl * czi;
+        const float W0 = (float)B.W[0], W1 = (float)B.W[1], W2 = (float)B.W[2];
+        uB[0] = (float)B.U[0] + (W1 * rb[2] - W2 * rb[1]);
+        uB[1] = (float)B.U[1] + (W2 * rb[0] - W0 * rb[2]);
+        uB[2] = (float)B.U[2] + (W0 * rb[1] - W1 * rb[0]);
+        d[0] = df[0];
+        d[1] = df[1];
+        d[2] = df[2];
+    }
+    // u_G = u(x_F + c_i, t) for Delta < 1/2 (Sec. 2.1)
+    long long G = -1;
+    if (delta < 0.5) {
+        int g[3] = {x + cxi, y + cyi, z + czi};
+        const int n[3] = {p.nx, p.ny, p.nz};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            if (g[a] >= 0 && g[a] < n[a]) continue;
+            if (!p.per[a]) ok = false;
+            else g[a] += g[a] < 0 ? n[a] : -n[a];
+        }
+        if (ok) {
+            G = cell_of(p, g[0], g[1], g[2]);
+            if (sb.owner_t[G] != 0) G = -1;
+        }
+        if (G < 0) atomicAdd(&sb.counters[0], 1ull);
+    }
+    double fa, fb, ps[3], pm[3];
+    if constexpr (P::exact) {
+        fb = ldP(pop + (long long)ib * N + cell);
+        const double rhoF = mac[4 * cell];
+        const double uF[3] = {mac[4 * cell + 1], mac[4 * cell + 2], mac[4 * cell + 3]};
+        double ubf[3], chi;
+        if (delta < 0.5) {
+            if (G >= 0) {
+                for (int a = 0; a < 3; ++a) ubf[a] = mac[4 * G + 1 + a];
+                chi = (2.0 * delta - 1.0) / (p.tau - 2.0);
+            } else {
+                for (int a = 0; a < 3; ++a) ubf[a] = uF[a];
+                chi = 0.0;
+            }
+        } else {
+            double k3 = 3.0 / (2.0 * delta);
+            for (int a = 0; a < 3; ++a) ubf[a] = uF[a] + k3 * (uB[a] - uF[a]);
+            chi = (2.0 * delta - 1.0) / (p.tau + 0.5);
+        }
+        double g = geq_x(p, tb, ib, rhoF, ubf, uF);
+        double rhow = p.eq == 0 ? p.rho0 : rhoF;
+        double cuB = (double)cxi * uB[0] + (double)cyi * uB[1] + (double)czi * uB[2];
+        double bc = (1.0 - chi) * fb + chi * g + 2.0 * tb.w[i] * rhow * 3.0 * cuB;
+        stS(pop + (long long)i * N + A, bc);
+        fa = bc;
+        double sum = fa + fb;
+        ps[0] = -cxi * sum;
+        ps[1] = -cyi * sum;
+        ps[2] = -czi * sum;
+        const int cb[3] = {-cxi, -cyi, -czi};
+        const int cc[3] = {cxi, cyi, czi};
+        for (int a = 0; a < 3; ++a) pm[a] = -(cc[a] - uB[a]) * fa + (cb[a] - uB[a]) * fb;
+    } else {
+        const float fbf = ldP(pop + (long long)ib * N + cell);
+        const float4 mF = reinterpret_cast<const float4 *>(mac)[cell];
+        const float uF[3] = {mF.y, mF.z, mF.w};
+        float ubf[3], chi;
+        const float dl = (float)delta;
+        if (delta < 0.5) {
+            if (G >= 0) {
+                const float4 mG = reinterpret_cast<const float4 *>(mac)[G];
+                ubf[0] = mG.y;
+                ubf[1] = mG.z;
+                ubf[2] = mG.w;
+                chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
+            } else {
+                ubf[0] = uF[0];
+                ubf[1] = uF[1];
+                ubf[2] = uF[2];
+                chi = 0.0f;
+            }
+        } else {
+            const float k3 = 3.0f / (2.0f * dl);
+            for (int a = 0; a < 3; ++a) ubf[a] = fmaf(k3, (float)uB[a] - uF[a], uF[a]);
+            chi = (2.0f * dl - 1.0f) / ((float)p.tau + 0.5f);
+        }
+        const float g = dgeq_f(p, tb, ib, mF.x, ubf, uF);
+        const float rhow = p.eq == 0 ? p.rho0f : 1.0f + mF.x;
+        const float cuB = cxi * (float)uB[0] + cyi * (float)uB[1] + czi * (float)uB[2];
+        const float bc = fmaf(6.0f * (float)tb.w[i] * rhow, cuB, fmaf(chi, g - fbf, fbf));
+        stS(pop + (long long)i * N + A, bc);
+        fa = (double)roundS(pop, bc);
+        fb = (double)fbf;
+        // deviation form: the constant parts -2 w_i c_i cancel over the
+        // closed link set of a body (N_i = N_ib on every lattice line);
+        // per-link products in FP32, the per-body sums in FP64
+        const float sum = (float)fa + fbf, dif = (float)fa - fbf;
+        const float d0 = (float)d[0], d1 = (float)d[1], d2 = (float)d[2];
+        const float s0 = -cxi * sum, s1 = -cyi * sum, s2 = -czi * sum;
+        const float m0 = fmaf((float)uB[0], dif, s0), m1 = fmaf((float)uB[1], dif, s1),
+                    m2 = fmaf((float)uB[2], dif, s2);
+        out[0] = s0;
+        out[1] = s1;
+        out[2] = s2;
+        out[3] = d1 * s2 - d2 * s1;
+        out[4] = d2 * s0 - d0 * s2;
+        out[5] = d0 * s1 - d1 * s0;
+        out[6] = m0;
+        out[7] = m1;
+        out[8] = m2;
+        out[9] = d1 * m2 - d2 * m1;
+        out[10] = d2 * m0 - d0 * m2;
+        out[11] = d0 * m1 - d1 * m0;
+        return;
+    }
+    double ts[3], tm[3];
+    cross3(d, ps, ts);
+    cross3(d, pm, tm);
+    out[0] = ps[0];
+    out[1] = ps[1];
+    out[2] = ps[2];
+    out[3] = ts[0];
+    out[4] = ts[1];
+    out[5] = ts[2];
+    out[6] = pm[0];
+    out[7] = pm[1];
+    out[8] = pm[2];
+    out[9] = tm[0];
+    out[10] = tm[1];
+    out[11] = tm[2];
+}
+
+// wall values on cut links + per-link momentum-exchange contributions.
+// FP64 mode: one thread per link over a global index, contributions stored
+// per link and summed by k_finish in link order.  Reduced-precision modes:
+// each block iteration takes one tile of LINK_THREADS consecutive links of
+// one body and sums the tile in FP64 (fixed order), so k_finish only adds a
+// few tile partials per body.
+template <class L, class P>
+__global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
     __shared__ LatTab tb;
     if (threadIdx.x == 0) tb = make_tab<L>();
     __syncthreads();
-    S *pop = (S *)sb.src;
-    const C *mac = (const C *)sb.mac_t;
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gsz = (long long)gridDim.x * blockDim.x;
-    const long long N = p.N;
-    const long long total = sb.link_pre[p.nb];
-    // one global index over the links of every body (load balanced)
-    for (long long k = gtid; k < total; k += gsz) {
-        int b = 0;
-        {
-            int hi = p.nb;
+    if constexpr (P::exact) {
+        const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long gsz = (long long)gridDim.x * blockDim.x;
+        const long long total = sb.link_pre[p.nb];
+        for (long long k = gtid; k < total; k += gsz) {
+            int b = 0, hi = p.nb;
             while (hi - b > 1) {
                 const int mid = (b + hi) >> 1;
                 if (sb.link_pre[mid] <= k) b = mid;
                 else hi = mid;
             }
-        }
-        const BodyDev &B = sb.bodies[b];
-        const double *X = sb.poses + (long long)b * POSE_STRIDE + 3; // wrapped pose at t
-        {
+            const BodyDev &B = sb.bodies[b];
+            const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;
             const long long j = B.link_off + (k - sb.link_pre[b]);
-            const long long cell = sb.Lcell[j];
-            const int i = sb.Ldir[j];
-            const double delta = sb.Ldelta[j];
-            int x, y, z;
-            coords_of(p, cell, x, y, z);
-            const int cxi = tb.c[i][0], cyi = tb.c[i][1], czi = tb.c[i][2];
-            const int ib = tb.opp[i];
-            const long long A =
-                cell_of(p, wrap_axis(x - cxi, p.nx), wrap_axis(y - cyi, p.ny), wrap_axis(z - czi, p.nz));
-            double d[3], uB[3];
-            if constexpr (P::exact) {
-                double rB[3];
-                disp(p, X, x, y, z, d);
-                rB[0] = d[0] - delta * cxi;
-                rB[1] = d[1] - delta * cyi;
-                rB[2] = d[2] - delta * czi;
-                body_velocity(B, rB, uB);
-            } else { // FP32 link geometry (reduced-precision modes)
-                const double *Pf = X + 9; // floor(Xw), frac(Xw)
-                const int c3[3] = {x, y, z};
-                float df[3], rb[3];
-                for (int a = 0; a < 3; ++a) {
-                    int kk = c3[a] - (int)Pf[a];
-                    if (p.per[a]) {
-                        const int n = axis_len(p, a);
-                        if (2 * kk > n) kk -= n;
-                        else if (2 * kk < -n) kk += n;
-                    }
-                    df[a] = (float)kk - (float)Pf[3 + a];
-                }
-                const float dl = (float)delta;
-                rb[0] = df[0] - dl * cxi;
-                rb[1] = df[1] - dl * cyi;
-                rb[2] = df[2] - dl * czi;
-                const float W0 = (float)B.W[0], W1 = (float)B.W[1], W2 = (float)B.W[2];
-                uB[0] = (float)B.U[0] + (W1 * rb[2] - W2 * rb[1]);
-                uB[1] = (float)B.U[1] + (W2 * rb[0] - W0 * rb[2]);
-                uB[2] = (float)B.U[2] + (W0 * rb[1] - W1 * rb[0]);
-                d[0] = df[0];
-                d[1] = df[1];
-                d[2] = df[2];
-            }
-            // u_G = u(x_F + c_i, t) for Delta < 1/2 (Sec. 2.1)
-            long long G = -1;
-            if (delta < 0.5) {
-                int g[3] = {x + cxi, y + cyi, z + czi};
-                const int n[3] = {p.nx, p.ny, p.nz};
-                bool ok = true;
-                for (int a = 0; a < 3; ++a) {
-                    if (g[a] >= 0 && g[a] < n[a]) continue;
-                    if (!p.per[a]) ok = false;
-                    else g[a] += g[a] < 0 ? n[a] : -n[a];
-                }
-                if (ok) {
-                    G = cell_of(p, g[0], g[1], g[2]);
-                    if (sb.owner_t[G] != 0) G = -1;
-                }
-                if (G < 0) atomicAdd(&sb.counters[0], 1ull);
-            }
-            double fa, fb, ps[3], pm[3];
-            if constexpr (P::exact) {
-                fb = ldP(pop + (long long)ib * N + cell);
-                const double rhoF = mac[4 * cell];
-                const double uF[3] = {mac[4 * cell + 1], mac[4 * cell + 2], mac[4 * cell + 3]};
-                double ubf[3], chi;
-                if (delta < 0.5) {
-                    if (G >= 0) {
-                        for (int a = 0; a < 3; ++a) ubf[a] = mac[4 * G + 1 + a];
-                        chi = (2.0 * delta - 1.0) / (p.tau - 2.0);
-                    } else {
-                        for (int a = 0; a < 3; ++a) ubf[a] = uF[a];
-                        chi = 0.0;
-                    }
-                } else {
-                    double k3 = 3.0 / (2.0 * delta);
-                    for (int a = 0; a < 3; ++a) ubf[a] = uF[a] + k3 * (uB[a] - uF[a]);
-                    chi = (2.0 * delta - 1.0) / (p.tau + 0.5);
-                }
-                double g = geq_x(p, tb, ib, rhoF, ubf, uF);
-                double rhow = p.eq == 0 ? p.rho0 : rhoF;
-                double cuB = (double)cxi * uB[0] + (double)cyi * uB[1] + (double)czi * uB[2];
-                double bc = (1.0 - chi) * fb + chi * g + 2.0 * tb.w[i] * rhow * 3.0 * cuB;
-                stS(pop + (long long)i * N + A, bc);
-                fa = bc;
-                double sum = fa + fb;
-                ps[0] = -cxi * sum;
-                ps[1] = -cyi * sum;
-                ps[2] = -czi * sum;
-                const int cb[3] = {-cxi, -cyi, -czi};
-                const int cc[3] = {cxi, cyi, czi};
-                for (int a = 0; a < 3; ++a) pm[a] = -(cc[a] - uB[a]) * fa + (cb[a] - uB[a]) * fb;
-            } else {
-                const float fbf = ldP(pop + (long long)ib * N + cell);
-                const float4 mF = reinterpret_cast<const float4 *>(mac)[cell];
-                const float uF[3] = {mF.y, mF.z, mF.w};
-                float ubf[3], chi;
-                const float dl = (float)delta;
-                if (delta < 0.5) {
-                    if (G >= 0) {
-                        const float4 mG = reinterpret_cast<const float4 *>(mac)[G];
-                        ubf[0] = mG.y;
-                        ubf[1] = mG.z;
-                        ubf[2] = mG.w;
-                        chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
-                    } else {
-                        ubf[0] = uF[0];
-                        ubf[1] = uF[1];
-                        ubf[2] = uF[2];
-                        chi = 0.0f;
-                    }
-                } else {
-                    const float k3 = 3.0f / (2.0f * dl);
-                    for (int a = 0; a < 3; ++a) ubf[a] = fmaf(k3, (float)uB[a] - uF[a], uF[a]);
-                    chi = (2.0f * dl - 1.0f) / ((float)p.tau + 0.5f);
-                }
-                const float g = dgeq_f(p, tb, ib, mF.x, ubf, uF);
-                const float rhow = p.eq == 0 ? p.rho0f : 1.0f + mF.x;
-                const float cuB = (float)(cxi * uB[0] + cyi * uB[1] + czi * uB[2]);
-                const float bc = fmaf(6.0f * (float)tb.w[i] * rhow, cuB, fmaf(chi, g - fbf, fbf));
-                stS(pop + (long long)i * N + A, bc);
-                fa = (double)roundS(pop, bc);
-                fb = (double)fbf;
-                // deviation form: the constant parts -2 w_i c_i cancel over the
-                // closed link set of a body (N_i = N_ib on every lattice line);
-                // per-link products in FP32, the per-body sums in FP64
-                const float sum = (float)fa + fbf, dif = (float)fa - fbf;
-                const float d0 = (float)d[0], d1 = (float)d[1], d2 = (float)d[2];
-                const float s0 = -cxi * sum, s1 = -cyi * sum, s2 = -czi * sum;
-                const float m0 = fmaf((float)uB[0], dif, s0), m1 = fmaf((float)uB[1], dif, s1),
-                            m2 = fmaf((float)uB[2], dif, s2);
-                const long long st = p.me_stride;
-                double *o = sb.me + j;
-                o[0 * st] = s0;
-                o[1 * st] = s1;
-                o[2 * st] = s2;
-                o[3 * st] = d1 * s2 - d2 * s1;
-                o[4 * st] = d2 * s0 - d0 * s2;
-                o[5 * st] = d0 * s1 - d1 * s0;
-                o[6 * st] = m0;
-                o[7 * st] = m1;
-                o[8 * st] = m2;
-                o[9 * st] = d1 * m2 - d2 * m1;
-                o[10 * st] = d2 * m0 - d0 * m2;
-                o[11 * st] = d0 * m1 - d1 * m0;
-                continue;
-            }
-            double ts[3], tm[3];
-            cross3(d, ps, ts);
-            cross3(d, pm, tm);
+            double out[ME_PER_LINK];
+            link_work<L, P>(p, sb, tb, B, X, j, out);
             const long long st = p.me_stride;
-            double *o = sb.me + j;
-            o[0 * st] = ps[0];
-            o[1 * st] = ps[1];
-            o[2 * st] = ps[2];
-            o[3 * st] = ts[0];
-            o[4 * st] = ts[1];
-            o[5 * st] = ts[2];
-            o[6 * st] = pm[0];
-            o[7 * st] = pm[1];
-            o[8 * st] = pm[2];
-            o[9 * st] = tm[0];
-            o[10 * st] = tm[1];
-            o[11 * st] = tm[2];
+            for (int c = 0; c < ME_PER_LINK; ++c) sb.me[c * st + j] = out[c];
+        }
+    } else {
+        __shared__ double red[LINK_THREADS / 32][ME_PER_LINK];
+        const long long tiles = sb.tile_pre[p.nb];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+            int b = 0, hi = p.nb;
+            while (hi - b > 1) {
+                const int mid = (b + hi) >> 1;
+                if (sb.tile_pre[mid] <= tile) b = mid;
+                else hi = mid;
+            }
+            const BodyDev &B = sb.bodies[b];
+            const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;
+            const long long k = (tile - sb.tile_pre[b]) * LINK_THREADS + threadIdx.x;
+            double out[ME_PER_LINK];
+            for (int c = 0; c < ME_PER_LINK; ++c) out[c] = 0.0;
+            if (k < sb.link_cnt[b]) link_work<L, P>(p, sb, tb, B, X, B.link_off + k, out);
+            for (int c = 0; c < ME_PER_LINK; ++c) {
+                double v = out[c];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) red[wid][c] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < ME_PER_LINK) {
+                double v = 0.0;
+                for (int w = 0; w < LINK_THREADS / 32; ++w) v += red[w][threadIdx.x];
+                sb.tile_part[tile * ME_PER_LINK + threadIdx.x] = v;
+            }
+            __syncthreads();
         }
     }
 }
@@ -548,12 +592,11 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
 // covered (sign +1) and uncovered (sign -1) nodes of one moving body:
 // impulsive terms and refill (one CTA per moving body)
 template <class L, class P>
-__global__ void __launch_bounds__(IMP_THREADS) k_imp(Params p, StepBufs sb) {
+__device__ __forceinline__ void imp_body(const Params &p, const StepBufs &sb, int b) {
     using S = typename P::S;
     using C = typename P::C;
     __shared__ double part[IMP_THREADS][6];
     __shared__ int sgn[IMP_THREADS];
-    const int b = sb.moving_ids[blockIdx.x];
     const BodyDev &B = sb.bodies[b];
     const long long cnt = sb.apm_cnt[b];
     const S *src = (const S *)sb.src;
@@ -662,47 +705,40 @@ __global__ void __launch_bounds__(IMP_THREADS) k_imp(Params p, StepBufs sb) {
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        for (int a = 0; a < 6; ++a) sb.imp[b * 6 + a] = acc[a];
+    if (threadIdx.x == 0) {
+        double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
+        for (int a = 0; a < 6; ++a) row[6 + a] = acc[a];
+    }
 }
 
 // per-body sum of the link contributions into the series row of step t
-template <bool EXACT>
-__global__ void __launch_bounds__(RED_THREADS) k_reduce(Params p, StepBufs sb) {
-    const int b = blockIdx.x;
+template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &p, const StepBufs &sb, int b) {
     const BodyDev &B = sb.bodies[b];
-    const long long cnt = sb.link_cnt[b];
-    const double *me = sb.me + B.link_off;
-    const long long st = p.me_stride;
     double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
-    if constexpr (EXACT) {
-        // sequential in link order (= cell, direction order of the oracle)
-        if (threadIdx.x < ME_PER_LINK) {
-            const int k = threadIdx.x;
-            const double *mk = me + k * st;
-            double acc = 0.0;
+    if (threadIdx.x < ME_PER_LINK) {
+        const int k = threadIdx.x;
+        double acc = 0.0;
+        if constexpr (EXACT) { // sequential in link order (= cell, direction order of the oracle)
+            const long long cnt = sb.link_cnt[b];
+            const double *mk = sb.me + k * p.me_stride + B.link_off;
             for (long long j = 0; j < cnt; ++j) acc += mk[j];
-            row[k < 6 ? k : k + 6] = acc;
+        } else { // tile partials of this body, in tile order
+            for (long long tl = sb.tile_pre[b]; tl < sb.tile_pre[b + 1]; ++tl) acc += sb.tile_part[tl * ME_PER_LINK + k];
         }
-    } else {
-        __shared__ double sh[ME_PER_LINK][RED_THREADS];
-        double acc[ME_PER_LINK];
-        for (int k = 0; k < ME_PER_LINK; ++k) acc[k] = 0.0;
-        for (long long j = threadIdx.x; j < cnt; j += RED_THREADS)
-            for (int k = 0; k < ME_PER_LINK; ++k) acc[k] += me[k * st + j];
-        for (int k = 0; k < ME_PER_LINK; ++k) sh[k][threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s)
-                for (int k = 0; k < ME_PER_LINK; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x < ME_PER_LINK) {
-            const int k = threadIdx.x;
-            row[k < 6 ? k : k + 6] = sh[k][0];
-        }
+        row[k < 6 ? k : k + 6] = acc;
     }
-    if (threadIdx.x < 6) row[6 + threadIdx.x] = B.moving ? sb.imp[b * 6 + threadIdx.x] : 0.0;
+    if (!B.moving && threadIdx.x < 6) row[6 + threadIdx.x] = 0.0;
+}
+
+// end of step: blocks [0, nb) reduce the link contributions of one body,
+// blocks [nb, nb + moving) handle the covered/uncovered nodes of one moving
+// body (they write disjoint parts of the series row)
+template <class L, class P> __global__ void __launch_bounds__(IMP_THREADS) k_finish(Params p, StepBufs sb) {
+    if ((int)blockIdx.x < p.nb) {
+        reduce_body<P::exact>(p, sb, blockIdx.x);
+        return;
+    }
+    imp_body<L, P>(p, sb, sb.moving_ids[blockIdx.x - p.nb]);
 }
 
 } // namespace lbm
