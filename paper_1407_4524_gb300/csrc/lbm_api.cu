@@ -106,7 +106,7 @@ struct lbm_domain {
     double *poses = nullptr;
     long long *link_pre = nullptr;
     long long *tile_pre = nullptr;
-    double *tile_part = nullptr;
+    unsigned long long *acc = nullptr;
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -169,7 +169,7 @@ void free_body_buffers(lbm_domain *D) {
     D->poses = nullptr;
     D->link_pre = nullptr;
     D->tile_pre = nullptr;
-    D->tile_part = nullptr;
+    D->acc = nullptr;
     D->prep_dirty = true;
     D->nb = D->n_moving = 0;
     D->nchunk_all = D->nchunk_mov = 0;
@@ -292,7 +292,7 @@ StepBufs step_bufs(lbm_domain *D) {
     sb.link_cnt = D->link_cnt[cur];
     sb.link_pre = D->link_pre;
     sb.tile_pre = D->tile_pre;
-    sb.tile_part = D->tile_part;
+    sb.acc = D->acc;
     sb.poses = D->poses;
     sb.Lcell = D->Lcell[cur];
     sb.Ldir = D->Ldir[cur];
@@ -330,7 +330,7 @@ GeomArgs geom_args(lbm_domain *D, bool moving_step) {
     g.t = D->t;
     g.t_link = moving_step ? D->t + 1 : D->t;
     g.do_apm = moving_step ? 1 : 0;
-    g.do_flags = moving_step ? 1 : 0;
+    g.do_flags = (moving_step && D->prec == LBM_FP64) ? 1 : 0;
     return g;
 }
 
@@ -577,7 +577,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->poses, nbx * POSE_STRIDE, &T))) return rc;
     if ((rc = alloc_t(D, &D->link_pre, nbx + 1, &T))) return rc;
     if ((rc = alloc_t(D, &D->tile_pre, nbx + 1, &T))) return rc;
-    if ((rc = alloc_t(D, &D->tile_part, (size_t)(tiles_cap + 1) * ME_PER_LINK, &T))) return rc;
+    if ((rc = alloc_t(D, &D->acc, nbx * SERIES_ROW, &T))) return rc;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
     (void)maxcnt;

@@ -94,7 +94,8 @@ __device__ __forceinline__ long long nbr(const Params &p, int x, int y, int z, i
     for (int a = 0; a < 3; ++a) {
         if (q[a] >= 0 && q[a] < n[a]) continue;
         if (!p.per[a]) return -1;
-        q[a] = ((q[a] % n[a]) + n[a]) % n[a];
+        while (q[a] < 0) q[a] += n[a]; // |k c_i| <= 2: at most two turns
+        while (q[a] >= n[a]) q[a] -= n[a];
     }
     return cell_of(p, q[0], q[1], q[2]);
 }
@@ -247,17 +248,16 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     region_lo(p, B, P, REGION_MARGIN, lo);
     RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y; // first chunk of this body
-    bool near = false;
+    float dist = -1.0f;
     if (rc.valid) {
         float d[3];
         frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
-        const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
-        const float R = (float)B.R;
-        near = dist >= R - 2.0f && dist <= R + 5.5f;
+        dist = sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
     }
+    const float R = (float)B.R;
     if (g.do_apm) {
         int flag = 0, sign = 0;
-        if (near) {
+        if (rc.valid && dist >= R - 2.0f && dist <= R + 2.0f) {
             const bool in_t = g.owner_t[rc.cell] == me, in1 = g.owner_t1[rc.cell] == me;
             flag = in_t != in1;
             sign = in1 ? 1 : -1;
@@ -277,15 +277,15 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
             g.apm_cnt[b] = n < B.apm_cap ? n : B.apm_cap;
         }
     }
+    // node flags (FP64 mode: the moment-store flag follows the geometry of t+1)
+    if (g.do_flags && rc.valid && dist >= R - 2.0f && dist <= R + 5.5f)
+        g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
     int nl = 0;
-    if (near) {
-        if (g.do_flags) g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
-        if (owner_L[rc.cell] == 0) {
+    if (rc.valid && dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
 #pragma unroll
-            for (int i = 1; i < L::Q; ++i) {
-                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                nl += (a >= 0 ? owner_L[a] : (uint16_t)0) == me;
-            }
+        for (int i = 1; i < L::Q; ++i) {
+            const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+            nl += (a >= 0 ? owner_L[a] : (uint16_t)0) == me;
         }
     }
     int total;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
         frame_disp_f(p, F, rc.x, rc.y, rc.z, df);
         const float dist = sqrtf(df[0] * df[0] + df[1] * df[1] + (B.shape == 1 ? df[2] * df[2] : 0.0f));
         const float R = (float)B.R;
-        if (dist >= R - 2.0f && dist <= R + 2.5f && owner_L[rc.cell] == 0) {
+        if (dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);

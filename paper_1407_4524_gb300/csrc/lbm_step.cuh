@@ -40,7 +40,7 @@ struct StepBufs {
     void *dst;       // fhat(t+1)
     const void *mac_t;
     void *mac_t1;
-    const uint8_t *flags;
+    uint8_t *flags;
     const uint16_t *owner_t;
     const BodyDev *bodies;
     const int *moving_ids;
@@ -48,7 +48,6 @@ struct StepBufs {
     const long long *link_cnt; // per body, current link buffer
     const long long *link_pre; // prefix of link_cnt over bodies (nb + 1 entries)
     const long long *tile_pre; // prefix of per-body link tiles (LINK_THREADS links each)
-    double *tile_part;         // per tile: ME_PER_LINK partial sums (reduced-precision modes)
     const double *poses;       // POSE_STRIDE doubles per body
     const uint32_t *Lcell;
     const uint8_t *Ldir;
@@ -60,6 +59,7 @@ struct StepBufs {
     double *imp;
     double *series;
     unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered
+    unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
 };
 
@@ -194,6 +194,50 @@ __device__ __forceinline__ float dgeq_f(const Params &p, const LatTab &tb, int i
     return (float)tb.w[ib] * fmaf(rr, poly, drhoF);
 }
 
+// ========================================================= fixed point ==
+// Reduced-precision modes accumulate the per-body momentum-exchange sums in
+// 64-bit fixed point (2^-36 resolution, range +-2^27 per body): integer
+// addition is exact and associative, so the sums are exact for the FP32
+// per-link terms and independent of summation order (atomics are safe and
+// the result is deterministic).
+constexpr float FX_SCALE = 68719476736.0f; // 2^36
+constexpr double FX_INV = 1.0 / 68719476736.0;
+
+__device__ __forceinline__ unsigned long long to_fx(float v) {
+    return (unsigned long long)__float2ll_rn(v * FX_SCALE);
+}
+__device__ __forceinline__ double from_fx(unsigned long long v) { return (double)(long long)v * FX_INV; }
+
+// moments of the stored post-collision populations (reduced-precision
+// modes): BGK conserves rho and rho u, so they are the moments of f(t); with
+// the Guo force the collided momentum carries one extra g, removed here.
+template <class L, class S>
+__device__ __forceinline__ void moments_hat(const Params &p, const S *__restrict__ pop, long long cell, float &drho,
+                                            float u[3]) {
+    float f[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = ldP(pop + (long long)i * p.N + cell);
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (p.has_force) {
+        g0 = p.gf[0];
+        g1 = p.gf[1];
+        g2 = p.gf[2];
+    }
+    float r = 0.f, j0 = -0.5f * g0, j1 = -0.5f * g1, j2 = -0.5f * g2;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        r += f[i];
+        j0 += (float)L::cx(i) * f[i];
+        j1 += (float)L::cy(i) * f[i];
+        j2 += (float)L::cz(i) * f[i];
+    }
+    const float inv = 1.0f / (p.eq == 0 ? p.rho0f : 1.0f + r);
+    drho = r;
+    u[0] = j0 * inv;
+    u[1] = j1 * inv;
+    u[2] = j2 * inv;
+}
+
 // ============================================================== streaming ==
 
 // inlet velocity at the wall point of an edge link (x_B = x_F - c_i / 2)
@@ -236,7 +280,12 @@ __device__ __noinline__ typename P::C pull_edge(const Params &p, const typename 
             double cuB = (double)L::cx(i) * uB[0] + (double)L::cy(i) * uB[1] + (double)L::cz(i) * uB[2];
             return fb + 2.0 * L::template w<double>(i) * rhow * 3.0 * cuB;
         } else {
-            float rhow = p.eq == 0 ? p.rho0f : 1.0f + mac_t[4 * cell];
+            float rhow = p.rho0f;
+            if (p.eq != 0) {
+                float dr, uu[3];
+                moments_hat<L>(p, src, cell, dr, uu);
+                rhow = 1.0f + dr;
+            }
             float cuB = (float)L::cx(i) * (float)uB0;
             return fmaf(6.0f * L::template w<float>(i) * rhow, cuB, fb);
         }
@@ -302,12 +351,6 @@ __global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *
         for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, 0.0f, u0, usq15);
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
-        if (mac_here) {
-            mac[4 * cell] = drho;
-            mac[4 * cell + 1] = u[0];
-            mac[4 * cell + 2] = u[1];
-            mac[4 * cell + 3] = u[2];
-        }
         collide_f<L>(p, f, drho, u);
     }
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
@@ -341,9 +384,6 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename 
     } else {
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
-        if (fl & FL_MAC) {
-            reinterpret_cast<float4 *>(mac_t1)[cell] = make_float4(drho, u[0], u[1], u[2]);
-        }
         collide_f<L>(p, f, drho, u);
     }
 #pragma unroll
@@ -359,11 +399,13 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename 
 // Equalities they need exactly the wall value and fhat_ib(x_F, t).
 template <class L, class P>
 __device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, const LatTab &tb,
-                                          const BodyDev &B, const double *X, long long j, double out[ME_PER_LINK]) {
+                                          const BodyDev &B, const double *X, long long j, double out[ME_PER_LINK],
+                                          float outf[ME_PER_LINK]) {
     using S = typename P::S;
     using C = typename P::C;
     S *pop = (S *)sb.src;
     const C *mac = (const C *)sb.mac_t;
+    (void)mac;
     const long long N = p.N;
     const long long cell = sb.Lcell[j];
     const int i = sb.Ldir[j];
@@ -458,16 +500,14 @@ __device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, c
         for (int a = 0; a < 3; ++a) pm[a] = -(cc[a] - uB[a]) * fa + (cb[a] - uB[a]) * fb;
     } else {
         const float fbf = ldP(pop + (long long)ib * N + cell);
-        const float4 mF = reinterpret_cast<const float4 *>(mac)[cell];
-        const float uF[3] = {mF.y, mF.z, mF.w};
+        float drF, uF[3];
+        moments_hat<L>(p, pop, cell, drF, uF);
         float ubf[3], chi;
         const float dl = (float)delta;
         if (delta < 0.5) {
             if (G >= 0) {
-                const float4 mG = reinterpret_cast<const float4 *>(mac)[G];
-                ubf[0] = mG.y;
-                ubf[1] = mG.z;
-                ubf[2] = mG.w;
+                float drG;
+                moments_hat<L>(p, pop, G, drG, ubf);
                 chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
             } else {
                 ubf[0] = uF[0];
@@ -480,8 +520,8 @@ __device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, c
             for (int a = 0; a < 3; ++a) ubf[a] = fmaf(k3, (float)uB[a] - uF[a], uF[a]);
             chi = (2.0f * dl - 1.0f) / ((float)p.tau + 0.5f);
         }
-        const float g = dgeq_f(p, tb, ib, mF.x, ubf, uF);
-        const float rhow = p.eq == 0 ? p.rho0f : 1.0f + mF.x;
+        const float g = dgeq_f(p, tb, ib, drF, ubf, uF);
+        const float rhow = p.eq == 0 ? p.rho0f : 1.0f + drF;
         const float cuB = cxi * (float)uB[0] + cyi * (float)uB[1] + czi * (float)uB[2];
         const float bc = fmaf(6.0f * (float)tb.w[i] * rhow, cuB, fmaf(chi, g - fbf, fbf));
         stS(pop + (long long)i * N + A, bc);
@@ -495,18 +535,18 @@ __device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, c
         const float s0 = -cxi * sum, s1 = -cyi * sum, s2 = -czi * sum;
         const float m0 = fmaf((float)uB[0], dif, s0), m1 = fmaf((float)uB[1], dif, s1),
                     m2 = fmaf((float)uB[2], dif, s2);
-        out[0] = s0;
-        out[1] = s1;
-        out[2] = s2;
-        out[3] = d1 * s2 - d2 * s1;
-        out[4] = d2 * s0 - d0 * s2;
-        out[5] = d0 * s1 - d1 * s0;
-        out[6] = m0;
-        out[7] = m1;
-        out[8] = m2;
-        out[9] = d1 * m2 - d2 * m1;
-        out[10] = d2 * m0 - d0 * m2;
-        out[11] = d0 * m1 - d1 * m0;
+        outf[0] = s0;
+        outf[1] = s1;
+        outf[2] = s2;
+        outf[3] = d1 * s2 - d2 * s1;
+        outf[4] = d2 * s0 - d0 * s2;
+        outf[5] = d0 * s1 - d1 * s0;
+        outf[6] = m0;
+        outf[7] = m1;
+        outf[8] = m2;
+        outf[9] = d1 * m2 - d2 * m1;
+        outf[10] = d2 * m0 - d0 * m2;
+        outf[11] = d0 * m1 - d1 * m0;
         return;
     }
     double ts[3], tm[3];
@@ -552,14 +592,14 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
             const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;
             const long long j = B.link_off + (k - sb.link_pre[b]);
             double out[ME_PER_LINK];
-            link_work<L, P>(p, sb, tb, B, X, j, out);
+            float outf[ME_PER_LINK];
+            link_work<L, P>(p, sb, tb, B, X, j, out, outf);
             const long long st = p.me_stride;
             for (int c = 0; c < ME_PER_LINK; ++c) sb.me[c * st + j] = out[c];
         }
     } else {
-        __shared__ double red[LINK_THREADS / 32][ME_PER_LINK];
         const long long tiles = sb.tile_pre[p.nb];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int lane = threadIdx.x & 31;
         for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
             int b = 0, hi = p.nb;
             while (hi - b > 1) {
@@ -570,21 +610,20 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
             const BodyDev &B = sb.bodies[b];
             const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;
             const long long k = (tile - sb.tile_pre[b]) * LINK_THREADS + threadIdx.x;
+            const long long cnt = sb.link_cnt[b];
+            const long long warp_first = k - lane;
+            if (warp_first >= cnt) continue; // whole warp past the body's links
             double out[ME_PER_LINK];
-            for (int c = 0; c < ME_PER_LINK; ++c) out[c] = 0.0;
-            if (k < sb.link_cnt[b]) link_work<L, P>(p, sb, tb, B, X, B.link_off + k, out);
+            float outf[ME_PER_LINK];
+            for (int c = 0; c < ME_PER_LINK; ++c) outf[c] = 0.0f;
+            if (k < cnt) link_work<L, P>(p, sb, tb, B, X, B.link_off + k, out, outf);
+            unsigned long long *acc = sb.acc + (long long)b * SERIES_ROW;
+#pragma unroll
             for (int c = 0; c < ME_PER_LINK; ++c) {
-                double v = out[c];
+                unsigned long long v = to_fx(outf[c]);
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0) red[wid][c] = v;
+                if (lane == 0) atomicAdd(acc + (c < 6 ? c : c + 6), v);
             }
-            __syncthreads();
-            if (threadIdx.x < ME_PER_LINK) {
-                double v = 0.0;
-                for (int w = 0; w < LINK_THREADS / 32; ++w) v += red[w][threadIdx.x];
-                sb.tile_part[tile * ME_PER_LINK + threadIdx.x] = v;
-            }
-            __syncthreads();
         }
     }
 }
@@ -592,7 +631,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
 // covered (sign +1) and uncovered (sign -1) nodes of one moving body:
 // impulsive terms and refill (one CTA per moving body)
 template <class L, class P>
-__device__ __forceinline__ void imp_body(const Params &p, const StepBufs &sb, int b) {
+__device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &sb, int b) {
     using S = typename P::S;
     using C = typename P::C;
     __shared__ double part[IMP_THREADS][6];
@@ -685,6 +724,7 @@ __device__ __forceinline__ void imp_body(const Params &p, const StepBufs &sb, in
             double r[3], tq[3];
             disp(p, X, x, y, z, r);
             cross3(r, m, tq);
+            sb.flags[A] = (uint8_t)((sb.flags[A] & ~FL_SOLID) | (s > 0 ? FL_SOLID : 0));
             part[threadIdx.x][0] = m[0];
             part[threadIdx.x][1] = m[1];
             part[threadIdx.x][2] = m[2];
@@ -711,6 +751,93 @@ __device__ __forceinline__ void imp_body(const Params &p, const StepBufs &sb, in
     }
 }
 
+
+// reduced-precision modes: same terms, FP32 per node, fixed-point block sum
+template <class L, class P>
+__device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &sb, int b) {
+    using S = typename P::S;
+    __shared__ unsigned long long acc_s[6];
+    if (threadIdx.x < 6) acc_s[threadIdx.x] = 0ull;
+    __syncthreads();
+    const BodyDev &B = sb.bodies[b];
+    const long long cnt = sb.apm_cnt[b];
+    const S *src = (const S *)sb.src;
+    S *dst = (S *)sb.dst;
+    const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;  // wrapped pose at t
+    const double *X1 = sb.poses + (long long)b * POSE_STRIDE + 9; // wrapped pose at t+1
+    for (long long e = threadIdx.x; e < cnt; e += IMP_THREADS) {
+        const long long A = sb.apm_cell[B.apm_off + e];
+        const int s = sb.apm_sign[B.apm_off + e];
+        int x, y, z;
+        coords_of(p, A, x, y, z);
+        float m[3] = {0.f, 0.f, 0.f};
+        float f[L::Q];
+        if (s > 0) { // covered: the streamed values f_i(A, t+1)
+            pull_all<L, P>(p, src, (const float *)nullptr, x, y, z, A, f);
+            atomicAdd(&sb.counters[1], 1ull);
+        } else { // uncovered: refill f(A, t+1) = f^eq(rho_bar, u_B or u_bar)
+            double r1[3], uBd[3];
+            disp(p, X1, x, y, z, r1);
+            body_velocity(B, r1, uBd);
+            float sum = 0.f, us[3] = {0.f, 0.f, 0.f};
+            int nn = 0;
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                int q[3] = {x + L::cx(i), y + L::cy(i), z + L::cz(i)};
+                const int n[3] = {p.nx, p.ny, p.nz};
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) {
+                    if (q[a] >= 0 && q[a] < n[a]) continue;
+                    if (!p.per[a]) ok = false;
+                    else q[a] += q[a] < 0 ? n[a] : -n[a];
+                }
+                if (!ok) continue;
+                const long long nb = cell_of(p, q[0], q[1], q[2]);
+                if (sb.owner_t[nb] != 0) continue;
+                float dr, uu[3];
+                moments_hat<L>(p, src, nb, dr, uu);
+                sum += dr;
+                us[0] += uu[0];
+                us[1] += uu[1];
+                us[2] += uu[2];
+                nn++;
+            }
+            const float drb = nn ? sum / (float)nn : 0.0f;
+            float uf[3];
+            for (int a = 0; a < 3; ++a) uf[a] = (p.refill == 1 && nn) ? us[a] / (float)nn : (float)uBd[a];
+            const float usq15 = 1.5f * (uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+            for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, drb, uf, usq15);
+            atomicAdd(&sb.counters[2], 1ull);
+        }
+        for (int i = 0; i < L::Q; ++i) {
+            m[0] += (float)L::cx(i) * f[i];
+            m[1] += (float)L::cy(i) * f[i];
+            m[2] += (float)L::cz(i) * f[i];
+        }
+        if (s < 0) { // the refilled node starts the next step collided
+            float drho, u[3];
+            moments_f<L>(p, f, drho, u);
+            collide_f<L>(p, f, drho, u);
+            for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + A, f[i]);
+        }
+        double r[3];
+        disp(p, X, x, y, z, r);
+        const float r0 = (float)r[0], r1_ = (float)r[1], r2 = (float)r[2];
+        const float tq[3] = {r1_ * m[2] - r2 * m[1], r2 * m[0] - r0 * m[2], r0 * m[1] - r1_ * m[0]};
+        const float sg = s > 0 ? 1.0f : -1.0f;
+        for (int a = 0; a < 3; ++a) {
+            atomicAdd(&acc_s[a], to_fx(sg * m[a]));
+            atomicAdd(&acc_s[3 + a], to_fx(sg * tq[a]));
+        }
+        sb.flags[A] = (uint8_t)((sb.flags[A] & ~FL_SOLID) | (s > 0 ? FL_SOLID : 0));
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
+        row[6 + threadIdx.x] = from_fx(acc_s[threadIdx.x]);
+    }
+}
+
 // per-body sum of the link contributions into the series row of step t
 template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &p, const StepBufs &sb, int b) {
     const BodyDev &B = sb.bodies[b];
@@ -722,8 +849,10 @@ template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &
             const long long cnt = sb.link_cnt[b];
             const double *mk = sb.me + k * p.me_stride + B.link_off;
             for (long long j = 0; j < cnt; ++j) acc += mk[j];
-        } else { // tile partials of this body, in tile order
-            for (long long tl = sb.tile_pre[b]; tl < sb.tile_pre[b + 1]; ++tl) acc += sb.tile_part[tl * ME_PER_LINK + k];
+        } else { // exact fixed-point sums accumulated by k_links; cleared for the next step
+            unsigned long long *a = sb.acc + (long long)b * SERIES_ROW + (k < 6 ? k : k + 6);
+            acc = from_fx(*a);
+            *a = 0ull;
         }
         row[k < 6 ? k : k + 6] = acc;
     }
@@ -738,7 +867,8 @@ template <class L, class P> __global__ void __launch_bounds__(IMP_THREADS) k_fin
         reduce_body<P::exact>(p, sb, blockIdx.x);
         return;
     }
-    imp_body<L, P>(p, sb, sb.moving_ids[blockIdx.x - p.nb]);
+    if constexpr (P::exact) imp_body_exact<L, P>(p, sb, sb.moving_ids[blockIdx.x - p.nb]);
+    else imp_body_fast<L, P>(p, sb, sb.moving_ids[blockIdx.x - p.nb]);
 }
 
 } // namespace lbm
