@@ -219,7 +219,7 @@ void body_params(const lbm_domain *D, const lbm_body &b, BodyDev &o) {
         o.ext[a] = e;
     }
     long long vol = (long long)o.ext[0] * o.ext[1] * o.ext[2];
-    o.nchunks = (int)((vol + GEOM_THREADS - 1) / GEOM_THREADS);
+    o.nchunks = (int)((vol + GEOM_CHUNK - 1) / GEOM_CHUNK);
     o.link_cap = link_capacity(D, b);
     o.apm_cap = vol;
 }
@@ -581,7 +581,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
     (void)maxcnt;
-    D->links_grid = (int)std::max<long long>(1, std::min<long long>(4 * 152, tiles_cap));
+    D->links_grid = (int)std::max<long long>(1, std::min<long long>(16 * 152, tiles_cap));
     if ((rc = upload_bodies(D))) return rc;
 
     // solid owners at t = 0, flags, links (both buffers), initial state

@@ -23,7 +23,9 @@ constexpr uint8_t FL_MAC = 2;   // store rho,u of f(t+1) at this node
 
 constexpr int SERIES_ROW = 18;  // Fs Ts Fi Ti Fm Tm
 constexpr int ME_PER_LINK = 12; // Fs Ts Fm Tm contributions of one link
-constexpr int GEOM_THREADS = 1024;
+constexpr int GEOM_THREADS = 512;
+constexpr int GEOM_CELLS = 8; // consecutive region cells per thread
+constexpr int GEOM_CHUNK = GEOM_THREADS * GEOM_CELLS;
 constexpr int REGION_MARGIN = 4;
 
 // ---------------------------------------------------------------- lattices --

@@ -66,11 +66,15 @@ struct RegionCell {
     long long cell;
 };
 
-__device__ __forceinline__ RegionCell region_cell(const Params &p, const BodyDev &B, const int lo[3], int chunk) {
+// the j-th (0..GEOM_CELLS-1) region cell of this thread in chunk `chunk`:
+// a thread owns GEOM_CELLS consecutive cells, so per-thread counts followed
+// by a block scan keep every list in cell order
+__device__ __forceinline__ RegionCell region_cell(const Params &p, const BodyDev &B, const int lo[3], int chunk,
+                                                  int j) {
     RegionCell rc{false, 0, 0, 0, 0};
     const int e0 = B.ext[0], e1 = B.ext[1];
     const int vol = e0 * e1 * B.ext[2];
-    const int k = chunk * GEOM_THREADS + (int)threadIdx.x;
+    const int k = chunk * GEOM_CHUNK + (int)threadIdx.x * GEOM_CELLS + j;
     if (k >= vol) return rc;
     const int kz = k / (e0 * e1);
     const int rem = k - kz * e0 * e1;
@@ -181,6 +185,12 @@ __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, 
     }
 }
 
+__device__ __forceinline__ float frame_dist(const Params &p, const BodyDev &B, const Frame &F, const RegionCell &rc) {
+    float d[3];
+    frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
+    return sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
+}
+
 __global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, uint16_t *owner, long long) {
     const int2 cm = g.chunk_map[blockIdx.x];
     const BodyDev &B = g.bodies[cm.x];
@@ -190,9 +200,10 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, u
     __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
-    RegionCell rc = region_cell(p, B, lo, cm.y);
-    if (!rc.valid) return;
-    if (inside_screened(p, B, F, rc.x, rc.y, rc.z)) owner[rc.cell] = (uint16_t)(cm.x + 1);
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (rc.valid && inside_screened(p, B, F, rc.x, rc.y, rc.z)) owner[rc.cell] = (uint16_t)(cm.x + 1);
+    }
 }
 
 // moving step, part a: owner at t+1 for this body's region; count A+/A-.
@@ -208,30 +219,26 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_a(Params p, GeomArgs g) {
     __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
-    RegionCell rc = region_cell(p, B, lo, cm.y);
-    int flag = 0;
-    if (rc.valid) {
-        float d[3];
-        frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
-        const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
-        const float R = (float)B.R;
-        if (dist >= R - 2.0f && dist <= R + 2.0f) {
-            const uint16_t me = (uint16_t)(b + 1);
-            const bool in_t = g.owner_t[rc.cell] == me;
-            const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
-            if (in1) g.owner_t1[rc.cell] = me;
-            else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
-            flag = in_t != in1;
-        }
+    const uint16_t me = (uint16_t)(b + 1);
+    const float R = (float)B.R;
+    int flags = 0;
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        const float dist = frame_dist(p, B, F, rc);
+        if (dist < R - 2.0f || dist > R + 2.0f) continue;
+        const bool in_t = g.owner_t[rc.cell] == me;
+        const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
+        if (in1) g.owner_t1[rc.cell] = me;
+        else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
+        flags += in_t != in1;
     }
     int total;
-    block_excl_scan(flag, &total);
+    block_excl_scan(flags, &total);
     if (threadIdx.x == 0) g.chunk_cnt_apm[blockIdx.x] = total;
 }
 
-// part b: A+/A- lists (moving step), node flags, link counts.  Nodes farther
-// than R+5 from the surface pose of the links, or deeper than R-2 inside,
-// keep their flags and carry no link.
+// part b: A+/A- lists (moving step), node flags (FP64 mode), link counts
 template <class L>
 __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     const int2 cm = g.chunk_map[blockIdx.x];
@@ -246,46 +253,48 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
-    RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y; // first chunk of this body
-    float dist = -1.0f;
-    if (rc.valid) {
-        float d[3];
-        frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
-        dist = sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
-    }
     const float R = (float)B.R;
-    if (g.do_apm) {
-        int flag = 0, sign = 0;
-        if (rc.valid && dist >= R - 2.0f && dist <= R + 2.0f) {
+    unsigned apm_mask = 0, apm_sign = 0;
+    int nl = 0;
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        const float dist = frame_dist(p, B, F, rc);
+        if (g.do_apm && dist >= R - 2.0f && dist <= R + 2.0f) {
             const bool in_t = g.owner_t[rc.cell] == me, in1 = g.owner_t1[rc.cell] == me;
-            flag = in_t != in1;
-            sign = in1 ? 1 : -1;
+            if (in_t != in1) {
+                apm_mask |= 1u << j;
+                if (in1) apm_sign |= 1u << j;
+            }
         }
+        // node flags (FP64 mode: the moment-store flag follows the geometry of t+1)
+        if (g.do_flags && dist >= R - 2.0f && dist <= R + 5.5f)
+            g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
+        if (dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                nl += (a >= 0 ? owner_L[a] : (uint16_t)0) == me;
+            }
+        }
+    }
+    if (g.do_apm) {
         const long long before = block_sum_range(g.chunk_cnt_apm, first, cm.y);
         int total;
-        const int pos = block_excl_scan(flag, &total);
-        if (flag) {
-            const long long at = B.apm_off + before + pos;
-            if (before + pos < B.apm_cap) {
-                g.apm_cell[at] = (uint32_t)rc.cell;
-                g.apm_sign[at] = (int8_t)sign;
+        long long at = before + block_excl_scan(__popc(apm_mask), &total);
+        for (int j = 0; j < GEOM_CELLS; ++j) {
+            if (!(apm_mask & (1u << j))) continue;
+            if (at < B.apm_cap) {
+                RegionCell rc = region_cell(p, B, lo, cm.y, j);
+                g.apm_cell[B.apm_off + at] = (uint32_t)rc.cell;
+                g.apm_sign[B.apm_off + at] = (int8_t)((apm_sign & (1u << j)) ? 1 : -1);
             }
+            at++;
         }
         if (cm.y == B.nchunks - 1 && threadIdx.x == 0) {
             long long n = before + total;
             g.apm_cnt[b] = n < B.apm_cap ? n : B.apm_cap;
-        }
-    }
-    // node flags (FP64 mode: the moment-store flag follows the geometry of t+1)
-    if (g.do_flags && rc.valid && dist >= R - 2.0f && dist <= R + 5.5f)
-        g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
-    int nl = 0;
-    if (rc.valid && dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
-#pragma unroll
-        for (int i = 1; i < L::Q; ++i) {
-            const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-            nl += (a >= 0 ? owner_L[a] : (uint16_t)0) == me;
         }
     }
     int total;
@@ -308,39 +317,44 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
     __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
-    RegionCell rc = region_cell(p, B, lo, cm.y);
     const int first = blockIdx.x - cm.y;
-    unsigned mask = 0;
+    const float R = (float)B.R;
+    unsigned mask[GEOM_CELLS];
     int nl = 0;
-    float df[3] = {0.f, 0.f, 0.f};
-    if (rc.valid) {
-        frame_disp_f(p, F, rc.x, rc.y, rc.z, df);
-        const float dist = sqrtf(df[0] * df[0] + df[1] * df[1] + (B.shape == 1 ? df[2] * df[2] : 0.0f));
-        const float R = (float)B.R;
+#pragma unroll
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        mask[j] = 0;
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        const float dist = frame_dist(p, B, F, rc);
         if (dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                if ((a >= 0 ? owner_L[a] : (uint16_t)0) == me) mask |= 1u << i;
+                if ((a >= 0 ? owner_L[a] : (uint16_t)0) == me) mask[j] |= 1u << i;
             }
-            nl = __popc(mask);
+            nl += __popc(mask[j]);
         }
     }
     const long long before = block_sum_range(g.chunk_cnt_link, first, cm.y);
     int total;
-    const int pos = block_excl_scan(nl, &total);
-    if (nl) {
+    long long at = before + block_excl_scan(nl, &total);
+#pragma unroll
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        if (!mask[j]) continue;
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
         double d[3];
+        float df[3];
         if (p.exact) disp(p, XL, rc.x, rc.y, rc.z, d);
-        long long at = before + pos;
+        else frame_disp_f(p, F, rc.x, rc.y, rc.z, df);
         for (int i = 1; i < L::Q; ++i) {
-            if (!(mask & (1u << i))) continue;
+            if (!(mask[j] & (1u << i))) continue;
             if (at < B.link_cap) {
-                const long long j = B.link_off + at;
-                g.Lcell[j] = (uint32_t)rc.cell;
-                g.Ldir[j] = (uint8_t)i;
-                g.Ldelta[j] = p.exact ? link_delta(B, d, L::cx(i), L::cy(i), L::cz(i))
-                                      : (double)link_delta_f(B, df, L::cx(i), L::cy(i), L::cz(i));
+                const long long jj = B.link_off + at;
+                g.Lcell[jj] = (uint32_t)rc.cell;
+                g.Ldir[jj] = (uint8_t)i;
+                g.Ldelta[jj] = p.exact ? link_delta(B, d, L::cx(i), L::cy(i), L::cz(i))
+                                       : (double)link_delta_f(B, df, L::cx(i), L::cy(i), L::cz(i));
             }
             at++;
         }

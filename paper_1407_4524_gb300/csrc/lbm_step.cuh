@@ -598,18 +598,25 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
             for (int c = 0; c < ME_PER_LINK; ++c) sb.me[c * st + j] = out[c];
         }
     } else {
-        const long long tiles = sb.tile_pre[p.nb];
+        // tile -> body map in shared memory (binary search), global beyond 1024 bodies
+        __shared__ long long tp_s[1025];
+        const bool in_smem = p.nb < 1025;
+        if (in_smem)
+            for (int k = threadIdx.x; k <= p.nb; k += blockDim.x) tp_s[k] = sb.tile_pre[k];
+        __syncthreads();
+        const long long *tp = in_smem ? tp_s : sb.tile_pre;
+        const long long tiles = tp[p.nb];
         const int lane = threadIdx.x & 31;
         for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
             int b = 0, hi = p.nb;
             while (hi - b > 1) {
                 const int mid = (b + hi) >> 1;
-                if (sb.tile_pre[mid] <= tile) b = mid;
+                if (tp[mid] <= tile) b = mid;
                 else hi = mid;
             }
             const BodyDev &B = sb.bodies[b];
             const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;
-            const long long k = (tile - sb.tile_pre[b]) * LINK_THREADS + threadIdx.x;
+            const long long k = (tile - tp[b]) * LINK_THREADS + threadIdx.x;
             const long long cnt = sb.link_cnt[b];
             const long long warp_first = k - lane;
             if (warp_first >= cnt) continue; // whole warp past the body's links
