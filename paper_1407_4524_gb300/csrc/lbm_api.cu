@@ -110,6 +110,10 @@ struct lbm_domain {
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
+    // side stream: in the reduced-precision modes the geometry of t+1 and the
+    // end-of-step kernel run on it, concurrently with the bulk kernel
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_prep = nullptr, ev_links = nullptr, ev_side = nullptr;
     // timing of the bulk kernel
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -370,10 +374,15 @@ int upload_bodies(lbm_domain *D) {
     return LBM_OK;
 }
 
+int do_step_overlapped(lbm_domain *D);
+
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
+    if (prec != LBM_FP64 && D->nb) return do_step_overlapped(D);
     if (D->nb && (D->n_moving || D->prep_dirty)) {
-        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t, D->s));
+        // the A+/A- lists of the previous step update the solid flags of t
+        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
+                       D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
         D->prep_dirty = false;
     }
     if (D->n_moving) {
@@ -400,6 +409,54 @@ int do_step(lbm_domain *D) {
         D->ev_used += 2;
     }
     if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
+    D->t += 1;
+    return LBM_OK;
+}
+
+// Reduced-precision modes.  Stream s: prep -> links -> bulk; side stream:
+// (after prep) geometry of t+1, (after links) end-of-step kernel.  The bulk
+// kernel reads only fhat(t) (with the wall values written by the link
+// kernel) and the solid flags of t; the geometry writes the owner and link
+// buffers of t+1 and the covered/uncovered lists, the end-of-step kernel the
+// series row, the refilled nodes (solid at t, skipped by the bulk kernel) and
+// the fixed-point accumulators, so the two streams touch disjoint data.
+int do_step_overlapped(lbm_domain *D) {
+    const int Q = D->Q, prec = D->prec;
+    if (D->n_moving || D->prep_dirty) {
+        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
+                       D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
+        D->prep_dirty = false;
+    }
+    if (D->n_moving) {
+        CK(cudaEventRecord(D->ev_prep, D->s));
+        CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
+        GeomArgs g = geom_args(D, true);
+        CK(launch_geom_a(Q, D->p, g, D->s2));
+        CK(launch_geom_b(Q, D->p, g, D->s2));
+        CK(launch_geom_c(Q, D->p, g, D->s2));
+    }
+    StepBufs sb = step_bufs(D);
+    CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
+    CK(cudaEventRecord(D->ev_links, D->s));
+    if (D->timing) {
+        if (D->ev_used + 2 > D->ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                D->ev.push_back(e);
+            }
+        }
+        CK(cudaEventRecord(D->ev[D->ev_used], D->s));
+    }
+    CK(launch_bulk(Q, prec, D->p, sb, D->s));
+    if (D->timing) {
+        CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
+        D->ev_used += 2;
+    }
+    CK(cudaStreamWaitEvent(D->s2, D->ev_links, 0));
+    CK(launch_finish(Q, prec, D->p, sb, D->s2));
+    CK(cudaEventRecord(D->ev_side, D->s2));
+    CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
     D->t += 1;
     return LBM_OK;
 }
@@ -504,6 +561,11 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
     if ((rc = alloc_t(D, &D->counters, 4, nullptr))) return bail(rc);
+    if ((e = cudaStreamCreateWithFlags(&D->s2, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&D->ev_prep, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&D->ev_links, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&D->ev_side, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(fail(LBM_ERR_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e)));
     if ((e = launch_flags_full(D->Q, p, D->owner[0], D->flags, D->s)) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, std::string("flags: ") + cudaGetErrorString(e)));
     if ((rc = init_populations(D))) return bail(rc);
@@ -525,6 +587,13 @@ int lbm_destroy_domain(lbm_domain *D) {
     D->release(D->flags);
     D->release(D->counters);
     for (cudaEvent_t e : D->ev) cudaEventDestroy(e);
+    if (D->s2) {
+        cudaStreamSynchronize(D->s2);
+        cudaStreamDestroy(D->s2);
+    }
+    if (D->ev_prep) cudaEventDestroy(D->ev_prep);
+    if (D->ev_links) cudaEventDestroy(D->ev_links);
+    if (D->ev_side) cudaEventDestroy(D->ev_side);
     delete D;
     return LBM_OK;
 }
@@ -587,7 +656,8 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     // solid owners at t = 0, flags, links (both buffers), initial state
     const size_t N = (size_t)D->p.N;
     CK(cudaMemsetAsync(D->owner[0], 0, N * sizeof(uint16_t), D->s));
-    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, D->s));
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr,
+                   nullptr, nullptr, D->s));
     GeomArgs g = geom_args(D, false);
     CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
     CK(cudaMemcpyAsync(D->owner[1], D->owner[0], N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
@@ -599,7 +669,8 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     CK(cudaMemcpyAsync(D->Ldir[1], D->Ldir[0], L, cudaMemcpyDeviceToDevice, D->s));
     CK(cudaMemcpyAsync(D->Ldelta[1], D->Ldelta[0], L * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
     CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice, D->s));
-    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, D->s));
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr,
+                   nullptr, nullptr, D->s));
     D->prep_dirty = false;
     if ((rc = init_populations(D))) return rc;
     CK(cudaStreamSynchronize(D->s));
@@ -782,7 +853,7 @@ int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
 
 int lbm_launches_per_step(const lbm_domain *D, int *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
-    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0);
+    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
     return LBM_OK;
 }
 

@@ -167,9 +167,24 @@ __device__ void prefix_over_bodies(const Params &p, const long long *link_cnt, l
     __syncthreads();
 }
 
-// wrapped poses at t and t+1, prefixes of link counts and link tiles
+// wrapped poses at t and t+1, prefixes of link counts and link tiles, and
+// the solid flags of the nodes that the previous step covered (A+) or
+// uncovered (A-), so that the flags describe the solid set of step t
 __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, const long long *link_cnt,
-                                               long long *link_pre, long long *tile_pre, double *poses, long long t) {
+                                               long long *link_pre, long long *tile_pre, double *poses, long long t,
+                                               uint8_t *flags, const long long *apm_cnt, const uint32_t *apm_cell,
+                                               const int8_t *apm_sign) {
+    if (flags) {
+        for (int b = 0; b < p.nb; ++b) {
+            const BodyDev &B = bodies[b];
+            const long long n = apm_cnt[b];
+            for (long long e = threadIdx.x; e < n; e += 1024) {
+                const long long c = apm_cell[B.apm_off + e];
+                flags[c] = (uint8_t)((flags[c] & ~FL_SOLID) | (apm_sign[B.apm_off + e] > 0 ? FL_SOLID : 0));
+            }
+        }
+        __syncthreads();
+    }
     prefix_over_bodies(p, link_cnt, link_pre, 0);
     prefix_over_bodies(p, link_cnt, tile_pre, 1);
     for (int b = threadIdx.x; b < p.nb; b += 1024) {
@@ -398,8 +413,10 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
 } // namespace
 
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
-                        long long *tile_pre, double *poses, long long t, cudaStream_t s) {
-    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, tile_pre, poses, t);
+                        long long *tile_pre, double *poses, long long t, uint8_t *flags, const long long *apm_cnt,
+                        const uint32_t *apm_cell, const int8_t *apm_sign, cudaStream_t s) {
+    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, tile_pre, poses, t, flags, apm_cnt, apm_cell,
+                              apm_sign);
     return cudaGetLastError();
 }
 

@@ -41,7 +41,8 @@ cudaError_t launch_finish(int Q, int prec, const Params &p, const StepBufs &sb, 
 
 // per step: wrapped poses at t and t+1 and the prefix of the link counts
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
-                        long long *tile_pre, double *poses, long long t, cudaStream_t s);
+                        long long *tile_pre, double *poses, long long t, uint8_t *flags, const long long *apm_cnt,
+                        const uint32_t *apm_cell, const int8_t *apm_sign, cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,

@@ -836,7 +836,6 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
             atomicAdd(&acc_s[a], to_fx(sg * m[a]));
             atomicAdd(&acc_s[3 + a], to_fx(sg * tq[a]));
         }
-        sb.flags[A] = (uint8_t)((sb.flags[A] & ~FL_SOLID) | (s > 0 ? FL_SOLID : 0));
     }
     __syncthreads();
     if (threadIdx.x < 6) {
