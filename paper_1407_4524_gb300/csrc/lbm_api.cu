@@ -561,7 +561,11 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
     if ((rc = alloc_t(D, &D->counters, 4, nullptr))) return bail(rc);
-    if ((e = cudaStreamCreateWithFlags(&D->s2, cudaStreamNonBlocking)) != cudaSuccess ||
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    // high priority: blocks of the short side-stream kernels are dispatched
+    // as soon as bulk-kernel blocks retire, instead of after the whole grid
+    if ((e = cudaStreamCreateWithPriority(&D->s2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&D->ev_prep, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&D->ev_links, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&D->ev_side, cudaEventDisableTiming)) != cudaSuccess)
