@@ -107,6 +107,10 @@ struct lbm_domain {
     long long *link_pre = nullptr;
     long long *tile_pre = nullptr;
     unsigned long long *acc = nullptr;
+    unsigned long long *chg_cnt = nullptr;
+    uint32_t *chg_cell = nullptr;
+    uint8_t *chg_val = nullptr;
+    long long chg_cap = 0;
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -174,6 +178,10 @@ void free_body_buffers(lbm_domain *D) {
     D->link_pre = nullptr;
     D->tile_pre = nullptr;
     D->acc = nullptr;
+    D->chg_cnt = nullptr;
+    D->chg_cell = nullptr;
+    D->chg_val = nullptr;
+    D->chg_cap = 0;
     D->prep_dirty = true;
     D->nb = D->n_moving = 0;
     D->nchunk_all = D->nchunk_mov = 0;
@@ -334,6 +342,10 @@ GeomArgs geom_args(lbm_domain *D, bool moving_step) {
     g.t = D->t;
     g.t_link = moving_step ? D->t + 1 : D->t;
     g.do_apm = moving_step ? 1 : 0;
+    g.chg_cnt = D->chg_cnt;
+    g.chg_cell = D->chg_cell;
+    g.chg_val = D->chg_val;
+    g.chg_cap = D->chg_cap;
     g.do_flags = (moving_step && D->prec == LBM_FP64) ? 1 : 0;
     return g;
 }
@@ -413,31 +425,36 @@ int do_step(lbm_domain *D) {
     return LBM_OK;
 }
 
-// Reduced-precision modes.  Stream s: prep -> links -> bulk; side stream:
-// (after prep) geometry of t+1, (after links) end-of-step kernel.  The bulk
-// kernel reads only fhat(t) (with the wall values written by the link
-// kernel) and the solid flags of t; the geometry writes the owner and link
-// buffers of t+1 and the covered/uncovered lists, the end-of-step kernel the
-// series row, the refilled nodes (solid at t, skipped by the bulk kernel) and
-// the fixed-point accumulators, so the two streams touch disjoint data.
+// Reduced-precision modes.  Stream s: prep -> bulk (every fluid node that is
+// not a boundary node).  Side stream, after prep: owner and flag changes of
+// t+1 (moving bodies), the boundary-node kernel (cut links, momentum
+// exchange, collision of the boundary nodes) and the end-of-step kernel
+// (series row, impulsive terms, refill).  The bulk kernel reads fhat(t) and
+// the flags of t and writes fhat(t+1) of the non-boundary fluid nodes; the
+// side stream writes fhat(t+1) of the boundary and refilled nodes, the owner
+// array of t+1, the lists and the accumulators: the two streams touch
+// disjoint data.  Flag changes are applied by the next prep.
 int do_step_overlapped(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     if (D->n_moving || D->prep_dirty) {
-        CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
-                       D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
+        CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->flags, D->chg_cnt, D->chg_cell, D->chg_val, D->chg_cap,
+                        D->apm_cnt, D->s));
         D->prep_dirty = false;
     }
-    if (D->n_moving) {
-        CK(cudaEventRecord(D->ev_prep, D->s));
-        CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
-        GeomArgs g = geom_args(D, true);
-        CK(launch_geom_a(Q, D->p, g, D->s2));
-        CK(launch_geom_b(Q, D->p, g, D->s2));
-        CK(launch_geom_c(Q, D->p, g, D->s2));
-    }
+    CK(cudaEventRecord(D->ev_prep, D->s));
+    CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
     StepBufs sb = step_bufs(D);
-    CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
-    CK(cudaEventRecord(D->ev_links, D->s));
+    GeomArgs g = geom_args(D, true);
+    if (D->n_moving) {
+        CK(launch_fgeom1(Q, D->p, g, D->s2));
+        CK(launch_fgeom2(Q, D->p, g, D->s2));
+    }
+    GeomArgs ga = g;
+    ga.chunk_map = D->chunk_all;
+    ga.nchunks = D->nchunk_all;
+    CK(launch_bnd(Q, prec, D->p, ga, sb, D->s2));
+    CK(launch_finish(Q, prec, D->p, sb, D->s2));
+    CK(cudaEventRecord(D->ev_side, D->s2));
     if (D->timing) {
         if (D->ev_used + 2 > D->ev.size()) {
             for (int k = 0; k < 64; ++k) {
@@ -453,9 +470,6 @@ int do_step_overlapped(lbm_domain *D) {
         CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
         D->ev_used += 2;
     }
-    CK(cudaStreamWaitEvent(D->s2, D->ev_links, 0));
-    CK(launch_finish(Q, prec, D->p, sb, D->s2));
-    CK(cudaEventRecord(D->ev_side, D->s2));
     CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
     D->t += 1;
     return LBM_OK;
@@ -560,7 +574,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
         if ((rc = alloc_t(D, &D->owner[k], N, nullptr))) return bail(rc);
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
-    if ((rc = alloc_t(D, &D->counters, 4, nullptr))) return bail(rc);
+    if ((rc = alloc_t(D, &D->counters, 8, nullptr))) return bail(rc);
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     // high priority: blocks of the short side-stream kernels are dispatched
@@ -651,6 +665,10 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->link_pre, nbx + 1, &T))) return rc;
     if ((rc = alloc_t(D, &D->tile_pre, nbx + 1, &T))) return rc;
     if ((rc = alloc_t(D, &D->acc, nbx * SERIES_ROW, &T))) return rc;
+    D->chg_cap = std::max<long long>(aoff, 1);
+    if ((rc = alloc_t(D, &D->chg_cnt, 1, &T))) return rc;
+    if ((rc = alloc_t(D, &D->chg_cell, (size_t)D->chg_cap, &T))) return rc;
+    if ((rc = alloc_t(D, &D->chg_val, (size_t)D->chg_cap, &T))) return rc;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
     (void)maxcnt;
@@ -801,7 +819,7 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
     std::memset(out, 0, sizeof(*out));
     CK(cudaStreamSynchronize(D->s));
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     CK(cudaMemcpy(c, D->counters, sizeof(c), cudaMemcpyDeviceToHost));
     out->step = D->t;
     out->cells = D->p.N;
@@ -811,7 +829,9 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     out->device_bytes = (int64_t)D->bytes;
     out->h2d_bytes = D->h2d;
     out->d2h_bytes = D->d2h;
-    if (D->nb) {
+    if (D->nb && D->prec != LBM_FP64 && D->t > 0) {
+        out->links = (int64_t)c[4]; // counted by the boundary-node kernel in the last step
+    } else if (D->nb) {
         std::vector<long long> lc(D->nb);
         CK(cudaMemcpy(lc.data(), D->link_cnt[D->t & 1], sizeof(long long) * D->nb, cudaMemcpyDeviceToHost));
         for (long long v : lc) out->links += v;
@@ -857,7 +877,10 @@ int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
 
 int lbm_launches_per_step(const lbm_domain *D, int *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
-    *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
+    if (D->prec != LBM_FP64 && D->nb)
+        *out = 3 + (D->n_moving ? 3 : (D->prep_dirty ? 1 : 0)); // bulk, bnd, finish (+ prep, geometry)
+    else
+        *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
     return LBM_OK;
 }
 

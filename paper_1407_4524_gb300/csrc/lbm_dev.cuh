@@ -19,7 +19,9 @@
 namespace lbm {
 
 constexpr uint8_t FL_SOLID = 1; // node inside a body at time t
-constexpr uint8_t FL_MAC = 2;   // store rho,u of f(t+1) at this node
+constexpr uint8_t FL_MAC = 2;   // store rho,u of f(t+1) at this node (FP64 mode)
+constexpr uint8_t FL_BND = 4;   // fluid node with a solid neighbour at t (handled by
+                                // the boundary-node kernel in the reduced-precision modes)
 
 constexpr int SERIES_ROW = 18;  // Fs Ts Fi Ti Fm Tm
 constexpr int ME_PER_LINK = 12; // Fs Ts Fm Tm contributions of one link

@@ -1,6 +1,7 @@
 // lbm_fp32.cu -- reduced-precision modes: FP32 arithmetic with populations
 // stored as deviations f - w in FP32 (p1) or FP16 (p2).
 #include "lbm_launch.cuh"
+#include "lbm_bnd.cuh"
 
 namespace lbm {
 
@@ -21,6 +22,11 @@ cudaError_t launch_bulk_p12(int Q, int prec, const Params &p, const StepBufs &sb
 cudaError_t launch_finish_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s) {
     if (prec == 1) return Q == 9 ? finish_t<Lat<9>, PF32>(p, sb, s) : finish_t<Lat<19>, PF32>(p, sb, s);
     return Q == 9 ? finish_t<Lat<9>, PF16>(p, sb, s) : finish_t<Lat<19>, PF16>(p, sb, s);
+}
+
+cudaError_t launch_bnd(int Q, int prec, const Params &p, const GeomArgs &g, const StepBufs &sb, cudaStream_t s) {
+    if (prec == 1) return Q == 9 ? bnd_t<Lat<9>, PF32>(p, g, sb, s) : bnd_t<Lat<19>, PF32>(p, g, sb, s);
+    return Q == 9 ? bnd_t<Lat<9>, PF16>(p, g, sb, s) : bnd_t<Lat<19>, PF16>(p, g, sb, s);
 }
 
 } // namespace lbm

@@ -11,6 +11,7 @@
 // direction order) whatever the launch configuration: the FP64 mode can then
 // sum link contributions in exactly the oracle's order.
 #include "lbm_internal.h"
+#include "lbm_region.cuh"
 
 namespace lbm {
 
@@ -60,72 +61,24 @@ __device__ __forceinline__ long long block_sum_range(const int *cnt, int first, 
     return r;
 }
 
-struct RegionCell {
-    bool valid;
-    int x, y, z;
-    long long cell;
-};
-
-// the j-th (0..GEOM_CELLS-1) region cell of this thread in chunk `chunk`:
-// a thread owns GEOM_CELLS consecutive cells, so per-thread counts followed
-// by a block scan keep every list in cell order
-__device__ __forceinline__ RegionCell region_cell(const Params &p, const BodyDev &B, const int lo[3], int chunk,
-                                                  int j) {
-    RegionCell rc{false, 0, 0, 0, 0};
-    const int e0 = B.ext[0], e1 = B.ext[1];
-    const int vol = e0 * e1 * B.ext[2];
-    const int k = chunk * GEOM_CHUNK + (int)threadIdx.x * GEOM_CELLS + j;
-    if (k >= vol) return rc;
-    const int kz = k / (e0 * e1);
-    const int rem = k - kz * e0 * e1;
-    const int ky = rem / e0;
-    const int kx = rem - ky * e0;
-    rc.x = region_axis(kx, lo[0], e0, p.nx, p.per[0]);
-    rc.y = region_axis(ky, lo[1], e1, p.ny, p.per[1]);
-    rc.z = region_axis(kz, lo[2], B.ext[2], p.nz, p.per[2]);
-    if (rc.x < 0 || rc.y < 0 || rc.z < 0) return rc;
-    rc.valid = true;
-    rc.cell = cell_of(p, rc.x, rc.y, rc.z);
-    return rc;
-}
-
-// neighbour x - k c_i; -1 if it falls outside a non-periodic axis
-template <class L>
-__device__ __forceinline__ long long nbr(const Params &p, int x, int y, int z, int i, int k) {
-    int q[3] = {x - k * L::cx(i), y - k * L::cy(i), z - k * L::cz(i)};
-    const int n[3] = {p.nx, p.ny, p.nz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (q[a] >= 0 && q[a] < n[a]) continue;
-        if (!p.per[a]) return -1;
-        while (q[a] < 0) q[a] += n[a]; // |k c_i| <= 2: at most two turns
-        while (q[a] >= n[a]) q[a] -= n[a];
-    }
-    return cell_of(p, q[0], q[1], q[2]);
-}
-
-__device__ __forceinline__ bool edge_node(const Params &p, int x, int y, int z) {
-    return (!p.per[0] && (x == 0 || x == p.nx - 1)) || (!p.per[1] && (y == 0 || y == p.ny - 1)) ||
-           (!p.per[2] && (z == 0 || z == p.nz - 1));
-}
-
-// store macros at x if x is fluid and within two hops of a solid node (the
-// fluid end of a cut link, or its u_G node), or on a non-periodic face
 template <class L>
 __device__ __forceinline__ uint8_t node_flags(const Params &p, const uint16_t *owner_t, const uint16_t *owner_m,
                                               int x, int y, int z, long long cell) {
     const uint8_t f = owner_t[cell] ? FL_SOLID : 0;
     if (owner_m[cell]) return f;
-    if (edge_node(p, x, y, z)) return f | FL_MAC;
     // all neighbour loads are independent (no early exit), so they overlap
-    unsigned any = 0;
+    unsigned one = 0, two = 0;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
         const long long a = nbr<L>(p, x, y, z, i, 1);
         const long long b = nbr<L>(p, x, y, z, i, 2);
-        any |= (a >= 0 ? owner_m[a] : 0u) | (b >= 0 ? owner_m[b] : 0u);
+        one |= (a >= 0 ? owner_m[a] : 0u);
+        two |= (b >= 0 ? owner_m[b] : 0u);
     }
-    return f | (any ? FL_MAC : 0);
+    uint8_t r = f;
+    if (one | two || edge_node(p, x, y, z)) r |= FL_MAC;
+    if (one && !owner_t[cell]) r |= FL_BND;
+    return r;
 }
 
 // exclusive prefix over bodies of v(b) = link_cnt[b] (tiles = 0) or of the
@@ -198,12 +151,6 @@ __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, 
             P[15 + a] = P[3 + a] - P[12 + a];
         }
     }
-}
-
-__device__ __forceinline__ float frame_dist(const Params &p, const BodyDev &B, const Frame &F, const RegionCell &rc) {
-    float d[3];
-    frame_disp_f(p, F, rc.x, rc.y, rc.z, d);
-    return sqrtf(d[0] * d[0] + d[1] * d[1] + (B.shape == 1 ? d[2] * d[2] : 0.0f));
 }
 
 __global__ void __launch_bounds__(GEOM_THREADS) k_raster(Params p, GeomArgs g, uint16_t *owner, long long) {
@@ -410,6 +357,107 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
     }
 }
 
+
+// ----------------------------------------------------------------------------
+// Reduced-precision modes.  Momentum-exchange sums are order independent
+// there (exact fixed point), so lists are appended with atomics.
+
+__global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies, double *poses, long long t,
+                                                uint8_t *flags, unsigned long long *chg_cnt, const uint32_t *chg_cell,
+                                                const uint8_t *chg_val, long long chg_cap, long long *apm_cnt) {
+    const long long n = (long long)min((unsigned long long)chg_cap, *chg_cnt);
+    for (long long e = threadIdx.x; e < n; e += 1024) {
+        const long long c = chg_cell[e];
+        flags[c] = (uint8_t)((flags[c] & ~(FL_SOLID | FL_BND)) | chg_val[e]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *chg_cnt = 0ull;
+    for (int b = threadIdx.x; b < p.nb; b += 1024) {
+        apm_cnt[b] = 0;
+        double *P = poses + (long long)b * POSE_STRIDE;
+        pose(bodies[b], t, P);
+        wrap_pose(p, P, P + 3);
+        pose(bodies[b], t + 1, P + 6);
+        wrap_pose(p, P + 6, P + 9);
+        for (int a = 0; a < 3; ++a) {
+            P[12 + a] = floor(P[3 + a]);
+            P[15 + a] = P[3 + a] - P[12 + a];
+        }
+    }
+}
+
+// owner at t+1 in the shell R-2 <= |x - X(t+1)| <= R+2, A+/A- appended
+__global__ void __launch_bounds__(GEOM_THREADS) k_fgeom1(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(P + 9, F);
+    __syncthreads();
+    int lo[3];
+    region_lo(p, B, P, REGION_MARGIN, lo);
+    const uint16_t me = (uint16_t)(b + 1);
+    const float R = (float)B.R;
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        const float dist = frame_dist(p, B, F, rc);
+        if (dist < R - 2.0f || dist > R + 2.0f) continue;
+        const bool in_t = g.owner_t[rc.cell] == me;
+        const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
+        if (in1) g.owner_t1[rc.cell] = me;
+        else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
+        if (in_t != in1) {
+            const unsigned long long at = atomicAdd((unsigned long long *)&g.apm_cnt[b], 1ull);
+            if ((long long)at < B.apm_cap) {
+                g.apm_cell[B.apm_off + at] = (uint32_t)rc.cell;
+                g.apm_sign[B.apm_off + at] = (int8_t)(in1 ? 1 : -1);
+            }
+        }
+    }
+}
+
+// flags of t+1 (solid, boundary node) in the shell R-2 .. R+3; changes appended
+template <class L>
+__global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(P + 9, F);
+    __syncthreads();
+    int lo[3];
+    region_lo(p, B, P, REGION_MARGIN, lo);
+    const float R = (float)B.R;
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        const float dist = frame_dist(p, B, F, rc);
+        if (dist < R - 2.0f || dist > R + 3.0f) continue;
+        uint8_t nf;
+        if (g.owner_t1[rc.cell]) {
+            nf = FL_SOLID;
+        } else {
+            unsigned one = 0;
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                one |= (a >= 0 ? g.owner_t1[a] : 0u);
+            }
+            nf = one ? FL_BND : 0;
+        }
+        if ((g.flags[rc.cell] & (FL_SOLID | FL_BND)) != nf) {
+            const unsigned long long at = atomicAdd(g.chg_cnt, 1ull);
+            if ((long long)at < g.chg_cap) {
+                g.chg_cell[at] = (uint32_t)rc.cell;
+                g.chg_val[at] = nf;
+            }
+        }
+    }
+}
+
 } // namespace
 
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
@@ -417,6 +465,26 @@ cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long 
                         const uint32_t *apm_cell, const int8_t *apm_sign, cudaStream_t s) {
     k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, tile_pre, poses, t, flags, apm_cnt, apm_cell,
                               apm_sign);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t, uint8_t *flags,
+                         unsigned long long *chg_cnt, const uint32_t *chg_cell, const uint8_t *chg_val,
+                         long long chg_cap, long long *apm_cnt, cudaStream_t s) {
+    k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fgeom1(int, const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    k_fgeom1<<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    if (Q == 9) k_fgeom2<Lat<9>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    else k_fgeom2<Lat<19>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,11 @@ struct GeomArgs {
     long long t_link; // pose time of the links being built
     int do_apm;       // covered/uncovered lists (moving step)
     int do_flags;     // rewrite flags in the regions
+    // reduced-precision modes: flag changes for t+1, applied by the next prep
+    unsigned long long *chg_cnt;
+    uint32_t *chg_cell;
+    uint8_t *chg_val;
+    long long chg_cap;
 };
 
 // precision: 0 FP64, 1 FP32, 2 FP16; Q: 9 or 19
@@ -43,6 +48,11 @@ cudaError_t launch_finish(int Q, int prec, const Params &p, const StepBufs &sb, 
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
                         long long *tile_pre, double *poses, long long t, uint8_t *flags, const long long *apm_cnt,
                         const uint32_t *apm_cell, const int8_t *apm_sign, cudaStream_t s);
+// reduced-precision modes: poses, and the flag changes of the previous step;
+// clears the change list and the covered/uncovered counters
+cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t, uint8_t *flags,
+                         unsigned long long *chg_cnt, const uint32_t *chg_cell, const uint8_t *chg_val,
+                         long long chg_cap, long long *apm_cnt, cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,
@@ -51,6 +61,12 @@ cudaError_t launch_geom_a(int Q, const Params &p, const GeomArgs &g, cudaStream_
 cudaError_t launch_geom_b(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 cudaError_t launch_geom_c(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 cudaError_t launch_flags_full(int Q, const Params &p, const uint16_t *owner, uint8_t *flags, cudaStream_t s);
+// reduced-precision modes: owner(t+1) + unordered A+/A- lists; flag changes
+cudaError_t launch_fgeom1(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
+cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
+// reduced-precision modes: boundary nodes of every body (pull, wall values,
+// momentum exchange, collision) -- runs beside k_bulk
+cudaError_t launch_bnd(int Q, int prec, const Params &p, const GeomArgs &g, const StepBufs &sb, cudaStream_t s);
 
 // population export: fhat as FP64 f (adds w back for the shifted modes)
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);

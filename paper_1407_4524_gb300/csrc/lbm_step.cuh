@@ -58,7 +58,8 @@ struct StepBufs {
     const int8_t *apm_sign;
     double *imp;
     double *series;
-    unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered
+    unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered,
+                                  // [3] links of this step, [4] links of the last step
     unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
 };
@@ -369,6 +370,9 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename 
     const long long cell = cell_of(p, x, y, z);
     const uint8_t fl = __ldg(flags + cell);
     if (fl & FL_SOLID) return;
+    if constexpr (!P::exact) {
+        if (fl & FL_BND) return; // boundary nodes: k_bnd
+    }
     C f[L::Q];
     pull_all<L, P>(p, src, mac_t, x, y, z, cell, f);
     if constexpr (P::exact) {
@@ -780,7 +784,11 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
         float m[3] = {0.f, 0.f, 0.f};
         float f[L::Q];
         if (s > 0) { // covered: the streamed values f_i(A, t+1)
-            pull_all<L, P>(p, src, (const float *)nullptr, x, y, z, A, f);
+            if (sb.flags[A] & FL_BND) { // a boundary node at t: kept by k_bnd
+                for (int i = 0; i < L::Q; ++i) f[i] = ldP(dst + (long long)i * p.N + A);
+            } else {
+                pull_all<L, P>(p, src, (const float *)nullptr, x, y, z, A, f);
+            }
             atomicAdd(&sb.counters[1], 1ull);
         } else { // uncovered: refill f(A, t+1) = f^eq(rho_bar, u_B or u_bar)
             double r1[3], uBd[3];
@@ -869,6 +877,10 @@ template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &
 // blocks [nb, nb + moving) handle the covered/uncovered nodes of one moving
 // body (they write disjoint parts of the series row)
 template <class L, class P> __global__ void __launch_bounds__(IMP_THREADS) k_finish(Params p, StepBufs sb) {
+    if (!P::exact && blockIdx.x == 0 && threadIdx.x == 0) {
+        sb.counters[4] = sb.counters[3];
+        sb.counters[3] = 0ull;
+    }
     if ((int)blockIdx.x < p.nb) {
         reduce_body<P::exact>(p, sb, blockIdx.x);
         return;
