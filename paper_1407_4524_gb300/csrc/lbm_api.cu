@@ -111,6 +111,12 @@ struct lbm_domain {
     uint32_t *chg_cell = nullptr;
     uint8_t *chg_val = nullptr;
     long long chg_cap = 0;
+    uint32_t *bn_static = nullptr;
+    uint32_t *bn_mov[2] = {nullptr, nullptr};
+    unsigned long long *bn_cnt = nullptr; // [0] static, [1], [2] moving lists of even / odd steps
+    long long bn_static_cap = 0, bn_mov_cap = 0;
+    bool lists_dirty = true;
+    int bnd_grid = 0;
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -182,6 +188,11 @@ void free_body_buffers(lbm_domain *D) {
     D->chg_cell = nullptr;
     D->chg_val = nullptr;
     D->chg_cap = 0;
+    D->bn_static = nullptr;
+    D->bn_mov[0] = D->bn_mov[1] = nullptr;
+    D->bn_cnt = nullptr;
+    D->bn_static_cap = D->bn_mov_cap = 0;
+    D->lists_dirty = true;
     D->prep_dirty = true;
     D->nb = D->n_moving = 0;
     D->nchunk_all = D->nchunk_mov = 0;
@@ -346,6 +357,12 @@ GeomArgs geom_args(lbm_domain *D, bool moving_step) {
     g.chg_cell = D->chg_cell;
     g.chg_val = D->chg_val;
     g.chg_cap = D->chg_cap;
+    g.bn_static = D->bn_static;
+    g.bn_static_cnt = D->bn_cnt;
+    g.bn_mov = D->bn_mov[nxt];
+    g.bn_mov_cnt = D->bn_cnt + 1 + nxt;
+    g.bn_static_cap = D->bn_static_cap;
+    g.bn_mov_cap = D->bn_mov_cap;
     g.do_flags = (moving_step && D->prec == LBM_FP64) ? 1 : 0;
     return g;
 }
@@ -436,10 +453,19 @@ int do_step(lbm_domain *D) {
 // disjoint data.  Flag changes are applied by the next prep.
 int do_step_overlapped(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
-    if (D->n_moving || D->prep_dirty) {
+    const int cur = (int)(D->t & 1), nxt = cur ^ 1;
+    if (D->n_moving || D->prep_dirty || D->lists_dirty) {
         CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->flags, D->chg_cnt, D->chg_cell, D->chg_val, D->chg_cap,
-                        D->apm_cnt, D->s));
+                        D->apm_cnt, D->bn_cnt + 1 + nxt, D->s));
         D->prep_dirty = false;
+    }
+    if (D->lists_dirty) { // boundary-node lists of step t from scratch
+        CK(cudaMemsetAsync(D->bn_cnt, 0, 3 * sizeof(unsigned long long), D->s));
+        GeomArgs gl = geom_args(D, false);
+        gl.bn_mov = D->bn_mov[cur];
+        gl.bn_mov_cnt = D->bn_cnt + 1 + cur;
+        CK(launch_bnd_lists(Q, D->p, gl, D->s));
+        D->lists_dirty = false;
     }
     CK(cudaEventRecord(D->ev_prep, D->s));
     CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
@@ -449,10 +475,18 @@ int do_step_overlapped(lbm_domain *D) {
         CK(launch_fgeom1(Q, D->p, g, D->s2));
         CK(launch_fgeom2(Q, D->p, g, D->s2));
     }
-    GeomArgs ga = g;
-    ga.chunk_map = D->chunk_all;
-    ga.nchunks = D->nchunk_all;
-    CK(launch_bnd(Q, prec, D->p, ga, sb, D->s2));
+    BndArgs ba{};
+    ba.static_cells = D->bn_static;
+    ba.static_cnt = D->bn_cnt;
+    ba.mov_cells = D->bn_mov[cur];
+    ba.mov_cnt = D->bn_cnt + 1 + cur;
+    ba.static_cap = D->bn_static_cap;
+    ba.mov_cap = D->bn_mov_cap;
+    ba.owner_t = D->owner[cur];
+    ba.owner_t1 = D->owner[nxt];
+    ba.bodies = D->dbodies;
+    ba.poses = D->poses;
+    CK(launch_bnd(Q, prec, D->p, ba, sb, D->bnd_grid, D->s2));
     CK(launch_finish(Q, prec, D->p, sb, D->s2));
     CK(cudaEventRecord(D->ev_side, D->s2));
     if (D->timing) {
@@ -669,6 +703,23 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->chg_cnt, 1, &T))) return rc;
     if ((rc = alloc_t(D, &D->chg_cell, (size_t)D->chg_cap, &T))) return rc;
     if ((rc = alloc_t(D, &D->chg_val, (size_t)D->chg_cap, &T))) return rc;
+    // boundary nodes of a body lie in the shell R < |x - X| <= R + sqrt(2):
+    // link_cap / (Q - 1) bounds their number (see link_capacity)
+    long long bns = 0, bnm = 0;
+    for (int b = 0; b < n; ++b) {
+        const long long nodes = D->hbd[b].link_cap / (D->Q - 1) + 64;
+        bns += nodes;
+        if (D->hbd[b].moving) bnm += nodes;
+    }
+    D->bn_static_cap = std::max<long long>(bns, 1);
+    D->bn_mov_cap = std::max<long long>(bns, 1); // bodies may start moving later
+    (void)bnm;
+    if ((rc = alloc_t(D, &D->bn_static, (size_t)D->bn_static_cap, &T))) return rc;
+    if ((rc = alloc_t(D, &D->bn_mov[0], (size_t)D->bn_mov_cap, &T))) return rc;
+    if ((rc = alloc_t(D, &D->bn_mov[1], (size_t)D->bn_mov_cap, &T))) return rc;
+    if ((rc = alloc_t(D, &D->bn_cnt, 3, &T))) return rc;
+    D->bnd_grid = (int)std::max<long long>(1, std::min<long long>(152 * 16, (bns + 7) / 8));
+    D->lists_dirty = true;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
     (void)maxcnt;
@@ -741,6 +792,7 @@ int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
         }
     }
     D->prep_dirty = true;
+    if (maps_changed) D->lists_dirty = true;
     if (maps_changed) return upload_bodies(D);
     return upload_body_array(D);
 }

@@ -24,9 +24,10 @@ cudaError_t launch_finish_p12(int Q, int prec, const Params &p, const StepBufs &
     return Q == 9 ? finish_t<Lat<9>, PF16>(p, sb, s) : finish_t<Lat<19>, PF16>(p, sb, s);
 }
 
-cudaError_t launch_bnd(int Q, int prec, const Params &p, const GeomArgs &g, const StepBufs &sb, cudaStream_t s) {
-    if (prec == 1) return Q == 9 ? bnd_t<Lat<9>, PF32>(p, g, sb, s) : bnd_t<Lat<19>, PF32>(p, g, sb, s);
-    return Q == 9 ? bnd_t<Lat<9>, PF16>(p, g, sb, s) : bnd_t<Lat<19>, PF16>(p, g, sb, s);
+cudaError_t launch_bnd(int Q, int prec, const Params &p, const BndArgs &a, const StepBufs &sb, int grid,
+                       cudaStream_t s) {
+    if (prec == 1) return Q == 9 ? bnd_t<Lat<9>, PF32>(p, a, sb, grid, s) : bnd_t<Lat<19>, PF32>(p, a, sb, grid, s);
+    return Q == 9 ? bnd_t<Lat<9>, PF16>(p, a, sb, grid, s) : bnd_t<Lat<19>, PF16>(p, a, sb, grid, s);
 }
 
 } // namespace lbm

@@ -364,14 +364,18 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
 
 __global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies, double *poses, long long t,
                                                 uint8_t *flags, unsigned long long *chg_cnt, const uint32_t *chg_cell,
-                                                const uint8_t *chg_val, long long chg_cap, long long *apm_cnt) {
+                                                const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
+                                                unsigned long long *bn_mov_next_cnt) {
     const long long n = (long long)min((unsigned long long)chg_cap, *chg_cnt);
     for (long long e = threadIdx.x; e < n; e += 1024) {
         const long long c = chg_cell[e];
         flags[c] = (uint8_t)((flags[c] & ~(FL_SOLID | FL_BND)) | chg_val[e]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) *chg_cnt = 0ull;
+    if (threadIdx.x == 0) {
+        *chg_cnt = 0ull;
+        *bn_mov_next_cnt = 0ull;
+    }
     for (int b = threadIdx.x; b < p.nb; b += 1024) {
         apm_cnt[b] = 0;
         double *P = poses + (long long)b * POSE_STRIDE;
@@ -441,12 +445,20 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
             nf = FL_SOLID;
         } else {
             unsigned one = 0;
+            int minmov = 1 << 20;
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                one |= (a >= 0 ? g.owner_t1[a] : 0u);
+                const unsigned o = a >= 0 ? g.owner_t1[a] : 0u;
+                one |= o;
+                if (o && g.bodies[o - 1].moving) minmov = min(minmov, (int)o);
             }
             nf = one ? FL_BND : 0;
+            // boundary node of t+1 next to a moving body: listed by the lowest one
+            if (minmov == b + 1 && dist <= R + 1.5f) {
+                const unsigned long long at = atomicAdd(g.bn_mov_cnt, 1ull);
+                if ((long long)at < g.bn_mov_cap) g.bn_mov[at] = (uint32_t)rc.cell;
+            }
         }
         if ((g.flags[rc.cell] & (FL_SOLID | FL_BND)) != nf) {
             const unsigned long long at = atomicAdd(g.chg_cnt, 1ull);
@@ -454,6 +466,48 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
                 g.chg_cell[at] = (uint32_t)rc.cell;
                 g.chg_val[at] = nf;
             }
+        }
+    }
+}
+
+
+// boundary-node lists of step t from scratch: nodes next only to static
+// bodies go to the static list, nodes next to a moving body to the moving
+// list of step t (each node once: by the lowest-numbered neighbour body)
+template <class L>
+__global__ void __launch_bounds__(GEOM_THREADS) k_bnd_lists(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(P + 3, F);
+    __syncthreads();
+    int lo[3];
+    region_lo(p, B, P, REGION_MARGIN, lo);
+    const float R = (float)B.R;
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        const float dist = frame_dist(p, B, F, rc);
+        if (dist < R - 0.5f || dist > R + 1.5f || g.owner_t[rc.cell] != 0) continue;
+        int minall = 1 << 20, minmov = 1 << 20;
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+            const unsigned o = a >= 0 ? g.owner_t[a] : 0u;
+            if (!o) continue;
+            minall = min(minall, (int)o);
+            if (g.bodies[o - 1].moving) minmov = min(minmov, (int)o);
+        }
+        if (minmov < (1 << 20)) {
+            if (minmov == b + 1) {
+                const unsigned long long at = atomicAdd(g.bn_mov_cnt, 1ull);
+                if ((long long)at < g.bn_mov_cap) g.bn_mov[at] = (uint32_t)rc.cell;
+            }
+        } else if (minall == b + 1) {
+            const unsigned long long at = atomicAdd(g.bn_static_cnt, 1ull);
+            if ((long long)at < g.bn_static_cap) g.bn_static[at] = (uint32_t)rc.cell;
         }
     }
 }
@@ -470,8 +524,17 @@ cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long 
 
 cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t, uint8_t *flags,
                          unsigned long long *chg_cnt, const uint32_t *chg_cell, const uint8_t *chg_val,
-                         long long chg_cap, long long *apm_cnt, cudaStream_t s) {
-    k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt);
+                         long long chg_cap, long long *apm_cnt, unsigned long long *bn_mov_next_cnt,
+                         cudaStream_t s) {
+    k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt,
+                               bn_mov_next_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    if (Q == 9) k_bnd_lists<Lat<9>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    else k_bnd_lists<Lat<19>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,25 @@ struct GeomArgs {
     uint32_t *chg_cell;
     uint8_t *chg_val;
     long long chg_cap;
+    // reduced-precision modes: boundary-node lists (static bodies; moving
+    // bodies of the step being built)
+    uint32_t *bn_static;
+    unsigned long long *bn_static_cnt;
+    uint32_t *bn_mov;
+    unsigned long long *bn_mov_cnt;
+    long long bn_static_cap, bn_mov_cap;
+};
+
+// arguments of the boundary-node kernel (reduced-precision modes)
+struct BndArgs {
+    const uint32_t *static_cells;
+    const unsigned long long *static_cnt;
+    const uint32_t *mov_cells; // nodes of step t next to moving bodies
+    const unsigned long long *mov_cnt;
+    long long static_cap, mov_cap;
+    const uint16_t *owner_t, *owner_t1;
+    const BodyDev *bodies;
+    const double *poses;
 };
 
 // precision: 0 FP64, 1 FP32, 2 FP16; Q: 9 or 19
@@ -52,7 +71,8 @@ cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long 
 // clears the change list and the covered/uncovered counters
 cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t, uint8_t *flags,
                          unsigned long long *chg_cnt, const uint32_t *chg_cell, const uint8_t *chg_val,
-                         long long chg_cap, long long *apm_cnt, cudaStream_t s);
+                         long long chg_cap, long long *apm_cnt, unsigned long long *bn_mov_next_cnt,
+                         cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,
@@ -66,7 +86,10 @@ cudaError_t launch_fgeom1(int Q, const Params &p, const GeomArgs &g, cudaStream_
 cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 // reduced-precision modes: boundary nodes of every body (pull, wall values,
 // momentum exchange, collision) -- runs beside k_bulk
-cudaError_t launch_bnd(int Q, int prec, const Params &p, const GeomArgs &g, const StepBufs &sb, cudaStream_t s);
+cudaError_t launch_bnd(int Q, int prec, const Params &p, const BndArgs &a, const StepBufs &sb, int grid,
+                       cudaStream_t s);
+// boundary-node lists of step t from scratch (all bodies)
+cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 
 // population export: fhat as FP64 f (adds w back for the shifted modes)
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);
