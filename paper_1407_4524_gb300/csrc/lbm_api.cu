@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -117,6 +118,7 @@ struct lbm_domain {
     long long bn_static_cap = 0, bn_mov_cap = 0;
     bool lists_dirty = true;
     int bnd_grid = 0;
+    int side_blocks = 0; // block cap of the side-stream kernels
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -471,6 +473,7 @@ int do_step_overlapped(lbm_domain *D) {
     CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
     StepBufs sb = step_bufs(D);
     GeomArgs g = geom_args(D, true);
+    g.grid_cap = D->side_blocks;
     if (D->n_moving) {
         CK(launch_fgeom1(Q, D->p, g, D->s2));
         CK(launch_fgeom2(Q, D->p, g, D->s2));
@@ -609,6 +612,13 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
     if ((rc = alloc_t(D, &D->counters, 8, nullptr))) return bail(rc);
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
+        int per = 2;
+        if (const char *ev = std::getenv("LBM_SIDE_BLOCKS_PER_SM")) per = std::max(1, std::atoi(ev));
+        D->side_blocks = std::max(1, sms) * per;
+    }
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     // high priority: blocks of the short side-stream kernels are dispatched
@@ -718,7 +728,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->bn_mov[0], (size_t)D->bn_mov_cap, &T))) return rc;
     if ((rc = alloc_t(D, &D->bn_mov[1], (size_t)D->bn_mov_cap, &T))) return rc;
     if ((rc = alloc_t(D, &D->bn_cnt, 3, &T))) return rc;
-    D->bnd_grid = (int)std::max<long long>(1, std::min<long long>(152 * 16, (bns + 7) / 8));
+    D->bnd_grid = (int)std::max<long long>(1, std::min<long long>(D->side_blocks, (bns + 7) / 8));
     D->lists_dirty = true;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);

@@ -392,31 +392,34 @@ __global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies,
 
 // owner at t+1 in the shell R-2 <= |x - X(t+1)| <= R+2, A+/A- appended
 __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom1(Params p, GeomArgs g) {
-    const int2 cm = g.chunk_map[blockIdx.x];
-    const int b = cm.x;
-    const BodyDev &B = g.bodies[b];
-    const double *P = g.poses + (long long)b * POSE_STRIDE;
     __shared__ Frame F;
-    if (threadIdx.x == 0) make_frame(P + 9, F);
-    __syncthreads();
-    int lo[3];
-    region_lo(p, B, P, REGION_MARGIN, lo);
-    const uint16_t me = (uint16_t)(b + 1);
-    const float R = (float)B.R;
-    for (int j = 0; j < GEOM_CELLS; ++j) {
-        RegionCell rc = region_cell(p, B, lo, cm.y, j);
-        if (!rc.valid) continue;
-        const float dist = frame_dist(p, B, F, rc);
-        if (dist < R - 2.0f || dist > R + 2.0f) continue;
-        const bool in_t = g.owner_t[rc.cell] == me;
-        const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
-        if (in1) g.owner_t1[rc.cell] = me;
-        else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
-        if (in_t != in1) {
-            const unsigned long long at = atomicAdd((unsigned long long *)&g.apm_cnt[b], 1ull);
-            if ((long long)at < B.apm_cap) {
-                g.apm_cell[B.apm_off + at] = (uint32_t)rc.cell;
-                g.apm_sign[B.apm_off + at] = (int8_t)(in1 ? 1 : -1);
+    for (int ch = blockIdx.x; ch < g.nchunks; ch += gridDim.x) {
+        const int2 cm = g.chunk_map[ch];
+        const int b = cm.x;
+        const BodyDev &B = g.bodies[b];
+        const double *P = g.poses + (long long)b * POSE_STRIDE;
+        __syncthreads();
+        if (threadIdx.x == 0) make_frame(P + 9, F);
+        __syncthreads();
+        int lo[3];
+        region_lo(p, B, P, REGION_MARGIN, lo);
+        const uint16_t me = (uint16_t)(b + 1);
+        const float R = (float)B.R;
+        for (int j = 0; j < GEOM_CELLS; ++j) {
+            RegionCell rc = region_cell(p, B, lo, cm.y, j);
+            if (!rc.valid) continue;
+            const float dist = frame_dist(p, B, F, rc);
+            if (dist < R - 2.0f || dist > R + 2.0f) continue;
+            const bool in_t = g.owner_t[rc.cell] == me;
+            const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
+            if (in1) g.owner_t1[rc.cell] = me;
+            else if (in_t || g.owner_t1[rc.cell] == me) g.owner_t1[rc.cell] = 0;
+            if (in_t != in1) {
+                const unsigned long long at = atomicAdd((unsigned long long *)&g.apm_cnt[b], 1ull);
+                if ((long long)at < B.apm_cap) {
+                    g.apm_cell[B.apm_off + at] = (uint32_t)rc.cell;
+                    g.apm_sign[B.apm_off + at] = (int8_t)(in1 ? 1 : -1);
+                }
             }
         }
     }
@@ -425,51 +428,53 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom1(Params p, GeomArgs g) {
 // flags of t+1 (solid, boundary node) in the shell R-2 .. R+3; changes appended
 template <class L>
 __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
-    const int2 cm = g.chunk_map[blockIdx.x];
-    const int b = cm.x;
-    const BodyDev &B = g.bodies[b];
-    const double *P = g.poses + (long long)b * POSE_STRIDE;
     __shared__ Frame F;
-    if (threadIdx.x == 0) make_frame(P + 9, F);
-    __syncthreads();
-    int lo[3];
-    region_lo(p, B, P, REGION_MARGIN, lo);
-    const float R = (float)B.R;
-    for (int j = 0; j < GEOM_CELLS; ++j) {
-        RegionCell rc = region_cell(p, B, lo, cm.y, j);
-        if (!rc.valid) continue;
-        const float dist = frame_dist(p, B, F, rc);
-        if (dist < R - 2.0f || dist > R + 3.0f) continue;
-        uint8_t nf;
-        if (g.owner_t1[rc.cell]) {
-            nf = FL_SOLID;
-        } else {
-            unsigned one = 0;
-            int minmov = 1 << 20;
+    for (int ch = blockIdx.x; ch < g.nchunks; ch += gridDim.x) {
+        const int2 cm = g.chunk_map[ch];
+        const int b = cm.x;
+        const BodyDev &B = g.bodies[b];
+        const double *P = g.poses + (long long)b * POSE_STRIDE;
+        __syncthreads();
+        if (threadIdx.x == 0) make_frame(P + 9, F);
+        __syncthreads();
+        int lo[3];
+        region_lo(p, B, P, REGION_MARGIN, lo);
+        const float R = (float)B.R;
+        for (int j = 0; j < GEOM_CELLS; ++j) {
+            RegionCell rc = region_cell(p, B, lo, cm.y, j);
+            if (!rc.valid) continue;
+            const float dist = frame_dist(p, B, F, rc);
+            if (dist < R - 2.0f || dist > R + 3.0f) continue;
+            uint8_t nf;
+            if (g.owner_t1[rc.cell]) {
+                nf = FL_SOLID;
+            } else {
+                unsigned one = 0;
+                int minmov = 1 << 20;
 #pragma unroll
-            for (int i = 1; i < L::Q; ++i) {
-                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                const unsigned o = a >= 0 ? g.owner_t1[a] : 0u;
-                one |= o;
-                if (o && g.bodies[o - 1].moving) minmov = min(minmov, (int)o);
+                for (int i = 1; i < L::Q; ++i) {
+                    const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                    const unsigned o = a >= 0 ? g.owner_t1[a] : 0u;
+                    one |= o;
+                    if (o && g.bodies[o - 1].moving) minmov = min(minmov, (int)o);
+                }
+                nf = one ? FL_BND : 0;
+                // boundary node of t+1 next to a moving body: listed by the lowest one
+                if (minmov == b + 1 && dist <= R + 1.5f) {
+                    const unsigned long long at = atomicAdd(g.bn_mov_cnt, 1ull);
+                    if ((long long)at < g.bn_mov_cap) g.bn_mov[at] = (uint32_t)rc.cell;
+                }
             }
-            nf = one ? FL_BND : 0;
-            // boundary node of t+1 next to a moving body: listed by the lowest one
-            if (minmov == b + 1 && dist <= R + 1.5f) {
-                const unsigned long long at = atomicAdd(g.bn_mov_cnt, 1ull);
-                if ((long long)at < g.bn_mov_cap) g.bn_mov[at] = (uint32_t)rc.cell;
-            }
-        }
-        if ((g.flags[rc.cell] & (FL_SOLID | FL_BND)) != nf) {
-            const unsigned long long at = atomicAdd(g.chg_cnt, 1ull);
-            if ((long long)at < g.chg_cap) {
-                g.chg_cell[at] = (uint32_t)rc.cell;
-                g.chg_val[at] = nf;
+            if ((g.flags[rc.cell] & (FL_SOLID | FL_BND)) != nf) {
+                const unsigned long long at = atomicAdd(g.chg_cnt, 1ull);
+                if ((long long)at < g.chg_cap) {
+                    g.chg_cell[at] = (uint32_t)rc.cell;
+                    g.chg_val[at] = nf;
+                }
             }
         }
     }
 }
-
 
 // boundary-node lists of step t from scratch: nodes next only to static
 // bodies go to the static list, nodes next to a moving body to the moving
@@ -540,14 +545,15 @@ cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStre
 
 cudaError_t launch_fgeom1(int, const Params &p, const GeomArgs &g, cudaStream_t s) {
     if (g.nchunks == 0) return cudaSuccess;
-    k_fgeom1<<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    k_fgeom1<<<g.grid_cap > 0 ? min(g.nchunks, g.grid_cap) : g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
     if (g.nchunks == 0) return cudaSuccess;
-    if (Q == 9) k_fgeom2<Lat<9>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
-    else k_fgeom2<Lat<19>><<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    const int grid = g.grid_cap > 0 ? min(g.nchunks, g.grid_cap) : g.nchunks;
+    if (Q == 9) k_fgeom2<Lat<9>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
+    else k_fgeom2<Lat<19>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ struct GeomArgs {
     uint32_t *bn_mov;
     unsigned long long *bn_mov_cnt;
     long long bn_static_cap, bn_mov_cap;
+    int grid_cap; // > 0: at most this many blocks (side-stream kernels)
 };
 
 // arguments of the boundary-node kernel (reduced-precision modes)
