@@ -615,7 +615,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
-        int per = 2;
+        int per = 3;
         if (const char *ev = std::getenv("LBM_SIDE_BLOCKS_PER_SM")) per = std::max(1, std::atoi(ev));
         D->side_blocks = std::max(1, sms) * per;
     }
