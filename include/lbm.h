@@ -228,6 +228,65 @@ int lbm_kernel_time(lbm_domain *dom, int64_t *launches, double *total_ms);
 /* Number of kernel launches lbm_step(dom, 1) issues at the current state. */
 int lbm_launches_per_step(const lbm_domain *dom, int *out);
 
+/* ---- serving: continuous batching of many solves ------------------------------
+ * A batch keeps up to max_slots independent solves resident on one GPU (each
+ * with its own populations, admitted against a device-memory budget) and
+ * advances all unfinished ones together: one tick is five kernel launches
+ * (bulk and boundary-node kernels per lattice, one end-of-step kernel) for
+ * the whole batch, replayed as a CUDA graph.  Supported: reduced-precision
+ * modes (LBM_FP32 / LBM_FP16) and static bodies.  Each solve runs the same
+ * arithmetic as a standalone domain of the same descriptor and its
+ * force/torque sums are exact, so its results are bit-identical alone and in
+ * any mix. */
+
+typedef struct lbm_batch lbm_batch;
+
+typedef struct lbm_batch_desc {
+    int device;
+    int max_slots;           /* resident solves at most (>= 1) */
+    int ticks_per_launch;    /* steps per lbm_batch_run launch; 0 -> 32 */
+    int reserved;
+    int64_t budget_bytes;    /* device memory the resident solves may hold */
+    void *stream;            /* cudaStream_t; NULL -> default stream */
+    lbm_alloc_fn alloc;      /* optional allocator for the solves' buffers */
+    lbm_free_fn free;
+    void *alloc_ctx;
+} lbm_batch_desc;
+
+int lbm_batch_create(const lbm_batch_desc *desc, lbm_batch **out);
+int lbm_batch_destroy(lbm_batch *batch);
+
+/* Device bytes a solve with this descriptor and body list would hold. */
+int lbm_batch_solve_bytes(const lbm_domain_desc *desc, const lbm_body *host_bodies, int n, int64_t steps,
+                          int64_t *bytes);
+
+/* Admit a solve of `steps` steps (desc->stream / alloc are ignored: the
+ * batch's are used).  LBM_ERR_OOM if it does not fit the remaining budget or
+ * no slot is free (nothing is allocated then); LBM_ERR_ARG for moving bodies
+ * or FP64.  *slot_out receives the slot index. */
+int lbm_batch_admit(lbm_batch *batch, const lbm_domain_desc *desc, const lbm_body *host_bodies, int n,
+                    int64_t steps, int *slot_out);
+
+/* Advance every resident unfinished solve by n * ticks_per_launch steps
+ * (each stops at its own step count).  Asynchronous. */
+int lbm_batch_run(lbm_batch *batch, int n);
+
+/* Slots that completed since the previous poll (synchronises):
+ * up to cap indices into slots_out, their number in *count_out. */
+int lbm_batch_poll(lbm_batch *batch, int *slots_out, int cap, int *count_out);
+
+/* Force/torque rows of a slot's solve, as lbm_get_force_torque. */
+int lbm_batch_get_force_torque(lbm_batch *batch, int slot, int64_t first, int64_t count, int kind, double *out);
+
+/* Current step of a slot's solve. */
+int64_t lbm_batch_time(const lbm_batch *batch, int slot);
+
+/* Free a slot (finished or not) and return its memory to the budget. */
+int lbm_batch_release(lbm_batch *batch, int slot);
+
+/* Resident solves and bytes held. */
+int lbm_batch_usage(const lbm_batch *batch, int *resident, int64_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_geom.cu", "lbm_fp64.cu", "lbm_fp32.cu"]
+SOURCES = ["lbm_api.cu", "lbm_geom.cu", "lbm_fp64.cu", "lbm_fp32.cu", "lbm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -407,6 +407,18 @@ int upload_bodies(lbm_domain *D) {
 
 int do_step_overlapped(lbm_domain *D);
 
+// reduced-precision modes: boundary-node lists of step t from scratch
+int build_bnd_lists(lbm_domain *D) {
+    const int cur = (int)(D->t & 1);
+    CK(cudaMemsetAsync(D->bn_cnt, 0, 3 * sizeof(unsigned long long), D->s));
+    GeomArgs gl = geom_args(D, false);
+    gl.bn_mov = D->bn_mov[cur];
+    gl.bn_mov_cnt = D->bn_cnt + 1 + cur;
+    CK(launch_bnd_lists(D->Q, D->p, gl, D->s));
+    D->lists_dirty = false;
+    return LBM_OK;
+}
+
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     if (prec != LBM_FP64 && D->nb) return do_step_overlapped(D);
@@ -461,13 +473,9 @@ int do_step_overlapped(lbm_domain *D) {
                         D->apm_cnt, D->bn_cnt + 1 + nxt, D->s));
         D->prep_dirty = false;
     }
-    if (D->lists_dirty) { // boundary-node lists of step t from scratch
-        CK(cudaMemsetAsync(D->bn_cnt, 0, 3 * sizeof(unsigned long long), D->s));
-        GeomArgs gl = geom_args(D, false);
-        gl.bn_mov = D->bn_mov[cur];
-        gl.bn_mov_cnt = D->bn_cnt + 1 + cur;
-        CK(launch_bnd_lists(Q, D->p, gl, D->s));
-        D->lists_dirty = false;
+    if (D->lists_dirty) {
+        int rc = build_bnd_lists(D);
+        if (rc) return rc;
     }
     CK(cudaEventRecord(D->ev_prep, D->s));
     CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
@@ -607,7 +615,10 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     int rc;
     for (int k = 0; k < 2; ++k) {
         if ((rc = alloc_into(D, &D->pop[k], N * D->Q * D->Ssize, nullptr))) return bail(rc);
-        if ((rc = alloc_into(D, &D->mac[k], N * 4 * D->Csize, nullptr))) return bail(rc);
+        // moments are stored only in the FP64 mode (the reduced-precision modes
+        // take them from the collided populations)
+        if ((rc = alloc_into(D, &D->mac[k], d.precision == LBM_FP64 ? N * 4 * D->Csize : 256, nullptr)))
+            return bail(rc);
         if ((rc = alloc_t(D, &D->owner[k], N, nullptr))) return bail(rc);
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
@@ -694,13 +705,17 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->chunk_mov, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->chunk_cnt_apm, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->chunk_cnt_link, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
+    // cut-link lists and per-link contributions: FP64 mode only (the
+    // reduced-precision modes evaluate links inside the boundary-node kernel)
+    const bool exact = D->prec == LBM_FP64;
+    const size_t Lsz = exact ? (size_t)std::max<long long>(loff, 1) : 1;
     for (int k = 0; k < 2; ++k) {
-        if ((rc = alloc_t(D, &D->Lcell[k], (size_t)std::max<long long>(loff, 1), &T))) return rc;
-        if ((rc = alloc_t(D, &D->Ldir[k], (size_t)std::max<long long>(loff, 1), &T))) return rc;
-        if ((rc = alloc_t(D, &D->Ldelta[k], (size_t)std::max<long long>(loff, 1), &T))) return rc;
+        if ((rc = alloc_t(D, &D->Lcell[k], Lsz, &T))) return rc;
+        if ((rc = alloc_t(D, &D->Ldir[k], Lsz, &T))) return rc;
+        if ((rc = alloc_t(D, &D->Ldelta[k], Lsz, &T))) return rc;
         if ((rc = alloc_t(D, &D->link_cnt[k], nbx, &T))) return rc;
     }
-    if ((rc = alloc_t(D, &D->me, (size_t)std::max<long long>(loff, 1) * ME_PER_LINK, &T))) return rc;
+    if ((rc = alloc_t(D, &D->me, Lsz * ME_PER_LINK, &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_cell, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_sign, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_cnt, nbx, &T))) return rc;
@@ -745,13 +760,16 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
     CK(cudaMemcpyAsync(D->owner[1], D->owner[0], N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
     CK(launch_flags_full(D->Q, D->p, D->owner[0], D->flags, D->s));
-    CK(launch_geom_b(D->Q, D->p, g, D->s));
-    CK(launch_geom_c(D->Q, D->p, g, D->s));
-    const size_t L = (size_t)std::max<long long>(loff, 1);
-    CK(cudaMemcpyAsync(D->Lcell[1], D->Lcell[0], L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, D->s));
-    CK(cudaMemcpyAsync(D->Ldir[1], D->Ldir[0], L, cudaMemcpyDeviceToDevice, D->s));
-    CK(cudaMemcpyAsync(D->Ldelta[1], D->Ldelta[0], L * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
-    CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice, D->s));
+    if (exact) {
+        CK(launch_geom_b(D->Q, D->p, g, D->s));
+        CK(launch_geom_c(D->Q, D->p, g, D->s));
+        const size_t L = Lsz;
+        CK(cudaMemcpyAsync(D->Lcell[1], D->Lcell[0], L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, D->s));
+        CK(cudaMemcpyAsync(D->Ldir[1], D->Ldir[0], L, cudaMemcpyDeviceToDevice, D->s));
+        CK(cudaMemcpyAsync(D->Ldelta[1], D->Ldelta[0], L * sizeof(double), cudaMemcpyDeviceToDevice, D->s));
+        CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice,
+                           D->s));
+    }
     CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr,
                    nullptr, nullptr, D->s));
     D->prep_dirty = false;
@@ -943,6 +961,458 @@ int lbm_launches_per_step(const lbm_domain *D, int *out) {
         *out = 3 + (D->n_moving ? 3 : (D->prep_dirty ? 1 : 0)); // bulk, bnd, finish (+ prep, geometry)
     else
         *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
+    return LBM_OK;
+}
+
+} // extern "C"
+
+// ---- serving: continuous batching ------------------------------------------
+//
+// A batch holds up to max_slots solves, each a complete lbm_domain (reduced
+// precision, static bodies) created on the batch's stream and allocator.  The
+// device keeps a table of SolveDev records (one per slot) that the batched
+// kernels read; for each (lattice, precision) group the host keeps a block
+// work table (slot, first cell) for the bulk kernel and a prefix of the
+// boundary-node counts for the boundary-node kernel.  A tick is: fork; bulk
+// kernels of every group on the batch stream and boundary-node kernels on the
+// high-priority side stream (disjoint nodes, both read fhat(t)); join; one
+// end-of-step kernel for every resident solve.  ticks_per_launch ticks are
+// captured once into a CUDA graph, re-captured whenever the resident set
+// changes.  Admission and release synchronise the batch stream, so the tables
+// are never rewritten under a running graph.
+
+struct lbm_batch {
+    lbm_batch_desc d{};
+    cudaStream_t s = nullptr, s2 = nullptr;
+    bool own_s = false;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int tpl = 32;
+    int side_blocks = 0;
+    int64_t used = 0;
+    struct Slot {
+        lbm_domain *D = nullptr;
+        int64_t t_end = 0;
+        long long nodes = 0;
+        bool reported = false;
+    };
+    std::vector<Slot> slots;
+    SolveDev *dsolves = nullptr;
+    struct Group {
+        int Q = 0, prec = 0;
+        int2 *work = nullptr;
+        int nwork = 0;
+        int *slots = nullptr;
+        long long *node_pre = nullptr;
+        int nslots = 0;
+        int grid = 0;
+    };
+    Group g[4];
+    int *dall = nullptr;
+    int nall = 0;
+    std::vector<void *> table_allocs;
+    cudaGraphExec_t exec = nullptr;
+    bool dirty = true;
+
+    void *alloc(size_t n) {
+        if (n == 0) n = 256;
+        void *ptr = nullptr;
+        if (d.alloc) ptr = d.alloc(n, d.alloc_ctx);
+        else if (cudaMalloc(&ptr, n) != cudaSuccess) ptr = nullptr;
+        return ptr;
+    }
+    void release(void *ptr) {
+        if (!ptr) return;
+        if (d.free) d.free(ptr, d.alloc_ctx);
+        else cudaFree(ptr);
+    }
+};
+
+namespace {
+
+int group_of(int Q, int prec) { return (Q == 19 ? 2 : 0) + (prec == LBM_FP16 ? 1 : 0); }
+
+// Device bytes lbm_create_domain + lbm_set_bodies request for this problem
+// (the same sizes, in the same order, without allocating).
+int domain_bytes(const lbm_domain_desc &d, const lbm_body *hb, int n, int64_t *bytes) {
+    lbm_domain T;
+    T.d = d;
+    T.Q = d.lattice;
+    T.prec = d.precision;
+    T.p.nx = d.nx;
+    T.p.ny = d.ny;
+    T.p.nz = d.nz;
+    T.p.N = (long long)d.nx * d.ny * d.nz;
+    for (int a = 0; a < 3; ++a) T.p.per[a] = d.edge[2 * a] == LBM_EDGE_PERIODIC;
+    int rc = validate_bodies(&T, hb, n);
+    if (rc) return rc;
+    const long long N = T.p.N;
+    const long long S = d.precision == LBM_FP64 ? 8 : (d.precision == LBM_FP32 ? 4 : 2);
+    const long long C = d.precision == LBM_FP64 ? 8 : 4;
+    const long long cap = d.series_capacity > 0 ? d.series_capacity : 8192;
+    long long b = 0;
+    b += 2 * (N * T.Q * S + (d.precision == LBM_FP64 ? N * 4 * C : 256) + N * 2); // pop, mac, owner
+    b += N + 8 * 8;                                                               // flags, counters
+    const long long nbx = std::max(n, 1);
+    long long loff = 0, aoff = 0, chunks = 0, bns = 0;
+    for (int k = 0; k < n; ++k) {
+        BodyDev o;
+        body_params(&T, hb[k], o);
+        loff += o.link_cap;
+        aoff += o.apm_cap;
+        chunks += o.nchunks;
+        bns += o.link_cap / (T.Q - 1) + 64;
+    }
+    const long long ch = std::max<long long>(chunks, 1);
+    const long long Lsz = d.precision == LBM_FP64 ? std::max<long long>(loff, 1) : 1;
+    const long long A = std::max<long long>(aoff, 1);
+    const long long B = std::max<long long>(bns, 1);
+    b += nbx * (long long)sizeof(BodyDev) + nbx * 4;             // bodies, moving ids
+    b += 2 * ch * 8 + 2 * ch * 4;                                // chunk maps, chunk counts
+    b += 2 * (Lsz * 4 + Lsz * 1 + Lsz * 8 + nbx * 8);            // link lists and counts
+    b += Lsz * ME_PER_LINK * 8;                                  // per-link contributions
+    b += A * 4 + A * 1 + nbx * 8;                                // covered/uncovered lists
+    b += cap * nbx * SERIES_ROW * 8 + nbx * POSE_STRIDE * 8;     // series, poses
+    b += 2 * (nbx + 1) * 8 + nbx * SERIES_ROW * 8;               // prefixes, accumulators
+    b += 8 + A * 4 + A * 1;                                      // flag-change list
+    b += B * 4 * 3 + 3 * 8;                                      // boundary-node lists
+    *bytes = b;
+    return LBM_OK;
+}
+
+int batch_check_desc(const lbm_domain_desc &d, const lbm_body *hb, int n, int64_t steps) {
+    if (steps < 1) return fail(LBM_ERR_ARG, "a served solve needs at least one step");
+    if (d.precision != LBM_FP32 && d.precision != LBM_FP16)
+        return fail(LBM_ERR_ARG, "served solves run in LBM_FP32 or LBM_FP16");
+    if ((long long)d.nx * d.ny * d.nz >= (1ll << 31)) return fail(LBM_ERR_ARG, "a served solve has < 2^31 cells");
+    if (n < 0 || (n > 0 && !hb)) return fail(LBM_ERR_ARG, "invalid body list");
+    for (int k = 0; k < n; ++k)
+        if (is_moving(hb[k])) return fail(LBM_ERR_ARG, "served solves take static bodies only");
+    if (d.has_force) return fail(LBM_ERR_ARG, "served solves take no body force");
+    return LBM_OK;
+}
+
+void batch_free_tables(lbm_batch *B) {
+    for (void *ptr : B->table_allocs) B->release(ptr);
+    B->table_allocs.clear();
+    for (auto &G : B->g) {
+        G.work = nullptr;
+        G.slots = nullptr;
+        G.node_pre = nullptr;
+        G.nwork = G.nslots = G.grid = 0;
+    }
+    B->dall = nullptr;
+    B->nall = 0;
+}
+
+template <class T> int batch_upload(lbm_batch *B, T **dst, const std::vector<T> &v) {
+    *dst = nullptr;
+    if (v.empty()) return LBM_OK;
+    void *ptr = B->alloc(v.size() * sizeof(T));
+    if (!ptr) return fail(LBM_ERR_OOM, "batch table allocation failed");
+    B->table_allocs.push_back(ptr);
+    CK(cudaMemcpyAsync(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, B->s));
+    *dst = (T *)ptr;
+    return LBM_OK;
+}
+
+// work tables of the resident unfinished solves, then the tick graph
+int batch_rebuild(lbm_batch *B) {
+    CK(cudaStreamSynchronize(B->s));
+    batch_free_tables(B);
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    std::vector<int2> work[4];
+    std::vector<int> gslots[4], all;
+    std::vector<long long> pre[4];
+    for (int k = 0; k < 4; ++k) pre[k].push_back(0);
+    for (int sl = 0; sl < (int)B->slots.size(); ++sl) {
+        const auto &S = B->slots[sl];
+        if (!S.D || S.D->t >= S.t_end) continue;
+        const int gi = group_of(S.D->Q, S.D->prec);
+        const long long N = S.D->p.N;
+        for (long long c = 0; c < N; c += BULK_THREADS) work[gi].push_back(make_int2(sl, (int)c));
+        gslots[gi].push_back(sl);
+        pre[gi].push_back(pre[gi].back() + S.nodes);
+        all.push_back(sl);
+    }
+    int rc;
+    for (int k = 0; k < 4; ++k) {
+        auto &G = B->g[k];
+        G.Q = k >= 2 ? 19 : 9;
+        G.prec = (k & 1) ? LBM_FP16 : LBM_FP32;
+        if ((rc = batch_upload(B, &G.work, work[k]))) return rc;
+        if ((rc = batch_upload(B, &G.slots, gslots[k]))) return rc;
+        if (!gslots[k].empty() && (rc = batch_upload(B, &G.node_pre, pre[k]))) return rc;
+        G.nwork = (int)work[k].size();
+        G.nslots = (int)gslots[k].size();
+        const long long nodes = pre[k].back();
+        G.grid = (int)std::min<long long>(B->side_blocks, (nodes + 7) / 8);
+    }
+    if ((rc = batch_upload(B, &B->dall, all))) return rc;
+    B->nall = (int)all.size();
+    B->dirty = false;
+    if (B->nall == 0) return LBM_OK;
+
+    // capture ticks_per_launch ticks
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < B->tpl && e == cudaSuccess; ++t) {
+        if ((e = cudaEventRecord(B->ev_fork, B->s)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(B->s2, B->ev_fork, 0)) != cudaSuccess) break;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            const auto &G = B->g[k];
+            if (G.nslots == 0) continue;
+            if (G.grid > 0)
+                e = launch_bbnd(G.Q, G.prec, B->dsolves, G.slots, G.node_pre, G.nslots, G.grid, B->s2);
+            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.prec, B->dsolves, G.work, G.nwork, B->s);
+        }
+        if (e != cudaSuccess) break;
+        if ((e = cudaEventRecord(B->ev_join, B->s2)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(B->s, B->ev_join, 0)) != cudaSuccess) break;
+        e = launch_bfinish(B->dsolves, B->dall, B->nall, B->s);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(B->s, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiateWithFlags(&B->exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        B->exec = nullptr;
+        B->dirty = true;
+        return fail(LBM_ERR_CUDA, std::string("batch tick graph: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_batch_desc *desc, lbm_batch **out) {
+    if (!desc || !out) return fail(LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    const lbm_batch_desc &d = *desc;
+    if (d.max_slots < 1 || d.max_slots > 4096) return fail(LBM_ERR_ARG, "max_slots must be in [1, 4096]");
+    if (d.ticks_per_launch < 0 || d.ticks_per_launch > 4096) return fail(LBM_ERR_ARG, "ticks_per_launch in [0, 4096]");
+    if (d.budget_bytes <= 0) return fail(LBM_ERR_ARG, "budget_bytes must be > 0");
+    if (d.reserved != 0) return fail(LBM_ERR_ARG, "reserved must be 0");
+    if ((d.alloc == nullptr) != (d.free == nullptr)) return fail(LBM_ERR_ARG, "alloc and free go together");
+    cudaError_t e = cudaSetDevice(d.device);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    lbm_batch *B = new lbm_batch();
+    B->d = d;
+    B->tpl = d.ticks_per_launch > 0 ? d.ticks_per_launch : 32;
+    B->slots.resize(d.max_slots);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
+    B->side_blocks = std::max(1, sms) * 3;
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (d.stream) {
+        B->s = (cudaStream_t)d.stream;
+    } else {
+        B->own_s = true;
+        e = cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&B->s2, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(B);
+        return fail(LBM_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+    }
+    B->dsolves = (SolveDev *)B->alloc(sizeof(SolveDev) * d.max_slots);
+    if (!B->dsolves) {
+        lbm_batch_destroy(B);
+        return fail(LBM_ERR_OOM, "batch solve table");
+    }
+    if ((e = cudaMemsetAsync(B->dsolves, 0, sizeof(SolveDev) * d.max_slots, B->s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(B->s)) != cudaSuccess) {
+        lbm_batch_destroy(B);
+        return fail(LBM_ERR_CUDA, std::string("batch create: ") + cudaGetErrorString(e));
+    }
+    *out = B;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch *B) {
+    if (!B) return LBM_OK;
+    if (B->s) cudaStreamSynchronize(B->s);
+    for (auto &S : B->slots)
+        if (S.D) lbm_destroy_domain(S.D);
+    batch_free_tables(B);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->release(B->dsolves);
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+    if (B->ev_join) cudaEventDestroy(B->ev_join);
+    if (B->s2) cudaStreamDestroy(B->s2);
+    if (B->own_s && B->s) cudaStreamDestroy(B->s);
+    delete B;
+    return LBM_OK;
+}
+
+int lbm_batch_solve_bytes(const lbm_domain_desc *desc, const lbm_body *hb, int n, int64_t steps, int64_t *bytes) {
+    if (!desc || !bytes) return fail(LBM_ERR_ARG, "null argument");
+    int rc = batch_check_desc(*desc, hb, n, steps);
+    if (rc) return rc;
+    lbm_domain_desc d = *desc;
+    if (d.series_capacity <= 0) d.series_capacity = steps;
+    return domain_bytes(d, hb, n, bytes);
+}
+
+int lbm_batch_admit(lbm_batch *B, const lbm_domain_desc *desc, const lbm_body *hb, int n, int64_t steps,
+                    int *slot_out) {
+    if (!B || !desc || !slot_out) return fail(LBM_ERR_ARG, "null argument");
+    *slot_out = -1;
+    int rc = batch_check_desc(*desc, hb, n, steps);
+    if (rc) return rc;
+    lbm_domain_desc d = *desc;
+    d.device = B->d.device;
+    d.stream = B->s;
+    d.alloc = B->d.alloc;
+    d.free = B->d.free;
+    d.alloc_ctx = B->d.alloc_ctx;
+    if (d.series_capacity <= 0) d.series_capacity = steps;
+    int64_t need = 0;
+    if ((rc = domain_bytes(d, hb, n, &need))) return rc;
+    int sl = -1;
+    for (int k = 0; k < (int)B->slots.size() && sl < 0; ++k)
+        if (!B->slots[k].D) sl = k;
+    if (sl < 0) return fail(LBM_ERR_OOM, "no free slot");
+    if (B->used + need > B->d.budget_bytes)
+        return fail(LBM_ERR_OOM, "solve needs " + std::to_string(need) + " bytes, " +
+                                     std::to_string(B->d.budget_bytes - B->used) + " left in the budget");
+    CK(cudaSetDevice(B->d.device));
+    lbm_domain *D = nullptr;
+    if ((rc = lbm_create_domain(&d, &D))) return rc;
+    if ((rc = lbm_set_bodies(D, hb, n))) {
+        lbm_destroy_domain(D);
+        return rc;
+    }
+    long long nodes = 0;
+    if (n > 0) {
+        // poses of t = 0 and the boundary-node list (all static)
+        cudaError_t e = launch_fprep(D->p, D->dbodies, D->poses, 0, D->flags, D->chg_cnt, D->chg_cell, D->chg_val,
+                                     D->chg_cap, D->apm_cnt, D->bn_cnt + 2, D->s);
+        if (e == cudaSuccess && (rc = build_bnd_lists(D))) {
+            lbm_destroy_domain(D);
+            return rc;
+        }
+        unsigned long long cnt = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, D->bn_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, D->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(D->s);
+        if (e != cudaSuccess) {
+            lbm_destroy_domain(D);
+            return fail(LBM_ERR_CUDA, std::string("admit: ") + cudaGetErrorString(e));
+        }
+        nodes = (long long)std::min<unsigned long long>(cnt, (unsigned long long)D->bn_static_cap);
+        D->prep_dirty = false;
+    }
+    SolveDev sv{};
+    sv.p = D->p;
+    sv.Q = D->Q;
+    sv.active = 1;
+    sv.t = 0;
+    sv.t_end = steps;
+    sv.pop[0] = D->pop[0];
+    sv.pop[1] = D->pop[1];
+    sv.flags = D->flags;
+    sv.owner = D->owner[0];
+    sv.bodies = D->dbodies;
+    sv.poses = D->poses;
+    sv.bn_static = D->bn_static;
+    sv.bn_cnt = D->bn_cnt;
+    sv.bn_cap = D->bn_static_cap;
+    sv.acc = D->acc;
+    sv.series = D->series;
+    sv.counters = D->counters;
+    cudaError_t e = cudaMemcpyAsync(B->dsolves + sl, &sv, sizeof(sv), cudaMemcpyHostToDevice, B->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->s);
+    if (e != cudaSuccess) {
+        lbm_destroy_domain(D);
+        return fail(LBM_ERR_CUDA, std::string("admit: ") + cudaGetErrorString(e));
+    }
+    auto &S = B->slots[sl];
+    S.D = D;
+    S.t_end = steps;
+    S.nodes = nodes;
+    S.reported = false;
+    B->used += (int64_t)D->bytes;
+    B->dirty = true;
+    *slot_out = sl;
+    return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch *B, int n) {
+    if (!B || n < 0) return fail(LBM_ERR_ARG, "invalid arguments");
+    CK(cudaSetDevice(B->d.device));
+    if (B->dirty) {
+        int rc = batch_rebuild(B);
+        if (rc) return rc;
+    }
+    if (!B->exec || n == 0) return LBM_OK;
+    for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(B->exec, B->s));
+    const int64_t ticks = (int64_t)n * B->tpl;
+    bool finished = false;
+    for (auto &S : B->slots) {
+        if (!S.D || S.D->t >= S.t_end) continue;
+        S.D->t = std::min<int64_t>(S.D->t + ticks, S.t_end); // the device stops each solve at t_end
+        if (S.D->t >= S.t_end) finished = true;
+    }
+    if (finished) B->dirty = true; // drop finished solves from the tables
+    return LBM_OK;
+}
+
+int lbm_batch_poll(lbm_batch *B, int *slots_out, int cap, int *count_out) {
+    if (!B || !count_out || cap < 0 || (cap > 0 && !slots_out)) return fail(LBM_ERR_ARG, "invalid arguments");
+    CK(cudaStreamSynchronize(B->s));
+    int c = 0;
+    for (int sl = 0; sl < (int)B->slots.size() && c < cap; ++sl) {
+        auto &S = B->slots[sl];
+        if (S.D && !S.reported && S.D->t >= S.t_end) {
+            S.reported = true;
+            slots_out[c++] = sl;
+        }
+    }
+    *count_out = c;
+    return LBM_OK;
+}
+
+int lbm_batch_get_force_torque(lbm_batch *B, int slot, int64_t first, int64_t count, int kind, double *out) {
+    if (!B || slot < 0 || slot >= (int)B->slots.size() || !B->slots[slot].D)
+        return fail(LBM_ERR_ARG, "no solve in this slot");
+    return lbm_get_force_torque(B->slots[slot].D, first, count, kind, out);
+}
+
+int64_t lbm_batch_time(const lbm_batch *B, int slot) {
+    if (!B || slot < 0 || slot >= (int)B->slots.size() || !B->slots[slot].D) return -1;
+    return B->slots[slot].D->t;
+}
+
+int lbm_batch_release(lbm_batch *B, int slot) {
+    if (!B || slot < 0 || slot >= (int)B->slots.size() || !B->slots[slot].D)
+        return fail(LBM_ERR_ARG, "no solve in this slot");
+    CK(cudaStreamSynchronize(B->s));
+    auto &S = B->slots[slot];
+    const bool running = S.D->t < S.t_end;
+    B->used -= (int64_t)S.D->bytes;
+    SolveDev zero{};
+    CK(cudaMemcpyAsync(B->dsolves + slot, &zero, sizeof(zero), cudaMemcpyHostToDevice, B->s));
+    CK(cudaStreamSynchronize(B->s));
+    lbm_destroy_domain(S.D);
+    S = lbm_batch::Slot{};
+    if (running) B->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_usage(const lbm_batch *B, int *resident, int64_t *bytes) {
+    if (!B || !resident || !bytes) return fail(LBM_ERR_ARG, "invalid arguments");
+    int r = 0;
+    for (const auto &S : B->slots) r += S.D != nullptr;
+    *resident = r;
+    *bytes = B->used;
     return LBM_OK;
 }
 

@@ -36,8 +36,10 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// the step of boundary node `cell` (one warp; lane = lattice direction)
 template <class L, class P>
-__global__ void __launch_bounds__(BND_THREADS) k_bnd(Params p, BndArgs a, StepBufs sb) {
+__device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, const StepBufs &sb, long long cell,
+                                         bool from_static, unsigned &nlinks) {
     using S = typename P::S;
     const int lane = threadIdx.x & 31;
     const bool act = lane < L::Q;
@@ -45,162 +47,167 @@ __global__ void __launch_bounds__(BND_THREADS) k_bnd(Params p, BndArgs a, StepBu
     const int cxi = L::cx(i), cyi = L::cy(i), czi = L::cz(i);
     const int ib = L::opp(i);
     const float wi = L::template w<float>(i);
+    const S *src = (const S *)sb.src;
+    S *dst = (S *)sb.dst;
+    const long long N = p.N;
+    if (a.owner_t[cell] != 0) return; // warp-uniform
+    int x, y, z;
+    coords_of(p, cell, x, y, z);
+    const long long sc = i == 0 ? cell : nbr<L>(p, x, y, z, i, 1);
+    const uint16_t o = (act && i > 0 && sc >= 0) ? a.owner_t[sc] : (uint16_t)0;
+    if (from_static) { // a moving body next to it: that body's list has it
+        const bool mv = o != 0 && a.bodies[o - 1].moving;
+        if (__any_sync(0xffffffffu, mv)) return;
+    }
+    const unsigned cutmask = __ballot_sync(0xffffffffu, o != 0);
+    if (!cutmask) return;
+    // moments of the collided populations fhat(x, t) (= those of f(x, t))
+    const float fo = act ? ldP(src + (long long)i * N + cell) : 0.0f;
+    const float drF = warp_sum(fo);
+    float uF[3];
+    {
+        float j0 = warp_sum(cxi * fo), j1 = warp_sum(cyi * fo), j2 = warp_sum(czi * fo);
+        if (p.has_force) {
+            j0 -= 0.5f * p.gf[0];
+            j1 -= 0.5f * p.gf[1];
+            j2 -= 0.5f * p.gf[2];
+        }
+        const float inv = 1.0f / (p.eq == 0 ? p.rho0f : 1.0f + drF);
+        uF[0] = j0 * inv;
+        uF[1] = j1 * inv;
+        uF[2] = j2 * inv;
+    }
+    const float fb = __shfl_sync(0xffffffffu, fo, ib); // fhat_ib(x, t)
+    float fi = 0.0f;
+    float v[ME_PER_LINK];
+#pragma unroll
+    for (int c = 0; c < ME_PER_LINK; ++c) v[c] = 0.0f;
+    const int bi = (int)o - 1;
+    if (o) {
+        const BodyDev &Bi = a.bodies[bi];
+        const double *Pf = a.poses + (long long)bi * POSE_STRIDE + 12; // floor, frac of the pose at t
+        float d[3];
+        const int c3[3] = {x, y, z};
+        for (int q = 0; q < 3; ++q) {
+            int kk = c3[q] - (int)Pf[q];
+            if (p.per[q]) {
+                const int n = axis_len(p, q);
+                if (2 * kk > n) kk -= n;
+                else if (2 * kk < -n) kk += n;
+            }
+            d[q] = (float)kk - (float)Pf[3 + q];
+        }
+        const float dl = link_delta_f(Bi, d, cxi, cyi, czi);
+        const float rb[3] = {d[0] - dl * cxi, d[1] - dl * cyi, d[2] - dl * czi};
+        const float W0 = (float)Bi.W[0], W1 = (float)Bi.W[1], W2 = (float)Bi.W[2];
+        const float uB[3] = {(float)Bi.U[0] + (W1 * rb[2] - W2 * rb[1]),
+                             (float)Bi.U[1] + (W2 * rb[0] - W0 * rb[2]),
+                             (float)Bi.U[2] + (W0 * rb[1] - W1 * rb[0])};
+        float ubf[3], chi;
+        if (dl < 0.5f) {
+            // u_bf = u_G = u(x_F + c_i, t), chi = (2 Delta - 1)/(tau - 2)
+            const long long G = nbr<L>(p, x, y, z, ib, 1); // x - c_ib = x + c_i
+            if (G >= 0 && a.owner_t[G] == 0) {
+                float drG;
+                moments_hat<L>(p, src, G, drG, ubf);
+                chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
+            } else {
+                ubf[0] = uF[0];
+                ubf[1] = uF[1];
+                ubf[2] = uF[2];
+                chi = 0.0f;
+                atomicAdd(&sb.counters[0], 1ull);
+            }
+        } else {
+            // u_bf = u_F + 3/(2 Delta) (u_B - u_F), chi = (2 Delta - 1)/(tau + 1/2)
+            const float k3 = 3.0f / (2.0f * dl);
+            for (int q = 0; q < 3; ++q) ubf[q] = fmaf(k3, uB[q] - uF[q], uF[q]);
+            chi = (2.0f * dl - 1.0f) / ((float)p.tau + 0.5f);
+        }
+        // fictitious equilibrium g_ib (Eq. Fillipova_equilibrium), deviation form
+        const float cbu = -(cxi * ubf[0] + cyi * ubf[1] + czi * ubf[2]);
+        const float cbF = -(cxi * uF[0] + cyi * uF[1] + czi * uF[2]);
+        const float uFsq = uF[0] * uF[0] + uF[1] * uF[1] + uF[2] * uF[2];
+        const float rr = p.eq == 0 ? p.rho0f : 1.0f + drF;
+        const float gq = wi * fmaf(rr, 3.0f * cbu + 4.5f * cbF * cbF - 1.5f * uFsq, drF);
+        const float cuB = cxi * uB[0] + cyi * uB[1] + czi * uB[2];
+        fi = fmaf(6.0f * wi * rr, cuB, fmaf(chi, gq - fb, fb));
+        // momentum exchange of this link (deviation form: the -2 w_i c_i
+        // parts cancel over the body's closed link set)
+        const float sum = fi + fb, dif = fi - fb;
+        const float s0 = -cxi * sum, s1 = -cyi * sum, s2 = -czi * sum;
+        const float m0 = fmaf(uB[0], dif, s0), m1 = fmaf(uB[1], dif, s1), m2 = fmaf(uB[2], dif, s2);
+        v[0] = s0;
+        v[1] = s1;
+        v[2] = s2;
+        v[3] = d[1] * s2 - d[2] * s1;
+        v[4] = d[2] * s0 - d[0] * s2;
+        v[5] = d[0] * s1 - d[1] * s0;
+        v[6] = m0;
+        v[7] = m1;
+        v[8] = m2;
+        v[9] = d[1] * m2 - d[2] * m1;
+        v[10] = d[2] * m0 - d[0] * m2;
+        v[11] = d[0] * m1 - d[1] * m0;
+    } else if (act) {
+        fi = sc >= 0 ? ldS(src + (long long)i * N + sc)
+                     : pull_edge<L, P>(p, src, (const float *)nullptr, x, y, z, cell, i);
+    }
+    // collision (or the streamed values of a node covered at t+1)
+    float out = fi;
+    if (a.owner_t1[cell] == 0) {
+        const float dr = warp_sum(fi);
+        float j0 = warp_sum(cxi * fi), j1 = warp_sum(cyi * fi), j2 = warp_sum(czi * fi);
+        if (p.has_force) {
+            j0 = fmaf(0.5f, p.gf[0], j0);
+            j1 = fmaf(0.5f, p.gf[1], j1);
+            j2 = fmaf(0.5f, p.gf[2], j2);
+        }
+        const float inv = 1.0f / (p.eq == 0 ? p.rho0f : 1.0f + dr);
+        const float u[3] = {j0 * inv, j1 * inv, j2 * inv};
+        const float usq15 = 1.5f * fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
+        const float cu = cxi * u[0] + cyi * u[1] + czi * u[2];
+        const float rr = p.eq == 0 ? p.rho0f : 1.0f + dr;
+        const float fe = wi * fmaf(rr, fmaf(cu, fmaf(4.5f, cu, 3.0f), -usq15), dr);
+        const float om = p.omegaf;
+        out = fmaf(-om, fi - fe, fi);
+        if (p.has_force) {
+            const float cg = cxi * p.gf[0] + cyi * p.gf[1] + czi * p.gf[2];
+            const float ug = u[0] * p.gf[0] + u[1] * p.gf[1] + u[2] * p.gf[2];
+            out = fmaf((1.0f - 0.5f * om) * wi, fmaf(9.0f * cu, cg, 3.0f * (cg - ug)), out);
+        }
+    }
+    if (act) stS(dst + (long long)i * N + cell, out);
+    // per-body fixed-point sums: one atomic per component when all the
+    // node's cut links belong to one body (the usual case)
+    nlinks += __popc(cutmask);
+    const int b0 = __shfl_sync(0xffffffffu, bi, __ffs(cutmask) - 1);
+    const bool one_body = __all_sync(0xffffffffu, o == 0 || bi == b0);
+    if (one_body) {
+        unsigned long long *acc = sb.acc + (long long)b0 * SERIES_ROW;
+#pragma unroll
+        for (int c = 0; c < ME_PER_LINK; ++c) {
+            const unsigned long long s = warp_sum_u64(to_fx(v[c]));
+            if (lane == c && s) atomicAdd(acc + (c < 6 ? c : c + 6), s);
+        }
+    } else if (o) {
+        unsigned long long *acc = sb.acc + (long long)bi * SERIES_ROW;
+        for (int c = 0; c < ME_PER_LINK; ++c) atomicAdd(acc + (c < 6 ? c : c + 6), to_fx(v[c]));
+    }
+}
+
+template <class L, class P>
+__global__ void __launch_bounds__(BND_THREADS) k_bnd(Params p, BndArgs a, StepBufs sb) {
+    const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long ns = (long long)min((unsigned long long)a.static_cap, *a.static_cnt);
     const long long nm = (long long)min((unsigned long long)a.mov_cap, *a.mov_cnt);
-    const S *src = (const S *)sb.src;
-    S *dst = (S *)sb.dst;
-    const long long N = p.N;
     unsigned nlinks = 0;
-
     for (long long k = warp; k < ns + nm; k += nwarps) {
         const bool from_static = k < ns;
         const long long cell = from_static ? a.static_cells[k] : a.mov_cells[k - ns];
-        if (a.owner_t[cell] != 0) continue; // warp-uniform
-        int x, y, z;
-        coords_of(p, cell, x, y, z);
-        const long long sc = i == 0 ? cell : nbr<L>(p, x, y, z, i, 1);
-        const uint16_t o = (act && i > 0 && sc >= 0) ? a.owner_t[sc] : (uint16_t)0;
-        if (from_static) { // a moving body next to it: that body's list has it
-            const bool mv = o != 0 && a.bodies[o - 1].moving;
-            if (__any_sync(0xffffffffu, mv)) continue;
-        }
-        const unsigned cutmask = __ballot_sync(0xffffffffu, o != 0);
-        if (!cutmask) continue;
-        // moments of the collided populations fhat(x, t) (= those of f(x, t))
-        const float fo = act ? ldP(src + (long long)i * N + cell) : 0.0f;
-        const float drF = warp_sum(fo);
-        float uF[3];
-        {
-            float j0 = warp_sum(cxi * fo), j1 = warp_sum(cyi * fo), j2 = warp_sum(czi * fo);
-            if (p.has_force) {
-                j0 -= 0.5f * p.gf[0];
-                j1 -= 0.5f * p.gf[1];
-                j2 -= 0.5f * p.gf[2];
-            }
-            const float inv = 1.0f / (p.eq == 0 ? p.rho0f : 1.0f + drF);
-            uF[0] = j0 * inv;
-            uF[1] = j1 * inv;
-            uF[2] = j2 * inv;
-        }
-        const float fb = __shfl_sync(0xffffffffu, fo, ib); // fhat_ib(x, t)
-        float fi = 0.0f;
-        float v[ME_PER_LINK];
-#pragma unroll
-        for (int c = 0; c < ME_PER_LINK; ++c) v[c] = 0.0f;
-        const int bi = (int)o - 1;
-        if (o) {
-            const BodyDev &Bi = a.bodies[bi];
-            const double *Pf = a.poses + (long long)bi * POSE_STRIDE + 12; // floor, frac of the pose at t
-            float d[3];
-            const int c3[3] = {x, y, z};
-            for (int q = 0; q < 3; ++q) {
-                int kk = c3[q] - (int)Pf[q];
-                if (p.per[q]) {
-                    const int n = axis_len(p, q);
-                    if (2 * kk > n) kk -= n;
-                    else if (2 * kk < -n) kk += n;
-                }
-                d[q] = (float)kk - (float)Pf[3 + q];
-            }
-            const float dl = link_delta_f(Bi, d, cxi, cyi, czi);
-            const float rb[3] = {d[0] - dl * cxi, d[1] - dl * cyi, d[2] - dl * czi};
-            const float W0 = (float)Bi.W[0], W1 = (float)Bi.W[1], W2 = (float)Bi.W[2];
-            const float uB[3] = {(float)Bi.U[0] + (W1 * rb[2] - W2 * rb[1]),
-                                 (float)Bi.U[1] + (W2 * rb[0] - W0 * rb[2]),
-                                 (float)Bi.U[2] + (W0 * rb[1] - W1 * rb[0])};
-            float ubf[3], chi;
-            if (dl < 0.5f) {
-                // u_bf = u_G = u(x_F + c_i, t), chi = (2 Delta - 1)/(tau - 2)
-                const long long G = nbr<L>(p, x, y, z, ib, 1); // x - c_ib = x + c_i
-                if (G >= 0 && a.owner_t[G] == 0) {
-                    float drG;
-                    moments_hat<L>(p, src, G, drG, ubf);
-                    chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
-                } else {
-                    ubf[0] = uF[0];
-                    ubf[1] = uF[1];
-                    ubf[2] = uF[2];
-                    chi = 0.0f;
-                    atomicAdd(&sb.counters[0], 1ull);
-                }
-            } else {
-                // u_bf = u_F + 3/(2 Delta) (u_B - u_F), chi = (2 Delta - 1)/(tau + 1/2)
-                const float k3 = 3.0f / (2.0f * dl);
-                for (int q = 0; q < 3; ++q) ubf[q] = fmaf(k3, uB[q] - uF[q], uF[q]);
-                chi = (2.0f * dl - 1.0f) / ((float)p.tau + 0.5f);
-            }
-            // fictitious equilibrium g_ib (Eq. Fillipova_equilibrium), deviation form
-            const float cbu = -(cxi * ubf[0] + cyi * ubf[1] + czi * ubf[2]);
-            const float cbF = -(cxi * uF[0] + cyi * uF[1] + czi * uF[2]);
-            const float uFsq = uF[0] * uF[0] + uF[1] * uF[1] + uF[2] * uF[2];
-            const float rr = p.eq == 0 ? p.rho0f : 1.0f + drF;
-            const float gq = wi * fmaf(rr, 3.0f * cbu + 4.5f * cbF * cbF - 1.5f * uFsq, drF);
-            const float cuB = cxi * uB[0] + cyi * uB[1] + czi * uB[2];
-            fi = fmaf(6.0f * wi * rr, cuB, fmaf(chi, gq - fb, fb));
-            // momentum exchange of this link (deviation form: the -2 w_i c_i
-            // parts cancel over the body's closed link set)
-            const float sum = fi + fb, dif = fi - fb;
-            const float s0 = -cxi * sum, s1 = -cyi * sum, s2 = -czi * sum;
-            const float m0 = fmaf(uB[0], dif, s0), m1 = fmaf(uB[1], dif, s1), m2 = fmaf(uB[2], dif, s2);
-            v[0] = s0;
-            v[1] = s1;
-            v[2] = s2;
-            v[3] = d[1] * s2 - d[2] * s1;
-            v[4] = d[2] * s0 - d[0] * s2;
-            v[5] = d[0] * s1 - d[1] * s0;
-            v[6] = m0;
-            v[7] = m1;
-            v[8] = m2;
-            v[9] = d[1] * m2 - d[2] * m1;
-            v[10] = d[2] * m0 - d[0] * m2;
-            v[11] = d[0] * m1 - d[1] * m0;
-        } else if (act) {
-            fi = sc >= 0 ? ldS(src + (long long)i * N + sc)
-                         : pull_edge<L, P>(p, src, (const float *)nullptr, x, y, z, cell, i);
-        }
-        // collision (or the streamed values of a node covered at t+1)
-        float out = fi;
-        if (a.owner_t1[cell] == 0) {
-            const float dr = warp_sum(fi);
-            float j0 = warp_sum(cxi * fi), j1 = warp_sum(cyi * fi), j2 = warp_sum(czi * fi);
-            if (p.has_force) {
-                j0 = fmaf(0.5f, p.gf[0], j0);
-                j1 = fmaf(0.5f, p.gf[1], j1);
-                j2 = fmaf(0.5f, p.gf[2], j2);
-            }
-            const float inv = 1.0f / (p.eq == 0 ? p.rho0f : 1.0f + dr);
-            const float u[3] = {j0 * inv, j1 * inv, j2 * inv};
-            const float usq15 = 1.5f * fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
-            const float cu = cxi * u[0] + cyi * u[1] + czi * u[2];
-            const float rr = p.eq == 0 ? p.rho0f : 1.0f + dr;
-            const float fe = wi * fmaf(rr, fmaf(cu, fmaf(4.5f, cu, 3.0f), -usq15), dr);
-            const float om = p.omegaf;
-            out = fmaf(-om, fi - fe, fi);
-            if (p.has_force) {
-                const float cg = cxi * p.gf[0] + cyi * p.gf[1] + czi * p.gf[2];
-                const float ug = u[0] * p.gf[0] + u[1] * p.gf[1] + u[2] * p.gf[2];
-                out = fmaf((1.0f - 0.5f * om) * wi, fmaf(9.0f * cu, cg, 3.0f * (cg - ug)), out);
-            }
-        }
-        if (act) stS(dst + (long long)i * N + cell, out);
-        // per-body fixed-point sums: one atomic per component when all the
-        // node's cut links belong to one body (the usual case)
-        nlinks += __popc(cutmask);
-        const int b0 = __shfl_sync(0xffffffffu, bi, __ffs(cutmask) - 1);
-        const bool one_body = __all_sync(0xffffffffu, o == 0 || bi == b0);
-        if (one_body) {
-            unsigned long long *acc = sb.acc + (long long)b0 * SERIES_ROW;
-#pragma unroll
-            for (int c = 0; c < ME_PER_LINK; ++c) {
-                const unsigned long long s = warp_sum_u64(to_fx(v[c]));
-                if (lane == c && s) atomicAdd(acc + (c < 6 ? c : c + 6), s);
-            }
-        } else if (o) {
-            unsigned long long *acc = sb.acc + (long long)bi * SERIES_ROW;
-            for (int c = 0; c < ME_PER_LINK; ++c) atomicAdd(acc + (c < 6 ? c : c + 6), to_fx(v[c]));
-        }
+        bnd_node<L, P>(p, a, sb, cell, from_static, nlinks);
     }
     if (lane == 0 && nlinks) atomicAdd(&sb.counters[3], (unsigned long long)nlinks);
 }

@@ -57,6 +57,26 @@ struct BndArgs {
     const double *poses;
 };
 
+// One resident solve of a serving batch (reduced-precision modes, static
+// bodies): everything the batched kernels need to step it.
+struct SolveDev {
+    Params p;
+    int Q;
+    int active;         // 0 once t reaches t_end
+    long long t, t_end; // current step, step at which the solve is complete
+    void *pop[2];
+    uint8_t *flags;
+    const uint16_t *owner; // solid owner (static bodies: constant)
+    const BodyDev *bodies;
+    const double *poses;
+    const uint32_t *bn_static;
+    const unsigned long long *bn_cnt;
+    long long bn_cap;
+    unsigned long long *acc;
+    double *series;
+    unsigned long long *counters;
+};
+
 // precision: 0 FP64, 1 FP32, 2 FP16; Q: 9 or 19
 cudaError_t launch_init(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
                         const double u0[3], cudaStream_t s);
@@ -89,6 +109,12 @@ cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_
 // momentum exchange, collision) -- runs beside k_bulk
 cudaError_t launch_bnd(int Q, int prec, const Params &p, const BndArgs &a, const StepBufs &sb, int grid,
                        cudaStream_t s);
+// batched serving kernels: one tick = bulk (per lattice), boundary nodes (per
+// lattice), finish (every solve)
+cudaError_t launch_bbulk(int Q, int prec, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s);
+cudaError_t launch_bbnd(int Q, int prec, const SolveDev *solves, const int *slots, const long long *node_pre,
+                        int nslots, int grid, cudaStream_t s);
+cudaError_t launch_bfinish(SolveDev *solves, const int *slots, int nslots, cudaStream_t s);
 // boundary-node lists of step t from scratch (all bodies)
 cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 

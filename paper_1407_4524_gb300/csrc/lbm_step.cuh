@@ -357,16 +357,13 @@ __global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
 }
 
-// pull-stream + moments + BGK collision over every fluid node
+// pull-stream + moments + BGK collision of one node (x, y, z)
 template <class L, class P>
-__global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename P::S *__restrict__ src,
-                                                       typename P::S *__restrict__ dst,
-                                                       const uint8_t *__restrict__ flags,
-                                                       const typename P::C *__restrict__ mac_t,
-                                                       typename P::C *__restrict__ mac_t1) {
+__device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *__restrict__ src,
+                                          typename P::S *__restrict__ dst, const uint8_t *__restrict__ flags,
+                                          const typename P::C *__restrict__ mac_t, typename P::C *__restrict__ mac_t1,
+                                          int x, int y, int z) {
     using C = typename P::C;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.nx) return;
     const long long cell = cell_of(p, x, y, z);
     const uint8_t fl = __ldg(flags + cell);
     if (fl & FL_SOLID) return;
@@ -392,6 +389,18 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename 
     }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
+}
+
+// pull-stream + moments + BGK collision over every fluid node
+template <class L, class P>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename P::S *__restrict__ src,
+                                                       typename P::S *__restrict__ dst,
+                                                       const uint8_t *__restrict__ flags,
+                                                       const typename P::C *__restrict__ mac_t,
+                                                       typename P::C *__restrict__ mac_t1) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx) return;
+    bulk_node<L, P>(p, src, dst, flags, mac_t, mac_t1, x, y, z);
 }
 
 // Work of one cut link j of body b: the wall value fhat_i(x_A, t) of Eq.

@@ -49,6 +49,14 @@ class lbm_body(C.Structure):
     ]
 
 
+class lbm_batch_desc(C.Structure):
+    _fields_ = [
+        ("device", C.c_int), ("max_slots", C.c_int), ("ticks_per_launch", C.c_int), ("reserved", C.c_int),
+        ("budget_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+        ("alloc_ctx", C.c_void_p),
+    ]
+
+
 class lbm_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("step", "cells", "fluid_cells", "links", "fallback_links",
                                           "covered", "uncovered", "device_bytes", "h2d_bytes", "d2h_bytes")]
@@ -93,6 +101,19 @@ def load(build_if_missing: bool = True):
     lib.lbm_set_kernel_timing.argtypes = [P, C.c_int]
     lib.lbm_kernel_time.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.lbm_launches_per_step.argtypes = [P, C.POINTER(C.c_int)]
+    lib.lbm_batch_create.argtypes = [C.POINTER(lbm_batch_desc), C.POINTER(C.c_void_p)]
+    lib.lbm_batch_destroy.argtypes = [P]
+    lib.lbm_batch_solve_bytes.argtypes = [C.POINTER(lbm_domain_desc), C.POINTER(lbm_body), C.c_int, C.c_int64,
+                                          C.POINTER(C.c_int64)]
+    lib.lbm_batch_admit.argtypes = [P, C.POINTER(lbm_domain_desc), C.POINTER(lbm_body), C.c_int, C.c_int64,
+                                    C.POINTER(C.c_int)]
+    lib.lbm_batch_run.argtypes = [P, C.c_int]
+    lib.lbm_batch_poll.argtypes = [P, P, C.c_int, C.POINTER(C.c_int)]
+    lib.lbm_batch_get_force_torque.argtypes = [P, C.c_int, C.c_int64, C.c_int64, C.c_int, P]
+    lib.lbm_batch_time.restype = C.c_int64
+    lib.lbm_batch_time.argtypes = [P, C.c_int]
+    lib.lbm_batch_release.argtypes = [P, C.c_int]
+    lib.lbm_batch_usage.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
     _lib = lib
     return lib
 
@@ -130,6 +151,44 @@ def body_struct(b: dict) -> lbm_body:
     return s
 
 
+def domain_desc(spec: dict, device: int = 0, series_capacity: int = 0):
+    """(lbm_domain_desc, Q, (nx, ny, nz)) of a problem dict; stream and
+    allocator are left unset."""
+    q = {"D2Q9": 9, "D3Q19": 19}[spec["lattice"]]
+    n = tuple(spec["n"]) + (1,) * (3 - len(spec["n"]))
+    d = lbm_domain_desc()
+    d.lattice, d.nx, d.ny, d.nz = q, n[0], n[1], n[2]
+    d.precision = PRECISION[spec.get("precision", "fp32")]
+    d.equilibrium = {"incomp": 0, "standard": 1}[spec.get("eq", "incomp")]
+    edges = spec.get("edges", {})
+    k = 0
+    for ax in "xyz":
+        e = edges.get(ax, "periodic")
+        lo, hi = (e, e) if isinstance(e, str) else e
+        d.edge[k], d.edge[k + 1] = EDGE[lo], EDGE[hi]
+        k += 2
+    inlet = spec.get("inlet", {})
+    d.inlet_profile = 1 if inlet.get("profile", "uniform") == "parabolic" else 0
+    d.u_in = float(inlet.get("u", 0.0))
+    d.refill = {"uB": 0, "ubar": 1}[spec.get("refill", "uB")]
+    g = spec.get("force")
+    d.has_force = int(g is not None)
+    for j in range(3):
+        d.force[j] = float(g[j]) if g is not None and j < len(g) else 0.0
+    u0 = tuple(spec.get("u0", (0.0, 0.0, 0.0)))
+    for j in range(3):
+        d.u0[j] = float(u0[j]) if j < len(u0) else 0.0
+    d.tau = float(spec["tau"])
+    d.rho0 = float(spec.get("rho0", 1.0))
+    d.device = int(device)
+    d.series_capacity = int(series_capacity or spec.get("series_capacity", 0) or 0)
+    return d, q, n
+
+
+def body_array(bodies):
+    return (lbm_body * max(len(bodies), 1))(*[body_struct(b) for b in bodies])
+
+
 class _TorchAllocator:
     """Routes the library's device allocations through torch's caching allocator."""
 
@@ -162,34 +221,7 @@ class Domain:
         lib = load()
         self.lib = lib
         self.spec = spec
-        q = {"D2Q9": 9, "D3Q19": 19}[spec["lattice"]]
-        n = tuple(spec["n"]) + (1,) * (3 - len(spec["n"]))
-        d = lbm_domain_desc()
-        d.lattice, d.nx, d.ny, d.nz = q, n[0], n[1], n[2]
-        d.precision = PRECISION[spec.get("precision", "fp32")]
-        d.equilibrium = {"incomp": 0, "standard": 1}[spec.get("eq", "incomp")]
-        edges = spec.get("edges", {})
-        k = 0
-        for ax in "xyz":
-            e = edges.get(ax, "periodic")
-            lo, hi = (e, e) if isinstance(e, str) else e
-            d.edge[k], d.edge[k + 1] = EDGE[lo], EDGE[hi]
-            k += 2
-        inlet = spec.get("inlet", {})
-        d.inlet_profile = 1 if inlet.get("profile", "uniform") == "parabolic" else 0
-        d.u_in = float(inlet.get("u", 0.0))
-        d.refill = {"uB": 0, "ubar": 1}[spec.get("refill", "uB")]
-        g = spec.get("force")
-        d.has_force = int(g is not None)
-        for j in range(3):
-            d.force[j] = float(g[j]) if g is not None and j < len(g) else 0.0
-        u0 = tuple(spec.get("u0", (0.0, 0.0, 0.0)))
-        for j in range(3):
-            d.u0[j] = float(u0[j]) if j < len(u0) else 0.0
-        d.tau = float(spec["tau"])
-        d.rho0 = float(spec.get("rho0", 1.0))
-        d.device = int(device)
-        d.series_capacity = int(series_capacity or spec.get("series_capacity", 0) or 0)
+        d, q, n = domain_desc(spec, device, series_capacity)
         self._alloc = None
         self.stream = stream
         stream_ptr = 0
@@ -297,3 +329,105 @@ class Domain:
         v = C.c_int()
         _check(self.lib.lbm_launches_per_step(self.h, C.byref(v)))
         return int(v.value)
+
+
+class Batch:
+    """A serving batch (include/lbm.h, lbm_batch_*): many static-body solves in
+    the reduced-precision modes resident on one GPU, admitted against a
+    device-memory budget and advanced together, ``ticks_per_launch`` steps per
+    replay of the batch's tick graph."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, ticks_per_launch: int = 32, device: int = 0,
+                 torch_allocator: bool = True):
+        lib = load()
+        self.lib = lib
+        import torch
+        if not torch.cuda.is_available():
+            raise LbmError("a serving batch needs a CUDA device")
+        self.device = int(device)
+        # a stream of its own: the tick graph is captured on it (the legacy
+        # default stream cannot be captured)
+        self.stream = torch.cuda.Stream(device)
+        stream_ptr = int(self.stream.cuda_stream)
+        d = lbm_batch_desc()
+        d.device, d.max_slots, d.ticks_per_launch = self.device, int(max_slots), int(ticks_per_launch)
+        d.budget_bytes = int(budget_bytes)
+        d.stream = C.c_void_p(stream_ptr)
+        self._alloc = _TorchAllocator(self.device, stream_ptr) if torch_allocator else None
+        if self._alloc is not None:
+            d.alloc, d.free = self._alloc.alloc, self._alloc.free
+        self._desc = d
+        h = C.c_void_p()
+        _check(lib.lbm_batch_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.ticks_per_launch = int(ticks_per_launch) or 32
+        self.specs = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _steps(spec, steps):
+        return int(spec["steps"] if steps is None else steps)
+
+    def solve_bytes(self, spec: dict, steps: int | None = None) -> int:
+        d, _, _ = domain_desc(spec, self.device)
+        bodies = list(spec.get("bodies", []))
+        out = C.c_int64()
+        _check(self.lib.lbm_batch_solve_bytes(C.byref(d), body_array(bodies), len(bodies),
+                                              self._steps(spec, steps), C.byref(out)))
+        return int(out.value)
+
+    def admit(self, spec: dict, steps: int | None = None):
+        """slot index, or None when the solve does not fit (budget or slots)"""
+        d, _, _ = domain_desc(spec, self.device)
+        bodies = list(spec.get("bodies", []))
+        slot = C.c_int(-1)
+        rc = self.lib.lbm_batch_admit(self.h, C.byref(d), body_array(bodies), len(bodies),
+                                      self._steps(spec, steps), C.byref(slot))
+        if rc == 2:  # LBM_ERR_OOM
+            return None
+        _check(rc)
+        self.specs[slot.value] = spec
+        return int(slot.value)
+
+    def run(self, n: int = 1):
+        _check(self.lib.lbm_batch_run(self.h, int(n)))
+
+    def poll(self) -> list:
+        cap = max(len(self.specs), 1)
+        out = (C.c_int * cap)()
+        cnt = C.c_int()
+        _check(self.lib.lbm_batch_poll(self.h, out, cap, C.byref(cnt)))
+        return [int(out[k]) for k in range(cnt.value)]
+
+    def time(self, slot: int) -> int:
+        return int(self.lib.lbm_batch_time(self.h, int(slot)))
+
+    def force_torque(self, slot: int, kind: str = "static", first: int = 0, count: int | None = None):
+        nb = len(self.specs[slot].get("bodies", []))
+        if count is None:
+            count = self.time(slot) - first
+        out = np.zeros((count, max(nb, 1), 6))
+        if nb and count:
+            _check(self.lib.lbm_batch_get_force_torque(self.h, int(slot), int(first), int(count),
+                                                       FT_KIND[kind], out.ctypes.data))
+        return out[:, :nb]
+
+    def release(self, slot: int):
+        _check(self.lib.lbm_batch_release(self.h, int(slot)))
+        self.specs.pop(slot, None)
+
+    def usage(self):
+        r = C.c_int()
+        b = C.c_int64()
+        _check(self.lib.lbm_batch_usage(self.h, C.byref(r), C.byref(b)))
+        return int(r.value), int(b.value)

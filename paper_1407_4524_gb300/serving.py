@@ -1,0 +1,117 @@
+"""Serving loop over a request trace: continuous batching versus one solve at a
+time on the same GPU.
+
+Requests are problem dicts with ``arrival_s`` (seconds after the start of the
+run) and ``steps`` (see ``workloads.serving_trace``).  Both loops run in real
+time: a request can be admitted only once its arrival time has passed, and its
+latency is its completion time minus its arrival time (queueing included).
+A request is complete when its whole force/torque series is back on the host.
+
+``serve_batched`` keeps a FIFO queue of arrived requests and admits from its
+head into a ``lbm.Batch`` while slots and the memory budget allow; the batch
+advances every resident solve together, ``ticks_per_launch`` steps per graph
+replay, and finished solves are read back and released between replays.
+``serve_sequential`` solves the requests one after another in arrival order,
+each as a standalone ``lbm.Domain`` advanced by ``lbm_step``.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+
+import numpy as np
+
+from . import lbm
+from .workloads import cells
+
+
+def _summary(lat, makespan, cell_updates, n):
+    lat = np.asarray(lat, dtype=float)
+    return {
+        "requests": int(n),
+        "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+        "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+        "mean_s": float(lat.mean()) if lat.size else None,
+        "makespan_s": float(makespan),
+        "cell_updates": int(cell_updates),
+        "mlups": float(cell_updates / makespan / 1e6) if makespan > 0 else None,
+    }
+
+
+def _wait_until(t0, t_abs):
+    while True:
+        now = time.perf_counter() - t0
+        if now >= t_abs:
+            return
+        time.sleep(min(t_abs - now, 0.002))
+
+
+def serve_batched(trace, budget_bytes: int, max_slots: int = 64, ticks_per_launch: int = 32,
+                  launches_per_round: int = 1, device: int = 0, keep_series: bool = False):
+    """Continuous batching.  Returns (summary dict, {request id: force/torque
+    series} if keep_series)."""
+    reqs = sorted(trace, key=lambda r: r["arrival_s"])
+    batch = lbm.Batch(budget_bytes, max_slots=max_slots, ticks_per_launch=ticks_per_launch, device=device)
+    pending = deque(reqs)
+    waiting = deque()
+    slot_req = {}
+    lat, series = [], {}
+    updates = 0
+    t0 = time.perf_counter()
+    try:
+        while pending or waiting or slot_req:
+            now = time.perf_counter() - t0
+            while pending and pending[0]["arrival_s"] <= now:
+                waiting.append(pending.popleft())
+            while waiting:
+                r = waiting[0]
+                slot = batch.admit(r)
+                if slot is None:
+                    if not slot_req:
+                        raise lbm.LbmError(f"request {r.get('id')} does not fit an empty batch")
+                    break
+                waiting.popleft()
+                slot_req[slot] = r
+            if not slot_req:
+                if pending:
+                    _wait_until(t0, pending[0]["arrival_s"])
+                continue
+            batch.run(launches_per_round)
+            for slot in batch.poll():
+                r = slot_req.pop(slot)
+                ft = batch.force_torque(slot, "static")
+                done = time.perf_counter() - t0
+                lat.append(done - r["arrival_s"])
+                updates += cells(r) * int(r["steps"])
+                if keep_series:
+                    series[r.get("id", len(series))] = ft
+                batch.release(slot)
+        makespan = time.perf_counter() - t0
+    finally:
+        batch.close()
+    return _summary(lat, makespan, updates, len(reqs)), series
+
+
+def serve_sequential(trace, device: int = 0, keep_series: bool = False):
+    """One solve at a time, in arrival order."""
+    import torch
+    reqs = sorted(trace, key=lambda r: r["arrival_s"])
+    lat, series = [], {}
+    updates = 0
+    t0 = time.perf_counter()
+    for r in reqs:
+        _wait_until(t0, r["arrival_s"])
+        dom = lbm.Domain(r, device=device, series_capacity=int(r["steps"]))
+        try:
+            dom.step(int(r["steps"]))
+            ft = dom.force_torque("static")
+        finally:
+            dom.close()
+        done = time.perf_counter() - t0
+        lat.append(done - r["arrival_s"])
+        updates += cells(r) * int(r["steps"])
+        if keep_series:
+            series[r.get("id", len(series))] = ft
+    torch.cuda.synchronize(device)
+    makespan = time.perf_counter() - t0
+    return _summary(lat, makespan, updates, len(reqs)), series

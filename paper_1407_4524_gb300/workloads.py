@@ -130,10 +130,10 @@ SERVING_D3Q19_SIZES = ((64, 64, 64), (128, 64, 64), (192, 96, 96))
 
 
 def serving_request(rng, lattice: str | None = None, precision: str = "fp16") -> dict:
-    """One served solve: D2Q9 (channel, parabolic inflow, walls) or D3Q19
-    (channel, uniform inflow, periodic cross-section), one body of radius
-    U[5,15] near x = nx/4, tau U[0.52,1.0], inflow U[0.01,0.05],
-    steps U{2000..20000}."""
+    """One served solve: D2Q9 (channel, parabolic inflow, walls; fluid at
+    rest) or D3Q19 (channel, uniform inflow, periodic cross-section; fluid
+    starting as the inflow stream), one body of radius U[5,15] near x = nx/4,
+    tau U[0.52,1.0], inflow U[0.01,0.05], steps U{2000..20000}."""
     if lattice is None:
         lattice = "D2Q9" if rng.uniform() < 0.5 else "D3Q19"
     tau = float(rng.uniform(0.52, 1.0))
@@ -157,7 +157,7 @@ def serving_request(rng, lattice: str | None = None, precision: str = "fp16") ->
     zc = float(rng.uniform(0.0, n[2]))
     return dict(name="serving_3d", lattice=lattice, n=n, tau=tau,
                 edges={"x": ("inlet", "outlet"), "y": "periodic", "z": "periodic"},
-                inlet={"profile": "uniform", "u": u_in},
+                inlet={"profile": "uniform", "u": u_in}, u0=(u_in, 0.0, 0.0),
                 bodies=[dict(shape="sphere", R=R, X0=(xc, yc, zc))],
                 precision=precision, steps=steps)
 
