@@ -19,10 +19,18 @@ namespace {
 // work[k] = (slot, first cell): block k does BULK_THREADS consecutive cells
 // of one solve (flat index, so small grids waste no threads on short rows)
 template <class L, class P>
-__global__ void __launch_bounds__(BULK_THREADS) k_bbulk(const SolveDev *__restrict__ solves,
-                                                        const int2 *__restrict__ work) {
+__global__ void __launch_bounds__(BULK_THREADS, BULK_MIN_BLOCKS) k_bbulk(const SolveDev *__restrict__ solves,
+                                                                         const int2 *__restrict__ work) {
+    // the solve's record in shared memory: its parameters are read many times
+    __shared__ SolveDev sv;
     const int2 w = work[blockIdx.x];
-    const SolveDev &sv = solves[w.x];
+    {
+        static_assert(sizeof(SolveDev) % 4 == 0, "SolveDev is copied as 32-bit words");
+        const int *from = (const int *)(solves + w.x);
+        int *to = (int *)&sv;
+        for (int k = threadIdx.x; k < (int)(sizeof(SolveDev) / 4); k += blockDim.x) to[k] = from[k];
+    }
+    __syncthreads();
     if (!sv.active) return;
     const long long cell = (long long)w.y + threadIdx.x;
     if (cell >= sv.p.N) return;

@@ -30,10 +30,16 @@ template <class L, class P> cudaError_t links_t(const Params &p, const StepBufs 
     return cudaGetLastError();
 }
 
+// fully periodic domains: the kernel without the face rule (fewer registers)
 template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
-    k_bulk<L, P><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, (const typename P::S *)sb.src, (typename P::S *)sb.dst,
-                                                         sb.flags, (const typename P::C *)sb.mac_t,
-                                                         (typename P::C *)sb.mac_t1);
+    if (p.nonper)
+        k_bulk<L, P, true><<<bulk_grid(p), bulk_block(p), 0, s>>>(
+            p, (const typename P::S *)sb.src, (typename P::S *)sb.dst, sb.flags, (const typename P::C *)sb.mac_t,
+            (typename P::C *)sb.mac_t1);
+    else
+        k_bulk<L, P, false><<<bulk_grid(p), bulk_block(p), 0, s>>>(
+            p, (const typename P::S *)sb.src, (typename P::S *)sb.dst, sb.flags, (const typename P::C *)sb.mac_t,
+            (typename P::C *)sb.mac_t1);
     return cudaGetLastError();
 }
 

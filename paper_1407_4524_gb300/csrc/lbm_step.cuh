@@ -32,6 +32,7 @@
 namespace lbm {
 
 constexpr int BULK_THREADS = 128;
+constexpr int BULK_MIN_BLOCKS = 8; // reduced precision: <= 64 registers, half the warps resident
 constexpr int LINK_THREADS = 256;
 constexpr int IMP_THREADS = 128;
 
@@ -294,29 +295,126 @@ __device__ __noinline__ typename P::C pull_edge(const Params &p, const typename 
     return ldS(src + (long long)i * p.N + cell_of(p, s[0], s[1], s[2]));
 }
 
+// Momentum terms of the wall / inlet links of one node (Delta = 1/2, chi = 0:
+// moving bounce-back, u_B = 0 on walls, the inlet profile on inlet links; a
+// wall wins at corners) -- the same expressions as pull_edge.
+template <class L, class P>
+__device__ __forceinline__ void face_terms(const Params &p, const typename P::S *__restrict__ src,
+                                        const typename P::C *__restrict__ mac_t, int y, long long cell,
+                                        unsigned bounce, unsigned inlet_only, typename P::C *f) {
+    if constexpr (P::exact) {
+        const double rhow = p.eq == 0 ? p.rho0 : mac_t[4 * cell];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            if (!((bounce >> i) & 1u)) continue;
+            const double uB0 = ((inlet_only >> i) & 1u) ? inlet_u(p, y, L::cy(i)) : 0.0;
+            const double uB[3] = {uB0, 0.0, 0.0};
+            const double cuB = (double)L::cx(i) * uB[0] + (double)L::cy(i) * uB[1] + (double)L::cz(i) * uB[2];
+            f[i] = f[i] + 2.0 * L::template w<double>(i) * rhow * 3.0 * cuB;
+        }
+    } else {
+        float rhow = p.rho0f;
+        if (p.eq != 0) {
+            float dr, uu[3];
+            moments_hat<L>(p, src, cell, dr, uu);
+            rhow = 1.0f + dr;
+        }
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            if (!((bounce >> i) & 1u)) continue;
+            const double uB0 = ((inlet_only >> i) & 1u) ? inlet_u(p, y, L::cy(i)) : 0.0;
+            const float cuB = (float)L::cx(i) * (float)uB0;
+            f[i] = fmaf(6.0f * L::template w<float>(i) * rhow, cuB, (float)f[i]);
+        }
+    }
+}
+
 __device__ __forceinline__ bool on_edge(const Params &p, int x, int y, int z) {
     return (!p.per[0] && (x == 0 || x == p.nx - 1)) || (!p.per[1] && (y == 0 || y == p.ny - 1)) ||
            (!p.per[2] && (z == 0 || z == p.nz - 1));
 }
 
-// f_i(x, t+1) for all i at node (x,y,z)
-template <class L, class P>
+// Directions whose component along `axis` equals `sgn` (bit i = direction i).
+template <class L> __host__ __device__ constexpr unsigned dir_mask(int axis, int sgn) {
+    unsigned m = 0u;
+    for (int i = 0; i < L::Q; ++i) {
+        const int c = axis == 0 ? L::cx(i) : (axis == 1 ? L::cy(i) : L::cz(i));
+        if (c == sgn) m |= 1u << i;
+    }
+    return m;
+}
+
+// Source coordinates along one axis for c = +1 (m) and c = -1 (pp), with the
+// face rule of pull_edge: periodic faces wrap, an outlet repeats the last
+// column, a wall or inlet face makes the link a bounce link.  fl collects,
+// per axis a, bounce bits (2a: c = +1, 2a+1: c = -1), wall bits (8 + ...)
+// and inlet bits (16 + ...).
+__device__ __forceinline__ void face_axis(int v, int n, int per, int e_lo, int e_hi, int axis, int &m, int &pp,
+                                          unsigned &fl) {
+    m = v - 1;
+    pp = v + 1;
+    if (v == 0) {
+        if (per || e_lo == 0 || e_lo == 3) m = n - 1;
+        else fl |= (1u | (e_lo == 1 ? 1u << 8 : 0u) | (e_lo == 2 ? 1u << 16 : 0u)) << (2 * axis);
+    }
+    if (v == n - 1) {
+        if (per || e_hi == 0) pp = 0;
+        else if (e_hi == 3) pp = n - 1;
+        else fl |= (2u | (e_hi == 1 ? 2u << 8 : 0u) | (e_hi == 2 ? 2u << 16 : 0u)) << (2 * axis);
+    }
+}
+
+// the direction mask selected by the six per-axis bits of fl starting at bit `base`
+template <class L> __device__ __forceinline__ unsigned face_dirs(unsigned fl, int base) {
+    return ((fl >> base) & 1u ? dir_mask<L>(0, 1) : 0u) | ((fl >> (base + 1)) & 1u ? dir_mask<L>(0, -1) : 0u) |
+           ((fl >> (base + 2)) & 1u ? dir_mask<L>(1, 1) : 0u) | ((fl >> (base + 3)) & 1u ? dir_mask<L>(1, -1) : 0u) |
+           ((fl >> (base + 4)) & 1u ? dir_mask<L>(2, 1) : 0u) | ((fl >> (base + 5)) & 1u ? dir_mask<L>(2, -1) : 0u);
+}
+
+// f_i(x, t+1) for all i at node (x,y,z).  Fully periodic domains, and warps
+// of a non-periodic domain with no node on a face, take the plain path;
+// other warps take the face path, where every direction applies the face
+// rule (the same values as pull_edge) and all Q loads are issued before any
+// is used.  Both paths give the same values at interior nodes.
+template <class L, class P, bool FACES = true>
 __device__ __forceinline__ void pull_all(const Params &p, const typename P::S *__restrict__ src,
                                          const typename P::C *__restrict__ mac_t, int x, int y, int z,
                                          long long cell, typename P::C f[]) {
-    if (p.nonper && on_edge(p, x, y, z)) {
-        for (int i = 0; i < L::Q; ++i) f[i] = pull_edge<L, P>(p, src, mac_t, x, y, z, cell, i);
+    bool plain = true;
+    if constexpr (FACES) plain = !p.nonper || !__any_sync(__activemask(), on_edge(p, x, y, z));
+    if (plain) {
+        const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
+            const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
+            const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
+            f[i] = ldS(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+        }
         return;
     }
-    const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+    if constexpr (FACES) {
+        int xm, xp, ym, yp, zm, zp;
+        unsigned fl = 0u;
+        face_axis(x, p.nx, p.per[0], p.edge[0], p.edge[1], 0, xm, xp, fl);
+        face_axis(y, p.ny, p.per[1], p.edge[2], p.edge[3], 1, ym, yp, fl);
+        face_axis(z, p.nz, p.per[2], p.edge[4], p.edge[5], 2, zm, zp, fl);
+        const unsigned bounce = face_dirs<L>(fl, 0);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
-        const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
-        const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
-        f[i] = ldS(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+        for (int i = 0; i < L::Q; ++i) {
+            const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
+            const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
+            const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
+            const long long idx = ((bounce >> i) & 1u) ? (long long)L::opp(i) * p.N + cell
+                                                       : (long long)i * p.N + cell_of(p, sx, sy, sz);
+            f[i] = ldS(src + idx);
+        }
+        if (bounce) {
+            const unsigned inlet_only = face_dirs<L>(fl, 16) & ~face_dirs<L>(fl, 8);
+            face_terms<L, P>(p, src, mac_t, y, cell, bounce, inlet_only, f);
+        }
     }
 }
 
@@ -358,7 +456,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *
 }
 
 // pull-stream + moments + BGK collision of one node (x, y, z)
-template <class L, class P>
+template <class L, class P, bool FACES = true>
 __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *__restrict__ src,
                                           typename P::S *__restrict__ dst, const uint8_t *__restrict__ flags,
                                           const typename P::C *__restrict__ mac_t, typename P::C *__restrict__ mac_t1,
@@ -371,7 +469,7 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
         if (fl & FL_BND) return; // boundary nodes: k_bnd
     }
     C f[L::Q];
-    pull_all<L, P>(p, src, mac_t, x, y, z, cell, f);
+    pull_all<L, P, FACES>(p, src, mac_t, x, y, z, cell, f);
     if constexpr (P::exact) {
         double rho, u[3];
         moments_x<L>(p, f, rho, u);
@@ -392,15 +490,15 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
 }
 
 // pull-stream + moments + BGK collision over every fluid node
-template <class L, class P>
-__global__ void __launch_bounds__(BULK_THREADS) k_bulk(Params p, const typename P::S *__restrict__ src,
+template <class L, class P, bool FACES>
+__global__ void __launch_bounds__(BULK_THREADS, P::exact ? 4 : BULK_MIN_BLOCKS) k_bulk(Params p, const typename P::S *__restrict__ src,
                                                        typename P::S *__restrict__ dst,
                                                        const uint8_t *__restrict__ flags,
                                                        const typename P::C *__restrict__ mac_t,
                                                        typename P::C *__restrict__ mac_t1) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= p.nx) return;
-    bulk_node<L, P>(p, src, dst, flags, mac_t, mac_t1, x, y, z);
+    bulk_node<L, P, FACES>(p, src, dst, flags, mac_t, mac_t1, x, y, z);
 }
 
 // Work of one cut link j of body b: the wall value fhat_i(x_A, t) of Eq.
