@@ -205,6 +205,30 @@ int lbm_get_series(lbm_domain *dom, int64_t first, int64_t count, double *out);
  * Synchronises. */
 int lbm_get_populations(lbm_domain *dom, double *out);
 
+/* lbm_get_populations without any device allocation (the paper has no
+ * counterpart; this is an interface for callers that may not allocate).
+ * lbm_get_populations stages the FP64 copy in a fresh N*Q-double device
+ * buffer.  A caller that holds its device memory to an exact budget (a
+ * serving batch filled up to its limit) has no room for that buffer, and a
+ * monitoring thread reading a domain while other streams run should not
+ * allocate either, since releasing plain CUDA memory synchronises the whole
+ * device.  This variant stages through one fixed scratch array that the
+ * library holds in its own device memory: at most
+ * LBM_NOALLOC_MAX_VALUES = 4,194,304 doubles (32 MiB), so it serves domains
+ * with N*Q <= 4,194,304 and returns LBM_ERR_ARG, with a message naming the
+ * limit, for larger ones (nothing is copied then).
+ * - The first call on a device (with that device current) looks up the
+ *   scratch address; later calls reuse it.  Make the first call before any
+ *   stream capture on that device.
+ * - No part of the scratch has to start at zero: a call writes every value it
+ *   copies out.
+ * - The scratch is shared by every domain on the device: calls that overlap
+ *   in time (other host threads, or work still in flight on another stream)
+ *   race on it, so the caller serialises them.
+ * Output, layout and synchronisation as lbm_get_populations. */
+#define LBM_NOALLOC_MAX_VALUES 4194304
+int lbm_get_populations_noalloc(lbm_domain *dom, double *out);
+
 /* Owning body index of every node at the current step (-1: fluid),
  * out[nz][ny][nx].  Synchronises. */
 int lbm_get_solid(lbm_domain *dom, int32_t *out);

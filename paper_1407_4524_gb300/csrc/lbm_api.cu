@@ -1417,3 +1417,47 @@ int lbm_batch_usage(const lbm_batch *B, int *resident, int64_t *bytes) {
 }
 
 } // extern "C"
+
+// ---- population export without device allocation -----------------------------
+//
+// lbm_get_populations stages its FP64 copy in a buffer allocated per call.
+// Callers that must not allocate at that moment (a serving batch that holds
+// its memory to an exact budget; a monitoring thread that must not trigger
+// the device-wide synchronisation of releasing CUDA memory) use
+// lbm_get_populations_noalloc, which runs the same export kernel into this
+// fixed scratch array instead.  Its address is looked up once per device
+// (with the device current) and cached.  Nothing in it has to start at zero:
+// each call writes all N*Q values it copies out.  Concurrent calls share it
+// and would race.
+
+static __device__ __align__(256) double g_export_scratch[LBM_NOALLOC_MAX_VALUES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double *g_export_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+} // namespace
+
+extern "C" int lbm_get_populations_noalloc(lbm_domain *D, double *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    const long long n = D->p.N * D->Q;
+    if (n > (long long)LBM_NOALLOC_MAX_VALUES)
+        return fail(LBM_ERR_ARG, "lbm_get_populations_noalloc: the domain holds " + std::to_string(n) +
+                                     " population values; the fixed scratch holds at most " +
+                                     std::to_string((long long)LBM_NOALLOC_MAX_VALUES) +
+                                     " (use lbm_get_populations)");
+    const int dev = D->d.device;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(LBM_ERR_ARG, "device index out of range");
+    CK(cudaSetDevice(dev));
+    if (!g_export_scratch_ptr[dev]) { // set-up, once per device
+        double *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_export_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(LBM_ERR_CUDA, std::string("scratch address lookup: ") + cudaGetErrorString(e));
+        g_export_scratch_ptr[dev] = ptr;
+    }
+    double *scratch = g_export_scratch_ptr[dev];
+    CK(launch_export(D->Q, D->prec, D->p, D->pop[D->t & 1], scratch, D->s));
+    CK(cudaMemcpyAsync(out, scratch, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, D->s));
+    CK(cudaStreamSynchronize(D->s));
+    return LBM_OK;
+}
