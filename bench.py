@@ -299,6 +299,8 @@ def run_ours(args):
                 "kernel": "k_bulk (pull-stream + BGK collide)", "kernel_ms": round(bulk_avg_s * 1e3, 4),
                 "alg_bytes_per_launch": int(alg_bytes)}
     step_frac = (bulk_ms / max(1e-9, ms)) if world == 1 else None
+    dom.close()
+    serving = run_serving(args, dev) if (world == 1 and args.serving_requests > 0) else None
     cpu = cpu_baseline(spec, budget_s=args.cpu_budget) if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -312,11 +314,35 @@ def run_ours(args):
                    "bulk_share_of_step": round(step_frac, 4) if step_frac else None},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
-    dom.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_serving(args, dev):
+    """The serving stream: Poisson arrivals (20 req/s, seed 4524) of D2Q9 and
+    D3Q19 channel solves of uneven sizes, FP32 arithmetic with FP16 f - w
+    storage, run in real time twice on the same GPU: continuous batching
+    (lbm_batch_*) and one solve at a time (lbm_step per solve, FIFO).
+    Latency = completion (series back on the host) - arrival."""
+    from paper_1407_4524_gb300 import serving
+    from paper_1407_4524_gb300 import workloads as W
+    trace = W.serving_trace(n_requests=args.serving_requests, precision="fp16")
+    free, _ = __import__("torch").cuda.mem_get_info(dev)
+    budget = int(min(64 << 30, 0.5 * free))
+    batched, _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=256, ticks_per_launch=32, device=dev)
+    seq, _ = serving.serve_sequential(trace, device=dev)
+    return {
+        "trace": f"{len(trace)} requests, Poisson 20/s (seed 4524), D2Q9 {{128x64..1024x512}} / "
+                 f"D3Q19 {{64^3..192x96x96}}, 2000-20000 steps, fp16 storage",
+        "budget_bytes": budget,
+        "batched": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in batched.items()},
+        "one_at_a_time": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in seq.items()},
+        "mlups_ratio": round(batched["mlups"] / seq["mlups"], 3) if seq["mlups"] else None,
+        "p50_s": round(batched["p50_s"], 4), "p99_s": round(batched["p99_s"], 4),
+    }
 
 
 def _kernel_rev() -> str:
@@ -344,6 +370,8 @@ def main():
     ap.add_argument("--print-kernel-rev", action="store_true")
     ap.add_argument("--n", default=None, help="override the box size, e.g. 256,256,128 (profiling cases)")
     ap.add_argument("--bodies", type=int, default=None)
+    ap.add_argument("--serving-requests", type=int, default=40,
+                    help="requests of the serving trace (0: skip the serving measurement)")
     args = ap.parse_args()
     if args.n:
         args.n = tuple(int(v) for v in args.n.split(","))
