@@ -168,37 +168,51 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    spec = _workload(args.workload, "fp64")
+    spec = _workload(args.workload, "fp64", args.n, args.bodies)
     import oracle
     from paper_1407_4524_gb300 import workloads as W
-    # size the sample so that W + K oracle steps take a few minutes at most
-    probe = W.sphere_swarm_3d(precision="fp64", n=(64, 64, 64), n_bodies=1, seed=1407)
-    o = oracle.Oracle(probe)
-    t0 = time.perf_counter()
-    o.step(2)
-    rate = 2 * 64 ** 3 / (time.perf_counter() - t0)  # cell updates per second
     budget = 150.0
-    cells_per_step = max(32 ** 3, min(512 * 256 * 256, rate * budget / max(1, args.steps + args.warmup)))
-    nz = max(32, int(round((cells_per_step / 4) ** (1 / 3) / 8)) * 8)
-    n = (4 * nz, nz, nz) if 4 * nz <= 512 else (512, min(256, nz), min(256, nz))
-    nbod = max(1, int(round(64 * np.prod(n) / (512 * 256 * 256))))
-    sample = W.sphere_swarm_3d(precision="fp64", n=n, n_bodies=nbod, seed=1407)
+    if args.workload == "sphere_swarm_3d":
+        # size a periodic sub-box so that W + K oracle steps take a few minutes at most
+        probe = W.sphere_swarm_3d(precision="fp64", n=(64, 64, 64), n_bodies=1, seed=1407)
+        o = oracle.Oracle(probe)
+        t0 = time.perf_counter()
+        o.step(2)
+        rate = 2 * 64 ** 3 / (time.perf_counter() - t0)  # cell updates per second
+        cells_per_step = max(32 ** 3, min(512 * 256 * 256, rate * budget / max(1, args.steps + args.warmup)))
+        nz = max(32, int(round((cells_per_step / 4) ** (1 / 3) / 8)) * 8)
+        n = (4 * nz, nz, nz) if 4 * nz <= 512 else (512, min(256, nz), min(256, nz))
+        nbod = max(1, int(round(64 * np.prod(n) / (512 * 256 * 256))))
+        sample = W.sphere_swarm_3d(precision="fp64", n=n, n_bodies=nbod, seed=1407)
+        what = f"periodic {'x'.join(map(str, n))} sub-box of the workload, {nbod} spheres"
+        steps, warmup = args.steps, args.warmup
+    else:
+        # the whole domain; the step count is cut so that the run stays within the budget
+        sample = spec
+        n = tuple(spec["n"])
+        o = oracle.Oracle(sample)
+        t0 = time.perf_counter()
+        o.step(1)
+        per_step = time.perf_counter() - t0
+        total = max(1, min(args.steps + args.warmup, int(budget / max(per_step, 1e-9))))
+        warmup = min(args.warmup, max(0, total - 1))
+        steps = max(1, total - warmup)
+        what = f"the whole {'x'.join(map(str, n))} domain, {steps} timed steps"
     o = oracle.Oracle(sample)
     cells = int(np.prod(o.shape))
-    o.step(args.warmup)
+    o.step(warmup)
     t0 = time.perf_counter()
-    o.step(args.steps)
+    o.step(steps)
     el = time.perf_counter() - t0
-    mlups = cells * args.steps / el / 1e6
+    mlups = cells * steps / el / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
     line = {
         "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / max(1, args.steps), 3),
+        "steps": steps, "warmup": warmup, "ms_per_step": round(1e3 * el / max(1, steps), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": _describe(spec), "sample": "x".join(map(str, n)) + f", {nbod} spheres",
-                   "parallelism": "cpu"},
+        "config": {"workload": _describe(spec), "sample": what, "parallelism": "cpu"},
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": f"periodic {'x'.join(map(str, n))} sub-box of the workload, {nbod} spheres"},
+                         "sample": what},
         "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

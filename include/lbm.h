@@ -149,6 +149,8 @@ typedef struct lbm_stats {
     int64_t device_bytes;    /* device memory held by the domain */
     int64_t h2d_bytes;       /* bytes copied host -> device by API calls */
     int64_t d2h_bytes;       /* bytes copied device -> host by API calls */
+    int64_t timeouts;        /* non-zero: a kernel gave up a bounded wait (the
+                                step's results are invalid; LBM_ERR_TIMEOUT) */
 } lbm_stats;
 
 typedef struct lbm_domain lbm_domain;

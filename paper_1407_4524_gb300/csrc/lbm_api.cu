@@ -588,6 +588,17 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     for (int k = 0; k < 6; ++k) p.edge[k] = d.edge[k];
     p.nonper = !(p.per[0] && p.per[1] && p.per[2]);
     p.exact = d.precision == LBM_FP64;
+    {
+        // LBM_STAGED=1 selects the stream-collide kernel that stages the
+        // source rows in shared memory by bulk copies (same results bit for
+        // bit; slower than the direct kernels with row-sized copies, so not
+        // the default)
+        const char *es = std::getenv("LBM_STAGED");
+        p.staged = (es && es[0] == '1') ? 1 : 0;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
+        p.nsm = sms;
+    }
     p.eq = d.equilibrium;
     p.inlet_parabolic = d.inlet_profile == LBM_INLET_PARABOLIC;
     p.has_force = d.has_force ? 1 : 0;
@@ -841,6 +852,11 @@ int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
     if (first < D->t - D->series_cap) return fail(LBM_ERR_ARG, "rows older than the series ring");
     if (D->nb == 0 || count == 0) return LBM_OK;
     CK(cudaStreamSynchronize(D->s));
+    {
+        unsigned long long flag = 0;
+        CK(cudaMemcpy(&flag, D->counters + 6, sizeof(flag), cudaMemcpyDeviceToHost));
+        if (flag) return fail(LBM_ERR_TIMEOUT, "a stream-collide block gave up waiting for its staged rows");
+    }
     const size_t row = (size_t)D->nb * SERIES_ROW;
     int64_t done = 0;
     while (done < count) {
@@ -907,6 +923,7 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     out->covered = (int64_t)c[1];
     out->uncovered = (int64_t)c[2];
     out->device_bytes = (int64_t)D->bytes;
+    out->timeouts = (int64_t)c[6];
     out->h2d_bytes = D->h2d;
     out->d2h_bytes = D->d2h;
     if (D->nb && D->prec != LBM_FP64 && D->t > 0) {
@@ -998,7 +1015,7 @@ struct lbm_batch {
     std::vector<Slot> slots;
     SolveDev *dsolves = nullptr;
     struct Group {
-        int Q = 0, prec = 0;
+        int Q = 0, prec = 0, kind = 0;
         int2 *work = nullptr;
         int nwork = 0;
         int *slots = nullptr;
@@ -1029,7 +1046,9 @@ struct lbm_batch {
 
 namespace {
 
-int group_of(int Q, int prec) { return (Q == 19 ? 2 : 0) + (prec == LBM_FP16 ? 1 : 0); }
+// bulk kind of a solve (lbm_internal.h) and its group: 2 kinds per lattice
+int bulk_kind(const lbm_domain *D) { return D->prec == LBM_FP16 ? BK_FP16 : BK_FP32; }
+int group_of(const lbm_domain *D) { return (D->Q == 19 ? 2 : 0) + bulk_kind(D); }
 
 // Device bytes lbm_create_domain + lbm_set_bodies request for this problem
 // (the same sizes, in the same order, without allocating).
@@ -1130,9 +1149,10 @@ int batch_rebuild(lbm_batch *B) {
     for (int sl = 0; sl < (int)B->slots.size(); ++sl) {
         const auto &S = B->slots[sl];
         if (!S.D || S.D->t >= S.t_end) continue;
-        const int gi = group_of(S.D->Q, S.D->prec);
+        const int gi = group_of(S.D);
         const long long N = S.D->p.N;
-        for (long long c = 0; c < N; c += BULK_THREADS) work[gi].push_back(make_int2(sl, (int)c));
+        const int step = BULK_THREADS;
+        for (long long c = 0; c < N; c += step) work[gi].push_back(make_int2(sl, (int)c));
         gslots[gi].push_back(sl);
         pre[gi].push_back(pre[gi].back() + S.nodes);
         all.push_back(sl);
@@ -1141,7 +1161,8 @@ int batch_rebuild(lbm_batch *B) {
     for (int k = 0; k < 4; ++k) {
         auto &G = B->g[k];
         G.Q = k >= 2 ? 19 : 9;
-        G.prec = (k & 1) ? LBM_FP16 : LBM_FP32;
+        G.kind = k % 2;
+        G.prec = G.kind == BK_FP32 ? LBM_FP32 : LBM_FP16;
         if ((rc = batch_upload(B, &G.work, work[k]))) return rc;
         if ((rc = batch_upload(B, &G.slots, gslots[k]))) return rc;
         if (!gslots[k].empty() && (rc = batch_upload(B, &G.node_pre, pre[k]))) return rc;
@@ -1167,7 +1188,7 @@ int batch_rebuild(lbm_batch *B) {
             if (G.nslots == 0) continue;
             if (G.grid > 0)
                 e = launch_bbnd(G.Q, G.prec, B->dsolves, G.slots, G.node_pre, G.nslots, G.grid, B->s2);
-            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.prec, B->dsolves, G.work, G.nwork, B->s);
+            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.kind, B->dsolves, G.work, G.nwork, B->s);
         }
         if (e != cudaSuccess) break;
         if ((e = cudaEventRecord(B->ev_join, B->s2)) != cudaSuccess) break;

@@ -104,9 +104,10 @@ __global__ void __launch_bounds__(128) k_bfinish(SolveDev *solves, const int *sl
     }
 }
 
-template <class L, class P> cudaError_t bbulk_t(const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s) {
+template <class L> cudaError_t bbulk_t(int kind, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s) {
     if (nwork == 0) return cudaSuccess;
-    k_bbulk<L, P><<<nwork, BULK_THREADS, 0, s>>>(solves, work);
+    if (kind == BK_FP16) k_bbulk<L, PF16><<<nwork, BULK_THREADS, 0, s>>>(solves, work);
+    else k_bbulk<L, PF32><<<nwork, BULK_THREADS, 0, s>>>(solves, work);
     return cudaGetLastError();
 }
 
@@ -120,9 +121,8 @@ cudaError_t bbnd_t(const SolveDev *solves, const int *slots, const long long *no
 
 } // namespace
 
-cudaError_t launch_bbulk(int Q, int prec, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s) {
-    if (prec == 1) return Q == 9 ? bbulk_t<Lat<9>, PF32>(solves, work, nwork, s) : bbulk_t<Lat<19>, PF32>(solves, work, nwork, s);
-    return Q == 9 ? bbulk_t<Lat<9>, PF16>(solves, work, nwork, s) : bbulk_t<Lat<19>, PF16>(solves, work, nwork, s);
+cudaError_t launch_bbulk(int Q, int kind, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s) {
+    return Q == 9 ? bbulk_t<Lat<9>>(kind, solves, work, nwork, s) : bbulk_t<Lat<19>>(kind, solves, work, nwork, s);
 }
 
 cudaError_t launch_bbnd(int Q, int prec, const SolveDev *solves, const int *slots, const long long *node_pre,

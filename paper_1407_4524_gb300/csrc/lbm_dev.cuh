@@ -136,6 +136,8 @@ struct Params {
     int nb;      // bodies
     int nonper;  // 1 if any axis is non-periodic
     int exact;   // FP64 mode: link geometry in FP64 (else FP32)
+    int staged;  // reduced precision: stream-collide from rows staged in shared memory
+    int nsm;     // multiprocessors of the device
     long long series_cap;
     long long me_stride; // ME contribution arrays are [ME_PER_LINK][me_stride]
     double tau, omega, rho0, u_in;

@@ -109,9 +109,12 @@ cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_
 // momentum exchange, collision) -- runs beside k_bulk
 cudaError_t launch_bnd(int Q, int prec, const Params &p, const BndArgs &a, const StepBufs &sb, int grid,
                        cudaStream_t s);
-// batched serving kernels: one tick = bulk (per lattice), boundary nodes (per
-// lattice), finish (every solve)
-cudaError_t launch_bbulk(int Q, int prec, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s);
+// batched serving kernels: one tick = bulk (per group), boundary nodes (per
+// group), finish (every solve).  A group is a lattice and a storage type
+// (BK_FP32 / BK_FP16); a bulk work item covers BULK_THREADS consecutive cells
+// of one solve.
+constexpr int BK_FP32 = 0, BK_FP16 = 1;
+cudaError_t launch_bbulk(int Q, int kind, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s);
 cudaError_t launch_bbnd(int Q, int prec, const SolveDev *solves, const int *slots, const long long *node_pre,
                         int nslots, int grid, cudaStream_t s);
 cudaError_t launch_bfinish(SolveDev *solves, const int *slots, int nslots, cudaStream_t s);

@@ -2,7 +2,10 @@
 // precision translation units (lbm_fp64.cu, lbm_fp32.cu).
 #pragma once
 
+#include <algorithm>
+
 #include "lbm_internal.h"
+#include "lbm_stage.cuh"
 
 namespace lbm {
 
@@ -30,8 +33,24 @@ template <class L, class P> cudaError_t links_t(const Params &p, const StepBufs 
     return cudaGetLastError();
 }
 
+// reduced precision with 16-byte aligned rows: rows staged by bulk copies
+template <class L, class P> void staged_launch(const Params &p, const StepBufs &sb, cudaStream_t s) {
+    using S = typename P::S;
+    const int seg = std::min(STAGE_SEG, p.nx);
+    const long long nseg = (long long)((p.nx + seg - 1) / seg) * p.ny * p.nz;
+    const int grid = (int)std::min<long long>(nseg, (long long)std::max(1, p.nsm) * STAGE_BLOCKS_PER_SM);
+    k_bulk_staged<L, P><<<grid, seg, stage_smem<L, S>(seg), s>>>(p, (const S *)sb.src, (S *)sb.dst, sb.flags,
+                                                                  sb.counters);
+}
+
 // fully periodic domains: the kernel without the face rule (fewer registers)
 template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
+    if constexpr (!P::exact) {
+        if (p.staged && staged_ok<L, P>(p)) {
+            staged_launch<L, P>(p, sb, s);
+            return cudaGetLastError();
+        }
+    }
     if (p.nonper)
         k_bulk<L, P, true><<<bulk_grid(p), bulk_block(p), 0, s>>>(
             p, (const typename P::S *)sb.src, (typename P::S *)sb.dst, sb.flags, (const typename P::C *)sb.mac_t,

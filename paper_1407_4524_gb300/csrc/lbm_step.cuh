@@ -27,6 +27,8 @@
 // formulas with FP32 arithmetic; the momentum-exchange sums stay FP64.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_dev.cuh"
 
 namespace lbm {
@@ -371,15 +373,24 @@ template <class L> __device__ __forceinline__ unsigned face_dirs(unsigned fl, in
            ((fl >> (base + 4)) & 1u ? dir_mask<L>(2, 1) : 0u) | ((fl >> (base + 5)) & 1u ? dir_mask<L>(2, -1) : 0u);
 }
 
-// f_i(x, t+1) for all i at node (x,y,z).  Fully periodic domains, and warps
-// of a non-periodic domain with no node on a face, take the plain path;
-// other warps take the face path, where every direction applies the face
-// rule (the same values as pull_edge) and all Q loads are issued before any
-// is used.  Both paths give the same values at interior nodes.
-template <class L, class P, bool FACES = true>
-__device__ __forceinline__ void pull_all(const Params &p, const typename P::S *__restrict__ src,
-                                         const typename P::C *__restrict__ mac_t, int x, int y, int z,
-                                         long long cell, typename P::C f[]) {
+// load of a stored population, either converted to the compute type or raw
+template <class V, class S> __device__ __forceinline__ V ld_as(const S *ptr) {
+    if constexpr (std::is_same<V, S>::value) return __ldg(ptr);
+    else return ldS(ptr);
+}
+
+// The Q source loads of node (x,y,z) into v[] (compute type, or raw storage
+// type for the two-node FP16 kernels).  Fully periodic domains, and warps of
+// a non-periodic domain with no node on a face, take the plain path; other
+// warps take the face path, where every direction applies the face rule (the
+// same sources as pull_edge) and all Q loads are issued before any is used.
+// Both paths load the same sources at interior nodes.  Returns the wall /
+// inlet links of the node (their momentum terms are added by face_terms)
+// and, in inlet_only, the inlet links not overridden by a wall.
+template <class L, class P, bool FACES, class V>
+__device__ __forceinline__ unsigned pull_core(const Params &p, const typename P::S *__restrict__ src, int x, int y,
+                                              int z, long long cell, V v[], unsigned &inlet_only) {
+    inlet_only = 0u;
     bool plain = true;
     if constexpr (FACES) plain = !p.nonper || !__any_sync(__activemask(), on_edge(p, x, y, z));
     if (plain) {
@@ -391,17 +402,18 @@ __device__ __forceinline__ void pull_all(const Params &p, const typename P::S *_
             const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
             const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
             const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
-            f[i] = ldS(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+            v[i] = ld_as<V>(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
         }
-        return;
+        return 0u;
     }
+    unsigned bounce = 0u;
     if constexpr (FACES) {
         int xm, xp, ym, yp, zm, zp;
         unsigned fl = 0u;
         face_axis(x, p.nx, p.per[0], p.edge[0], p.edge[1], 0, xm, xp, fl);
         face_axis(y, p.ny, p.per[1], p.edge[2], p.edge[3], 1, ym, yp, fl);
         face_axis(z, p.nz, p.per[2], p.edge[4], p.edge[5], 2, zm, zp, fl);
-        const unsigned bounce = face_dirs<L>(fl, 0);
+        bounce = face_dirs<L>(fl, 0);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
@@ -409,14 +421,26 @@ __device__ __forceinline__ void pull_all(const Params &p, const typename P::S *_
             const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
             const long long idx = ((bounce >> i) & 1u) ? (long long)L::opp(i) * p.N + cell
                                                        : (long long)i * p.N + cell_of(p, sx, sy, sz);
-            f[i] = ldS(src + idx);
+            v[i] = ld_as<V>(src + idx);
         }
-        if (bounce) {
-            const unsigned inlet_only = face_dirs<L>(fl, 16) & ~face_dirs<L>(fl, 8);
-            face_terms<L, P>(p, src, mac_t, y, cell, bounce, inlet_only, f);
-        }
+        if (bounce) inlet_only = face_dirs<L>(fl, 16) & ~face_dirs<L>(fl, 8);
+    }
+    return bounce;
+}
+
+// f_i(x, t+1) for all i at node (x,y,z): the pulls of pull_core plus the
+// momentum terms of the node's wall / inlet links
+template <class L, class P, bool FACES = true>
+__device__ __forceinline__ void pull_all(const Params &p, const typename P::S *__restrict__ src,
+                                         const typename P::C *__restrict__ mac_t, int x, int y, int z,
+                                         long long cell, typename P::C f[]) {
+    unsigned inlet_only;
+    const unsigned bounce = pull_core<L, P, FACES>(p, src, x, y, z, cell, f, inlet_only);
+    if constexpr (FACES) {
+        if (bounce) face_terms<L, P>(p, src, mac_t, y, cell, bounce, inlet_only, f);
     }
 }
+
 
 // ================================================================== kernels ==
 

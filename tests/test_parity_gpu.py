@@ -42,12 +42,23 @@ CASES_2D = {
     "channel_cylinder": dict(
         lattice="D2Q9", n=(61, 29), tau=0.8, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
         inlet={"profile": "parabolic", "u": 0.05}, bodies=[dict(shape="cylinder", R=6.3, X0=(15.4, 14.2))]),
+    "channel_cylinder_even": dict(  # even nx: FP16 node pairs at the inlet, outlet and walls
+        lattice="D2Q9", n=(62, 30), tau=0.7, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+        inlet={"profile": "parabolic", "u": 0.05}, u0=(0.02, 0.0),
+        bodies=[dict(shape="cylinder", R=5.7, X0=(17.2, 14.6))]),
+    "channel_cylinder_64": dict(  # 16-byte rows: stream-collide from staged rows (FP32 and FP16)
+        lattice="D2Q9", n=(64, 30), tau=0.7, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+        inlet={"profile": "parabolic", "u": 0.05}, u0=(0.02, 0.0),
+        bodies=[dict(shape="cylinder", R=5.7, X0=(17.2, 14.6))]),
+    "long_rows_periodic": dict(  # rows of several staging segments, the last one partial
+        lattice="D2Q9", n=(328, 24), tau=0.65, u0=(0.03, -0.01),
+        bodies=[dict(shape="cylinder", R=4.5, X0=(300.3, 11.2), U=(0.03, 0.0))]),
     "moving_cylinders_periodic": dict(
         lattice="D2Q9", n=(97, 66), tau=0.6,
         bodies=[dict(shape="cylinder", R=8.2, X0=(6.3, 20.4), U=(0.06, -0.03)),  # crosses the seam
                 dict(shape="cylinder", R=7.0, X0=(60.0, 45.0), W=0.004)]),
     "standard_eq_walls": dict(
-        lattice="D2Q9", n=(50, 40), tau=0.7, eq="standard", u0=(0.03, 0.0),
+        lattice="D2Q9", n=(48, 40), tau=0.7, eq="standard", u0=(0.03, 0.0),
         edges={"x": "periodic", "y": ("wall", "wall")},
         bodies=[dict(shape="cylinder", R=5.1, X0=(20.5, 19.3), U=(0.04, 0.0), W=-0.003)]),
     "refill_ubar": dict(
@@ -78,6 +89,9 @@ CASES_3D = {
                 dict(shape="sphere", R=4.7, X0=(30.0, 24.5, 2.2), U=(0.05, -0.02, 0.04), W=(0.002, 0.0, -0.003)),
                 dict(shape="sphere", R=3.9, X0=(28.0, 7.0, 20.0), U=(-0.03, 0.04, 0.01))]),
     "single_cell_box": dict(lattice="D3Q19", n=(1, 1, 1), tau=0.8, u0=(0.01, 0.02, -0.03)),
+    "walled_channel_sphere": dict(  # 16-byte rows, walls on y, inlet / outlet on x
+        lattice="D3Q19", n=(48, 20, 18), tau=0.62, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+        inlet={"u": 0.03}, u0=(0.03, 0.0, 0.0), bodies=[dict(shape="sphere", R=4.6, X0=(14.2, 9.7, 8.9))]),
     "walled_box_cylinder3d": dict(
         lattice="D3Q19", n=(30, 28, 9), tau=0.7, u0=(0.02, 0.01, 0.0),
         edges={"x": ("wall", "wall"), "y": ("wall", "wall"), "z": "periodic"},
@@ -111,8 +125,11 @@ def test_fp64_is_bit_identical(oracle_mod):
     assert np.array_equal(dom.series(), ref.series())
 
 
+# every case in both reduced-precision modes: odd and even nx (FP16 storage
+# moves node pairs when nx is even), all edge kinds (walls on x and y, inlet,
+# outlet), both equilibria, forcing, moving and static bodies
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("name", ["channel_cylinder", "moving_cylinders_periodic"])
+@pytest.mark.parametrize("name", sorted(CASES_2D))
 def test_reduced_precision_2d(oracle_mod, name, prec):
     spec = dict(CASES_2D[name], precision=prec)
     dom, ref = _run_both(oracle_mod, spec, 120)
@@ -123,7 +140,7 @@ def test_reduced_precision_2d(oracle_mod, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("name", ["channel_sphere", "moving_spheres_periodic"])
+@pytest.mark.parametrize("name", sorted(CASES_3D))
 def test_reduced_precision_3d(oracle_mod, name, prec):
     spec = dict(CASES_3D[name], precision=prec)
     dom, ref = _run_both(oracle_mod, spec, 40)
@@ -165,3 +182,36 @@ def test_invalid_bodies_rejected():
         dom.set_bodies([dict(shape="cylinder", R=4.0, X0=(20.0, 15.0))])
     with pytest.raises(lbm.LbmError, match="LBM_ERR_ARG"):
         dom.force_torque("static", first=0, count=5)
+
+
+# With LBM_STAGED=1, reduced-precision domains whose rows are 16-byte aligned
+# stream-collide from rows staged in shared memory by bulk copies (the default
+# kernels load straight from global memory).  Same arithmetic per node: the
+# results must agree bit for bit.
+def _staged_cases():
+    out = []
+    for dim, cases in (("2d", CASES_2D), ("3d", CASES_3D)):
+        for name in sorted(cases):
+            nx = cases[name]["n"][0]
+            for prec, s in (("fp32", 4), ("fp16", 2)):
+                if nx >= 32 and (nx * s) % 16 == 0:
+                    out.append((dim, name, prec))
+    return out
+
+
+@pytest.mark.parametrize("dim,name,prec", _staged_cases())
+def test_staged_rows_bitwise(monkeypatch, dim, name, prec):
+    from paper_1407_4524_gb300 import lbm
+    spec = dict((CASES_2D if dim == "2d" else CASES_3D)[name], precision=prec)
+    out = {}
+    for staged in ("1", "0"):
+        monkeypatch.setenv("LBM_STAGED", staged)
+        dom = lbm.Domain(spec, device=0)
+        dom.step(60)
+        out[staged] = (dom.populations(), dom.series() if dom.bodies else None, dom.solid(), dom.stats())
+        dom.close()
+    assert out["1"][3]["timeouts"] == 0
+    fl = out["1"][2] < 0
+    assert np.array_equal(out["1"][0][:, fl], out["0"][0][:, fl])
+    if out["1"][1] is not None:
+        assert np.array_equal(out["1"][1], out["0"][1])
