@@ -127,14 +127,22 @@ def _dist():
     return world, rank, local
 
 
-def _barrier_max(x: float, world: int):
+def _barrier_max(x: float, world: int, device: str = "cuda"):
+    """max of x over the ranks (NCCL on the GPU, gloo on the CPU)"""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_mlups(ms_local: float, cells: int, steps: int, world: int, device: str = "cuda"):
+    """Replicas: every rank advances its own copy of the workload; the job
+    time is the slowest rank's, the work is all ranks' cell updates."""
+    ms = _barrier_max(ms_local, world, device)
+    return ms, world * cells * steps / (ms * 1e-3) / 1e6
 
 
 def cpu_baseline(spec, budget_s: float = 15.0):
@@ -262,8 +270,7 @@ def run_ours(args):
     n_bulk, bulk_ms = dom.kernel_time()
     dom.set_kernel_timing(False)
     clocks = sampler.stop() if sampler else None
-    ms = _barrier_max(ms, world)
-    mlups = world * cells * args.steps / (ms * 1e-3) / 1e6
+    ms, mlups = replica_mlups(ms, cells, args.steps, world)
 
     # end-to-end through the C ABI with host buffers: each step uploads the
     # bodies' kinematics (lbm_update_bodies) and reads the step's force/torque
