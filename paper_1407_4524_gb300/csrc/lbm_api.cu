@@ -117,8 +117,9 @@ struct lbm_domain {
     unsigned long long *bn_cnt = nullptr; // [0] static, [1], [2] moving lists of even / odd steps
     long long bn_static_cap = 0, bn_mov_cap = 0;
     bool lists_dirty = true;
-    int bnd_grid = 0;
+    int bnd_grid = 0, bnd_grid_full = 0;
     int side_blocks = 0; // block cap of the side-stream kernels
+    bool side_serial = false; // run the surface kernels before k_bulk on one stream, uncapped
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -477,14 +478,18 @@ int do_step_overlapped(lbm_domain *D) {
         int rc = build_bnd_lists(D);
         if (rc) return rc;
     }
-    CK(cudaEventRecord(D->ev_prep, D->s));
-    CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
+    // side stream, or the main stream itself in the serial arrangement
+    cudaStream_t ss = D->side_serial ? D->s : D->s2;
+    if (!D->side_serial) {
+        CK(cudaEventRecord(D->ev_prep, D->s));
+        CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
+    }
     StepBufs sb = step_bufs(D);
     GeomArgs g = geom_args(D, true);
-    g.grid_cap = D->side_blocks;
+    g.grid_cap = D->side_serial ? 0 : D->side_blocks;
     if (D->n_moving) {
-        CK(launch_fgeom1(Q, D->p, g, D->s2));
-        CK(launch_fgeom2(Q, D->p, g, D->s2));
+        CK(launch_fgeom1(Q, D->p, g, ss));
+        CK(launch_fgeom2(Q, D->p, g, ss));
     }
     BndArgs ba{};
     ba.static_cells = D->bn_static;
@@ -497,9 +502,9 @@ int do_step_overlapped(lbm_domain *D) {
     ba.owner_t1 = D->owner[nxt];
     ba.bodies = D->dbodies;
     ba.poses = D->poses;
-    CK(launch_bnd(Q, prec, D->p, ba, sb, D->bnd_grid, D->s2));
-    CK(launch_finish(Q, prec, D->p, sb, D->s2));
-    CK(cudaEventRecord(D->ev_side, D->s2));
+    CK(launch_bnd(Q, prec, D->p, ba, sb, D->side_serial ? D->bnd_grid_full : D->bnd_grid, ss));
+    CK(launch_finish(Q, prec, D->p, sb, ss));
+    if (!D->side_serial) CK(cudaEventRecord(D->ev_side, D->s2));
     if (D->timing) {
         if (D->ev_used + 2 > D->ev.size()) {
             for (int k = 0; k < 64; ++k) {
@@ -515,7 +520,7 @@ int do_step_overlapped(lbm_domain *D) {
         CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
         D->ev_used += 2;
     }
-    CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
+    if (!D->side_serial) CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
     D->t += 1;
     return LBM_OK;
 }
@@ -640,6 +645,9 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
         int per = 3;
         if (const char *ev = std::getenv("LBM_SIDE_BLOCKS_PER_SM")) per = std::max(1, std::atoi(ev));
         D->side_blocks = std::max(1, sms) * per;
+        // LBM_SIDE_SERIAL=1: surface kernels before k_bulk on one stream
+        const char *es = std::getenv("LBM_SIDE_SERIAL");
+        D->side_serial = es && es[0] == '1';
     }
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
@@ -755,6 +763,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->bn_mov[1], (size_t)D->bn_mov_cap, &T))) return rc;
     if ((rc = alloc_t(D, &D->bn_cnt, 3, &T))) return rc;
     D->bnd_grid = (int)std::max<long long>(1, std::min<long long>(D->side_blocks, (bns + 7) / 8));
+    D->bnd_grid_full = (int)std::max<long long>(1, std::min<long long>(16ll * D->p.nsm, (bns + 7) / 8));
     D->lists_dirty = true;
     long long maxcnt = 0;
     for (int b = 0; b < n; ++b) maxcnt = std::max(maxcnt, D->hbd[b].link_cap);
@@ -1015,15 +1024,16 @@ struct lbm_batch {
     std::vector<Slot> slots;
     SolveDev *dsolves = nullptr;
     struct Group {
-        int Q = 0, prec = 0, kind = 0;
-        int2 *work = nullptr;
+        int Q = 0, prec = 0, kind = 0, fm = 0;
+        int4 *work = nullptr;
         int nwork = 0;
         int *slots = nullptr;
         long long *node_pre = nullptr;
         int nslots = 0;
         int grid = 0;
     };
-    Group g[4];
+    static constexpr int NGROUPS = 12; // lattice x storage x face mode
+    Group g[NGROUPS];
     int *dall = nullptr;
     int nall = 0;
     std::vector<void *> table_allocs;
@@ -1046,9 +1056,9 @@ struct lbm_batch {
 
 namespace {
 
-// bulk kind of a solve (lbm_internal.h) and its group: 2 kinds per lattice
+// bulk kind of a solve (lbm_internal.h) and its group: lattice x kind x face mode
 int bulk_kind(const lbm_domain *D) { return D->prec == LBM_FP16 ? BK_FP16 : BK_FP32; }
-int group_of(const lbm_domain *D) { return (D->Q == 19 ? 2 : 0) + bulk_kind(D); }
+int group_of(const lbm_domain *D) { return ((D->Q == 19 ? 2 : 0) + bulk_kind(D)) * 3 + face_mode(D->p); }
 
 // Device bytes lbm_create_domain + lbm_set_bodies request for this problem
 // (the same sizes, in the same order, without allocating).
@@ -1142,26 +1152,28 @@ int batch_rebuild(lbm_batch *B) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
     }
-    std::vector<int2> work[4];
-    std::vector<int> gslots[4], all;
-    std::vector<long long> pre[4];
-    for (int k = 0; k < 4; ++k) pre[k].push_back(0);
+    constexpr int NG = lbm_batch::NGROUPS;
+    std::vector<int4> work[NG];
+    std::vector<int> gslots[NG], all;
+    std::vector<long long> pre[NG];
+    for (int k = 0; k < NG; ++k) pre[k].push_back(0);
     for (int sl = 0; sl < (int)B->slots.size(); ++sl) {
         const auto &S = B->slots[sl];
         if (!S.D || S.D->t >= S.t_end) continue;
         const int gi = group_of(S.D);
-        const long long N = S.D->p.N;
-        const int step = BULK_THREADS;
-        for (long long c = 0; c < N; c += step) work[gi].push_back(make_int2(sl, (int)c));
+        const int rows = S.D->p.ny * S.D->p.nz;
+        for (int r = 0; r < rows; ++r)
+            for (int x0 = 0; x0 < S.D->p.nx; x0 += BBULK_THREADS) work[gi].push_back(make_int4(sl, r, x0, 0));
         gslots[gi].push_back(sl);
         pre[gi].push_back(pre[gi].back() + S.nodes);
         all.push_back(sl);
     }
     int rc;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NG; ++k) {
         auto &G = B->g[k];
-        G.Q = k >= 2 ? 19 : 9;
-        G.kind = k % 2;
+        G.Q = k / 3 >= 2 ? 19 : 9;
+        G.kind = (k / 3) % 2;
+        G.fm = k % 3;
         G.prec = G.kind == BK_FP32 ? LBM_FP32 : LBM_FP16;
         if ((rc = batch_upload(B, &G.work, work[k]))) return rc;
         if ((rc = batch_upload(B, &G.slots, gslots[k]))) return rc;
@@ -1183,12 +1195,12 @@ int batch_rebuild(lbm_batch *B) {
     for (int t = 0; t < B->tpl && e == cudaSuccess; ++t) {
         if ((e = cudaEventRecord(B->ev_fork, B->s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(B->s2, B->ev_fork, 0)) != cudaSuccess) break;
-        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+        for (int k = 0; k < NG && e == cudaSuccess; ++k) {
             const auto &G = B->g[k];
             if (G.nslots == 0) continue;
             if (G.grid > 0)
                 e = launch_bbnd(G.Q, G.prec, B->dsolves, G.slots, G.node_pre, G.nslots, G.grid, B->s2);
-            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.kind, B->dsolves, G.work, G.nwork, B->s);
+            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.kind, G.fm, B->dsolves, G.work, G.nwork, B->s);
         }
         if (e != cudaSuccess) break;
         if ((e = cudaEventRecord(B->ev_join, B->s2)) != cudaSuccess) break;

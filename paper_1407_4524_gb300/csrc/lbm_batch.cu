@@ -16,14 +16,16 @@ namespace lbm {
 
 namespace {
 
-// work[k] = (slot, first cell): block k does BULK_THREADS consecutive cells
-// of one solve (flat index, so small grids waste no threads on short rows)
-template <class L, class P>
-__global__ void __launch_bounds__(BULK_THREADS, BULK_MIN_BLOCKS) k_bbulk(const SolveDev *__restrict__ solves,
-                                                                         const int2 *__restrict__ work) {
+// work[k] = (slot, row, x0): block k does the BBULK_THREADS nodes x0 .. of one
+// row (y, z) of one solve, row = y + ny * z.  Row-aligned blocks keep a warp
+// on one row (so only the blocks at the row ends take the face path) and
+// need no 64-bit division per node.
+template <class L, class P, int FM>
+__global__ void __launch_bounds__(BBULK_THREADS) k_bbulk(const SolveDev *__restrict__ solves,
+                                                         const int4 *__restrict__ work) {
     // the solve's record in shared memory: its parameters are read many times
     __shared__ SolveDev sv;
-    const int2 w = work[blockIdx.x];
+    const int4 w = work[blockIdx.x];
     {
         static_assert(sizeof(SolveDev) % 4 == 0, "SolveDev is copied as 32-bit words");
         const int *from = (const int *)(solves + w.x);
@@ -32,13 +34,12 @@ __global__ void __launch_bounds__(BULK_THREADS, BULK_MIN_BLOCKS) k_bbulk(const S
     }
     __syncthreads();
     if (!sv.active) return;
-    const long long cell = (long long)w.y + threadIdx.x;
-    if (cell >= sv.p.N) return;
-    int x, y, z;
-    coords_of(sv.p, cell, x, y, z);
+    const int x = w.z + threadIdx.x;
+    if (x >= sv.p.nx) return;
+    const int z = w.y / sv.p.ny, y = w.y - z * sv.p.ny;
     const int cur = (int)(sv.t & 1);
-    bulk_node<L, P>(sv.p, (const typename P::S *)sv.pop[cur], (typename P::S *)sv.pop[cur ^ 1], sv.flags,
-                    (const typename P::C *)nullptr, (typename P::C *)nullptr, x, y, z);
+    bulk_node<L, P, FM>(sv.p, (const typename P::S *)sv.pop[cur], (typename P::S *)sv.pop[cur ^ 1], sv.flags,
+                        (const typename P::C *)nullptr, (typename P::C *)nullptr, x, y, z);
 }
 
 // warp per boundary node over the node lists of the slots of one lattice
@@ -104,11 +105,18 @@ __global__ void __launch_bounds__(128) k_bfinish(SolveDev *solves, const int *sl
     }
 }
 
-template <class L> cudaError_t bbulk_t(int kind, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s) {
-    if (nwork == 0) return cudaSuccess;
-    if (kind == BK_FP16) k_bbulk<L, PF16><<<nwork, BULK_THREADS, 0, s>>>(solves, work);
-    else k_bbulk<L, PF32><<<nwork, BULK_THREADS, 0, s>>>(solves, work);
+template <class L, class P>
+cudaError_t bbulk_fm(int fm, const SolveDev *solves, const int4 *work, int nwork, cudaStream_t s) {
+    if (fm == FM_PERIODIC) k_bbulk<L, P, FM_PERIODIC><<<nwork, BBULK_THREADS, 0, s>>>(solves, work);
+    else if (fm == FM_XFACES) k_bbulk<L, P, FM_XFACES><<<nwork, BBULK_THREADS, 0, s>>>(solves, work);
+    else k_bbulk<L, P, FM_GENERAL><<<nwork, BBULK_THREADS, 0, s>>>(solves, work);
     return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t bbulk_t(int kind, int fm, const SolveDev *solves, const int4 *work, int nwork, cudaStream_t s) {
+    if (nwork == 0) return cudaSuccess;
+    return kind == BK_FP16 ? bbulk_fm<L, PF16>(fm, solves, work, nwork, s) : bbulk_fm<L, PF32>(fm, solves, work, nwork, s);
 }
 
 template <class L, class P>
@@ -121,8 +129,9 @@ cudaError_t bbnd_t(const SolveDev *solves, const int *slots, const long long *no
 
 } // namespace
 
-cudaError_t launch_bbulk(int Q, int kind, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s) {
-    return Q == 9 ? bbulk_t<Lat<9>>(kind, solves, work, nwork, s) : bbulk_t<Lat<19>>(kind, solves, work, nwork, s);
+cudaError_t launch_bbulk(int Q, int kind, int fm, const SolveDev *solves, const int4 *work, int nwork,
+                         cudaStream_t s) {
+    return Q == 9 ? bbulk_t<Lat<9>>(kind, fm, solves, work, nwork, s) : bbulk_t<Lat<19>>(kind, fm, solves, work, nwork, s);
 }
 
 cudaError_t launch_bbnd(int Q, int prec, const SolveDev *solves, const int *slots, const long long *node_pre,

@@ -110,11 +110,14 @@ cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_
 cudaError_t launch_bnd(int Q, int prec, const Params &p, const BndArgs &a, const StepBufs &sb, int grid,
                        cudaStream_t s);
 // batched serving kernels: one tick = bulk (per group), boundary nodes (per
-// group), finish (every solve).  A group is a lattice and a storage type
-// (BK_FP32 / BK_FP16); a bulk work item covers BULK_THREADS consecutive cells
-// of one solve.
+// group), finish (every solve).  A group is a lattice, a storage type
+// (BK_FP32 / BK_FP16) and a face mode; a bulk work item (slot, row, x0, 0)
+// covers BBULK_THREADS nodes of one row of one solve.
 constexpr int BK_FP32 = 0, BK_FP16 = 1;
-cudaError_t launch_bbulk(int Q, int kind, const SolveDev *solves, const int2 *work, int nwork, cudaStream_t s);
+constexpr int BBULK_THREADS = 64;
+// fm: face mode of the group's solves (FM_PERIODIC / FM_XFACES / FM_GENERAL)
+cudaError_t launch_bbulk(int Q, int kind, int fm, const SolveDev *solves, const int4 *work, int nwork,
+                         cudaStream_t s);
 cudaError_t launch_bbnd(int Q, int prec, const SolveDev *solves, const int *slots, const long long *node_pre,
                         int nslots, int grid, cudaStream_t s);
 cudaError_t launch_bfinish(SolveDev *solves, const int *slots, int nslots, cudaStream_t s);

@@ -43,7 +43,7 @@ template <class L, class P> void staged_launch(const Params &p, const StepBufs &
                                                                   sb.counters);
 }
 
-// fully periodic domains: the kernel without the face rule (fewer registers)
+// one kernel per face mode: the fewer faces, the less code in the loop
 template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &sb, cudaStream_t s) {
     if constexpr (!P::exact) {
         if (p.staged && staged_ok<L, P>(p)) {
@@ -51,14 +51,17 @@ template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &
             return cudaGetLastError();
         }
     }
-    if (p.nonper)
-        k_bulk<L, P, true><<<bulk_grid(p), bulk_block(p), 0, s>>>(
-            p, (const typename P::S *)sb.src, (typename P::S *)sb.dst, sb.flags, (const typename P::C *)sb.mac_t,
-            (typename P::C *)sb.mac_t1);
+    const int fm = face_mode(p);
+    const typename P::S *src = (const typename P::S *)sb.src;
+    typename P::S *dst = (typename P::S *)sb.dst;
+    const typename P::C *mt = (const typename P::C *)sb.mac_t;
+    typename P::C *mt1 = (typename P::C *)sb.mac_t1;
+    if (fm == FM_PERIODIC)
+        k_bulk<L, P, FM_PERIODIC><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
+    else if (fm == FM_XFACES)
+        k_bulk<L, P, FM_XFACES><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
     else
-        k_bulk<L, P, false><<<bulk_grid(p), bulk_block(p), 0, s>>>(
-            p, (const typename P::S *)sb.src, (typename P::S *)sb.dst, sb.flags, (const typename P::C *)sb.mac_t,
-            (typename P::C *)sb.mac_t1);
+        k_bulk<L, P, FM_GENERAL><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
     return cudaGetLastError();
 }
 

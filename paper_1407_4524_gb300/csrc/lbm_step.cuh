@@ -380,34 +380,70 @@ template <class V, class S> __device__ __forceinline__ V ld_as(const S *ptr) {
 }
 
 // The Q source loads of node (x,y,z) into v[] (compute type, or raw storage
-// type for the two-node FP16 kernels).  Fully periodic domains, and warps of
-// a non-periodic domain with no node on a face, take the plain path; other
-// warps take the face path, where every direction applies the face rule (the
-// same sources as pull_edge) and all Q loads are issued before any is used.
-// Both paths load the same sources at interior nodes.  Returns the wall /
-// inlet links of the node (their momentum terms are added by face_terms)
-// and, in inlet_only, the inlet links not overridden by a wall.
-template <class L, class P, bool FACES, class V>
+// type).  Fully periodic domains, and warps of a non-periodic domain with no
+// node on a y or z face, take the plain path, which applies the x-face rule
+// per direction (wall / inlet links bounce, an outlet repeats the last
+// column) with a few selects; warps with a node on a y or z face take the
+// face path, where every direction applies the full face rule.  Both give
+// the sources of pull_edge, and all Q loads are issued before any is used.
+// Returns the wall / inlet links of the node (their momentum terms are added
+// by face_terms) and, in inlet_only, the inlet links not overridden by a
+// wall.
+// Face modes of the stream-collide kernels: FM_PERIODIC (every axis
+// periodic), FM_XFACES (only x non-periodic: channels with periodic cross
+// sections), FM_GENERAL (any edges).
+constexpr int FM_PERIODIC = 0, FM_XFACES = 1, FM_GENERAL = 2;
+
+inline int face_mode(const Params &p) {
+    if (!p.nonper) return FM_PERIODIC;
+    return (p.per[1] && p.per[2]) ? FM_XFACES : FM_GENERAL;
+}
+
+template <class L, class P, int FM, class V>
 __device__ __forceinline__ unsigned pull_core(const Params &p, const typename P::S *__restrict__ src, int x, int y,
                                               int z, long long cell, V v[], unsigned &inlet_only) {
     inlet_only = 0u;
     bool plain = true;
-    if constexpr (FACES) plain = !p.nonper || !__any_sync(__activemask(), on_edge(p, x, y, z));
+    if constexpr (FM == FM_GENERAL) {
+        const bool yzface = (!p.per[1] && (y == 0 || y == p.ny - 1)) || (!p.per[2] && (z == 0 || z == p.nz - 1));
+        plain = !p.nonper || !__any_sync(__activemask(), yzface);
+    }
     if (plain) {
-        const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+        int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+        bool lo_b = false, hi_b = false, lo_in = false, hi_in = false;
+        if constexpr (FM != FM_PERIODIC) {
+            if (!p.per[0]) { // x faces: wall / inlet links bounce, an outlet repeats the last column
+                const int e_lo = p.edge[0], e_hi = p.edge[1];
+                lo_b = x == 0 && (e_lo == 1 || e_lo == 2);
+                hi_b = x == p.nx - 1 && (e_hi == 1 || e_hi == 2);
+                lo_in = lo_b && e_lo == 2;
+                hi_in = hi_b && e_hi == 2;
+                if (x == p.nx - 1) xp = p.nx - 1;
+            }
+        }
         const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
         const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+        unsigned bounce = 0u;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
             const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
             const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
-            v[i] = ld_as<V>(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+            if constexpr (FM != FM_PERIODIC) {
+                const bool b = (L::cx(i) == 1 && lo_b) || (L::cx(i) == -1 && hi_b);
+                const long long idx =
+                    b ? (long long)L::opp(i) * p.N + cell : (long long)i * p.N + cell_of(p, sx, sy, sz);
+                v[i] = ld_as<V>(src + idx);
+                bounce |= (b ? 1u : 0u) << i;
+                inlet_only |= ((L::cx(i) == 1 && lo_in) || (L::cx(i) == -1 && hi_in) ? 1u : 0u) << i;
+            } else {
+                v[i] = ld_as<V>(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+            }
         }
-        return 0u;
+        return bounce;
     }
     unsigned bounce = 0u;
-    if constexpr (FACES) {
+    if constexpr (FM == FM_GENERAL) {
         int xm, xp, ym, yp, zm, zp;
         unsigned fl = 0u;
         face_axis(x, p.nx, p.per[0], p.edge[0], p.edge[1], 0, xm, xp, fl);
@@ -430,13 +466,13 @@ __device__ __forceinline__ unsigned pull_core(const Params &p, const typename P:
 
 // f_i(x, t+1) for all i at node (x,y,z): the pulls of pull_core plus the
 // momentum terms of the node's wall / inlet links
-template <class L, class P, bool FACES = true>
+template <class L, class P, int FM = FM_GENERAL>
 __device__ __forceinline__ void pull_all(const Params &p, const typename P::S *__restrict__ src,
                                          const typename P::C *__restrict__ mac_t, int x, int y, int z,
                                          long long cell, typename P::C f[]) {
     unsigned inlet_only;
-    const unsigned bounce = pull_core<L, P, FACES>(p, src, x, y, z, cell, f, inlet_only);
-    if constexpr (FACES) {
+    const unsigned bounce = pull_core<L, P, FM>(p, src, x, y, z, cell, f, inlet_only);
+    if constexpr (FM != FM_PERIODIC) {
         if (bounce) face_terms<L, P>(p, src, mac_t, y, cell, bounce, inlet_only, f);
     }
 }
@@ -480,7 +516,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *
 }
 
 // pull-stream + moments + BGK collision of one node (x, y, z)
-template <class L, class P, bool FACES = true>
+template <class L, class P, int FM = FM_GENERAL>
 __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *__restrict__ src,
                                           typename P::S *__restrict__ dst, const uint8_t *__restrict__ flags,
                                           const typename P::C *__restrict__ mac_t, typename P::C *__restrict__ mac_t1,
@@ -493,7 +529,7 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
         if (fl & FL_BND) return; // boundary nodes: k_bnd
     }
     C f[L::Q];
-    pull_all<L, P, FACES>(p, src, mac_t, x, y, z, cell, f);
+    pull_all<L, P, FM>(p, src, mac_t, x, y, z, cell, f);
     if constexpr (P::exact) {
         double rho, u[3];
         moments_x<L>(p, f, rho, u);
@@ -514,7 +550,7 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
 }
 
 // pull-stream + moments + BGK collision over every fluid node
-template <class L, class P, bool FACES>
+template <class L, class P, int FM>
 __global__ void __launch_bounds__(BULK_THREADS, P::exact ? 4 : BULK_MIN_BLOCKS) k_bulk(Params p, const typename P::S *__restrict__ src,
                                                        typename P::S *__restrict__ dst,
                                                        const uint8_t *__restrict__ flags,
@@ -522,7 +558,7 @@ __global__ void __launch_bounds__(BULK_THREADS, P::exact ? 4 : BULK_MIN_BLOCKS) 
                                                        typename P::C *__restrict__ mac_t1) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= p.nx) return;
-    bulk_node<L, P, FACES>(p, src, dst, flags, mac_t, mac_t1, x, y, z);
+    bulk_node<L, P, FM>(p, src, dst, flags, mac_t, mac_t1, x, y, z);
 }
 
 // Work of one cut link j of body b: the wall value fhat_i(x_A, t) of Eq.
