@@ -241,12 +241,12 @@ __device__ __forceinline__ double link_delta(const BodyDev &b, const double d[3]
 }
 
 // FP32 link distance (reduced-precision modes): same formula as link_delta
-__device__ __forceinline__ float link_delta_f(const BodyDev &b, const float d[3], int cxi, int cyi, int czi) {
-    if (b.halfway) return 0.5f;
+__device__ __forceinline__ float link_delta_f(int halfway, int shape, float R, const float d[3], int cxi, int cyi,
+                                              int czi) {
+    if (halfway) return 0.5f;
     float cx = cxi, cy = cyi, cz = czi;
     float a, bb, cc;
-    const float R = (float)b.R;
-    if (b.shape == 1) {
+    if (shape == 1) {
         a = cx * cx + cy * cy + cz * cz;
         bb = d[0] * cx + d[1] * cy + d[2] * cz;
         cc = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - R * R;
@@ -316,11 +316,15 @@ __device__ __forceinline__ long long cell_of(const Params &p, int x, int y, int 
     return ((long long)z * p.ny + y) * p.nx + x;
 }
 
+// node coordinates of a cell index (domains hold fewer than 2^32 cells, so
+// 32-bit unsigned division is exact)
 __device__ __forceinline__ void coords_of(const Params &p, long long c, int &x, int &y, int &z) {
-    long long row = c / p.nx;
-    x = (int)(c - row * p.nx);
-    z = (int)(row / p.ny);
-    y = (int)(row - (long long)z * p.ny);
+    const unsigned cu = (unsigned)c, nx = (unsigned)p.nx, ny = (unsigned)p.ny;
+    const unsigned row = cu / nx;
+    x = (int)(cu - row * nx);
+    const unsigned zz = row / ny;
+    z = (int)zz;
+    y = (int)(row - zz * ny);
 }
 
 // i-th coordinate of a region axis in ascending wrapped order: the region

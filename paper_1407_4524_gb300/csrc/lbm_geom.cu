@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
                 g.Lcell[jj] = (uint32_t)rc.cell;
                 g.Ldir[jj] = (uint8_t)i;
                 g.Ldelta[jj] = p.exact ? link_delta(B, d, L::cx(i), L::cy(i), L::cz(i))
-                                       : (double)link_delta_f(B, df, L::cx(i), L::cy(i), L::cz(i));
+                                       : (double)link_delta_f(B.halfway, B.shape, (float)B.R, df, L::cx(i), L::cy(i), L::cz(i));
             }
             at++;
         }
