@@ -56,3 +56,61 @@ def test_invalid_descriptor_is_rejected_without_gpu():
     d.lattice, d.nx, d.ny, d.nz, d.tau, d.rho0 = 9, 8, 8, 1, 0.4, 1.0
     rc = lib.lbm_create_domain(ctypes.byref(d), ctypes.byref(h))
     assert rc == 1 and b"tau" in lib.lbm_last_error()
+
+
+def _desc(lbm, spec):
+    d, _, _ = lbm.domain_desc(spec, 0)
+    return d
+
+
+def test_batch_solve_bytes_without_gpu():
+    """Admission arithmetic is host-only: the bytes a solve would hold."""
+    from paper_1407_4524_gb300 import lbm
+    from paper_1407_4524_gb300 import workloads as W
+    import numpy as np
+    lib = lbm.load()
+    rng = np.random.default_rng(3)
+    r = W.serving_request(rng, lattice="D3Q19", precision="fp16")
+    bodies = lbm.body_array(r["bodies"])
+    out = ctypes.c_int64()
+
+    def nbytes(spec, steps):
+        rc = lib.lbm_batch_solve_bytes(ctypes.byref(_desc(lbm, spec)), bodies, len(spec["bodies"]), steps,
+                                       ctypes.byref(out))
+        return rc, out.value
+
+    rc, b16 = nbytes(r, 1000)
+    assert rc == 0
+    n = int(np.prod(r["n"]))
+    assert b16 >= 2 * 19 * 2 * n  # two FP16 population copies at least
+    rc, b16_long = nbytes(r, 5000)
+    assert rc == 0 and b16_long - b16 == 4000 * 18 * 8  # the force/torque series grows with the steps
+    rc, b32 = nbytes(dict(r, precision="fp32"), 1000)
+    assert rc == 0 and b32 - b16 == 2 * 19 * 2 * n  # FP32 doubles the populations only
+    rc, _ = nbytes(dict(r, precision="fp64"), 1000)
+    assert rc == 1 and b"LBM_FP32 or LBM_FP16" in lib.lbm_last_error()
+    rc, _ = nbytes(r, 0)
+    assert rc == 1
+
+
+def test_batch_rejects_bad_arguments_without_gpu():
+    from paper_1407_4524_gb300 import lbm
+    lib = lbm.load()
+    d = lbm.lbm_batch_desc()
+    h = ctypes.c_void_p()
+    d.max_slots, d.budget_bytes = 0, 1 << 20
+    assert lib.lbm_batch_create(ctypes.byref(d), ctypes.byref(h)) == 1 and not h.value
+    d.max_slots, d.budget_bytes = 4, 0
+    assert lib.lbm_batch_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    d.budget_bytes, d.reserved = 1 << 20, 1
+    assert lib.lbm_batch_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    slot = ctypes.c_int()
+    assert lib.lbm_batch_admit(None, None, None, 0, 10, ctypes.byref(slot)) == 1
+    assert lib.lbm_batch_run(None, 1) == 1
+    cnt = ctypes.c_int()
+    assert lib.lbm_batch_poll(None, None, 0, ctypes.byref(cnt)) == 1
+    assert lib.lbm_batch_release(None, 0) == 1
+    assert lib.lbm_batch_time(None, 0) == -1
+    fn = lib.lbm_get_populations_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert fn(None, None) == 1
