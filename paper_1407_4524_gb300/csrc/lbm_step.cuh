@@ -159,10 +159,27 @@ __device__ __forceinline__ void moments_f(const Params &p, const float f[], floa
     u[2] = j2 * inv;
 }
 
+// c_i . u with the lattice components folded in (adds and subtracts only:
+// the library is built without contraction, so products with 0 and +-1 are
+// not removed by the compiler)
+template <class L> __device__ __forceinline__ float cdot_f(int i, const float u[3]) {
+    float s = 0.0f;
+    bool any = false;
+    const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (c[k] == 0) continue;
+        const float t = c[k] > 0 ? u[k] : -u[k];
+        s = any ? s + t : t;
+        any = true;
+    }
+    return s;
+}
+
 // deviation of the equilibrium, f^eq_i - w_i
 template <class L>
 __device__ __forceinline__ float dfeq_f(const Params &p, int i, float drho, const float u[3], float usq15) {
-    float cu = (float)L::cx(i) * u[0] + (float)L::cy(i) * u[1] + (float)L::cz(i) * u[2];
+    const float cu = cdot_f<L>(i, u);
     float poly = fmaf(cu, fmaf(4.5f, cu, 3.0f), -usq15); // 3cu + 4.5cu^2 - 1.5u^2
     float rr = p.eq == 0 ? p.rho0f : 1.0f + drho;
     return L::template w<float>(i) * fmaf(rr, poly, drho);
@@ -423,21 +440,24 @@ __device__ __forceinline__ unsigned pull_core(const Params &p, const typename P:
         }
         const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
         const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+        // 32-bit in-plane indices (fewer than 2^32 cells) and one wide
+        // multiply-add per plane pointer
+        const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, N32 = (unsigned)p.N;
         unsigned bounce = 0u;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
             const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
             const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
+            const unsigned k = ((unsigned)sz * ny + (unsigned)sy) * nx + (unsigned)sx;
             if constexpr (FM != FM_PERIODIC) {
                 const bool b = (L::cx(i) == 1 && lo_b) || (L::cx(i) == -1 && hi_b);
-                const long long idx =
-                    b ? (long long)L::opp(i) * p.N + cell : (long long)i * p.N + cell_of(p, sx, sy, sz);
-                v[i] = ld_as<V>(src + idx);
+                const typename P::S *plane = src + (size_t)N32 * (unsigned)(b ? L::opp(i) : i);
+                v[i] = ld_as<V>(plane + (b ? (unsigned)cell : k));
                 bounce |= (b ? 1u : 0u) << i;
                 inlet_only |= ((L::cx(i) == 1 && lo_in) || (L::cx(i) == -1 && hi_in) ? 1u : 0u) << i;
             } else {
-                v[i] = ld_as<V>(src + (long long)i * p.N + cell_of(p, sx, sy, sz));
+                v[i] = ld_as<V>(src + (size_t)N32 * (unsigned)i + k);
             }
         }
         return bounce;
@@ -545,8 +565,9 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
         moments_f<L>(p, f, drho, u);
         collide_f<L>(p, f, drho, u);
     }
+    const unsigned N32 = (unsigned)p.N, c32 = (unsigned)cell;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
+    for (int i = 0; i < L::Q; ++i) stS(dst + (size_t)N32 * (unsigned)i + c32, f[i]);
 }
 
 // pull-stream + moments + BGK collision over every fluid node

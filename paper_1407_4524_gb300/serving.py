@@ -115,3 +115,32 @@ def serve_sequential(trace, device: int = 0, keep_series: bool = False):
     torch.cuda.synchronize(device)
     makespan = time.perf_counter() - t0
     return _summary(lat, makespan, updates, len(reqs)), series
+
+
+def main(argv=None):
+    """python -m paper_1407_4524_gb300.serving: run the seeded serving trace."""
+    import argparse
+    import json
+
+    from .workloads import serving_trace
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--mode", choices=["batched", "sequential", "both"], default="both")
+    ap.add_argument("--slots", type=int, default=256)
+    ap.add_argument("--ticks", type=int, default=32, help="steps per graph replay")
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16"])
+    args = ap.parse_args(argv)
+    trace = serving_trace(n_requests=args.requests, rate_hz=args.rate, precision=args.precision)
+    out = {}
+    if args.mode in ("batched", "both"):
+        out["batched"], _ = serve_batched(trace, int(args.budget_gb * (1 << 30)), max_slots=args.slots,
+                                          ticks_per_launch=args.ticks)
+    if args.mode in ("sequential", "both"):
+        out["one_at_a_time"], _ = serve_sequential(trace)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
