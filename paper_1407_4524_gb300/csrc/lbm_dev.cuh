@@ -143,6 +143,9 @@ struct Params {
     double tau, omega, rho0, u_in;
     double g[3];
     float omegaf, rho0f, u_inf;
+    float inv_rho0f;  // 1 / rho0f (correctly rounded, as the device division)
+    float keepf;      // 1 - omegaf
+    float wom[19];    // omegaf * w_i
     float gf[3];
 };
 

@@ -42,12 +42,10 @@ __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned coun
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(bar)), "r"(bytes)
+    asm volatile("{\n\t.reg .b64 st;\n\t"
+                 "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
                  : "memory");
-    (void)state;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {

@@ -151,8 +151,7 @@ __device__ __forceinline__ void moments_f(const Params &p, const float f[], floa
         j1 = fmaf(0.5f, p.gf[1], j1);
         j2 = fmaf(0.5f, p.gf[2], j2);
     }
-    float den = p.eq == 0 ? p.rho0f : 1.0f + r;
-    float inv = 1.0f / den;
+    const float inv = p.eq == 0 ? p.inv_rho0f : 1.0f / (1.0f + r);
     drho = r;
     u[0] = j0 * inv;
     u[1] = j1 * inv;
@@ -185,19 +184,22 @@ __device__ __forceinline__ float dfeq_f(const Params &p, int i, float drho, cons
     return L::template w<float>(i) * fmaf(rr, poly, drho);
 }
 
+// BGK relaxation fhat = (1 - omega) f + omega f^eq in the deviation form,
+// with omega w_i taken from the parameters
 template <class L>
 __device__ __forceinline__ void collide_f(const Params &p, float f[], float drho, const float u[3]) {
     const float om = p.omegaf;
     const float usq15 = 1.5f * fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
+    const float rr = p.eq == 0 ? p.rho0f : 1.0f + drho;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        float fe = dfeq_f<L>(p, i, drho, u, usq15);
-        float v = fmaf(-om, f[i] - fe, f[i]);
+        const float cu = cdot_f<L>(i, u);
+        const float poly = fmaf(cu, fmaf(4.5f, cu, 3.0f), -usq15); // 3cu + 4.5cu^2 - 1.5u^2
+        float v = fmaf(p.keepf, f[i], p.wom[i] * fmaf(rr, poly, drho));
         if (p.has_force) {
             float cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
             float cg = cx * p.gf[0] + cy * p.gf[1] + cz * p.gf[2];
             float ug = u[0] * p.gf[0] + u[1] * p.gf[1] + u[2] * p.gf[2];
-            float cu = cx * u[0] + cy * u[1] + cz * u[2];
             v = fmaf((1.0f - 0.5f * om) * L::template w<float>(i), fmaf(9.0f * cu, cg, 3.0f * (cg - ug)), v);
         }
         f[i] = v;
