@@ -353,14 +353,23 @@ def run_serving(args, dev):
     trace = W.serving_trace(n_requests=args.serving_requests, precision="fp16")
     free, _ = __import__("torch").cuda.mem_get_info(dev)
     budget = int(min(64 << 30, 0.5 * free))
-    batched, _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=256, ticks_per_launch=32, device=dev)
+    def rnd(d):
+        return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
+
+    by_slots = {}
+    for slots in sorted({args.serving_slots, 256}):
+        res, _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=slots, ticks_per_launch=32, device=dev)
+        by_slots[slots] = res
+    batched = by_slots[args.serving_slots]
     seq, _ = serving.serve_sequential(trace, device=dev)
     return {
         "trace": f"{len(trace)} requests, Poisson 20/s (seed 4524), D2Q9 {{128x64..1024x512}} / "
                  f"D3Q19 {{64^3..192x96x96}}, 2000-20000 steps, fp16 storage",
         "budget_bytes": budget,
-        "batched": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in batched.items()},
-        "one_at_a_time": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in seq.items()},
+        "slots": args.serving_slots,
+        "batched": rnd(batched),
+        "batched_by_slots": {str(k): rnd(v) for k, v in by_slots.items()},
+        "one_at_a_time": rnd(seq),
         "mlups_ratio": round(batched["mlups"] / seq["mlups"], 3) if seq["mlups"] else None,
         "p50_s": round(batched["p50_s"], 4), "p99_s": round(batched["p99_s"], 4),
     }
@@ -393,6 +402,8 @@ def main():
     ap.add_argument("--bodies", type=int, default=None)
     ap.add_argument("--serving-requests", type=int, default=40,
                     help="requests of the serving trace (0: skip the serving measurement)")
+    ap.add_argument("--serving-slots", type=int, default=16,
+                    help="resident solves at most in the batched serving run (a run with 256 is added)")
     args = ap.parse_args()
     if args.n:
         args.n = tuple(int(v) for v in args.n.split(","))
