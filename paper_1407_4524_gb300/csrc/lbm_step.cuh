@@ -3,28 +3,30 @@
 // lbm_fp32.cu).
 //
 // Storage convention: the population buffer of step t holds the
-// post-collision values fhat(x, t) (Eq. collision) at every fluid node.  One
-// step is, in launch order:
-//   k_links  : for every cut link (x_F fluid, x_A = x_F - c_i solid) compute
-//              the wall value fhat_i(x_A, t) of Eq. Fillipova_interpolation and
-//              store it in the (otherwise unused) slot i of the solid node x_A,
-//              and write the link's momentum-exchange contributions
-//              (Eqs. flow_force_2, flow_torque_2, ForceInMovementMovingFrame,
+// post-collision values fhat(x, t) (Eq. collision) at every fluid node.
+//
+// FP64 mode (parity), one stream, per step:
+//   k_links  : for every cut link (x_F fluid, x_A = x_F - c_i solid) the wall
+//              value fhat_i(x_A, t) of Eq. Fillipova_interpolation, stored in
+//              the (otherwise unused) slot i of the solid node x_A, and the
+//              link's momentum-exchange contributions (Eqs. flow_force_2,
+//              flow_torque_2, ForceInMovementMovingFrame,
 //              TorqueInMovementMovingFrame), which by Eq. Equalities need
 //              exactly that wall value and fhat_ib(x_F, t);
 //   k_bulk   : pull-streaming f_i(x, t+1) = fhat_i(x - c_i, t) (Eq.
 //              streaming) -- at cut links the pull reads the wall value --,
 //              moments (Eqs. LBMmacroscopics_0/1), BGK collision, store;
-//   k_imp    : moving bodies only -- covered / uncovered nodes A+ / A-
-//              (Sec. 3.2.2): impulsive terms of Eqs. ForceInMovement /
-//              TorqueInMovement, refill of uncovered nodes;
-//   k_reduce : deterministic per-body sum of the link contributions into the
-//              force/torque series row of step t.
+//   k_finish : per-body sums of the link contributions in link order into the
+//              force/torque row of step t; for moving bodies the covered /
+//              uncovered nodes A+ / A- (Sec. 3.2.2): impulsive terms of Eqs.
+//              ForceInMovement / TorqueInMovement, refill of uncovered nodes.
+// Every formula there has the FP64 CPU oracle's operation order, so the FP64
+// mode reproduces it bit for bit.
 //
-// P::exact (FP64 mode) evaluates every formula with the same fixed operation
-// order as the FP64 CPU oracle, so the FP64 mode reproduces it bit for bit.
-// The FP32/FP16 modes store f - w and evaluate the deviation form of the same
-// formulas with FP32 arithmetic; the momentum-exchange sums stay FP64.
+// FP32 / FP16 modes: k_bulk skips the boundary nodes (fluid nodes with a solid
+// neighbour), which the boundary-node kernel (lbm_bnd.cuh) steps on a second
+// stream; k_finish converts the exact fixed-point per-body sums.  Storage is
+// f - w, arithmetic FP32.
 #pragma once
 
 #include <type_traits>
