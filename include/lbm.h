@@ -47,7 +47,8 @@ extern "C" {
 #define LBM_ERR_ARG 1      /* invalid argument or descriptor */
 #define LBM_ERR_OOM 2      /* device or host allocation failed */
 #define LBM_ERR_CUDA 3     /* a CUDA runtime call failed (message has the reason) */
-#define LBM_ERR_UNSTABLE 4 /* a NaN or |u| > 0.3 was detected in a checked step */
+#define LBM_ERR_UNSTABLE 4 /* a NaN or |u| > 0.3 was detected in a checked step
+                             (returned by the series / force reads of that solve) */
 #define LBM_ERR_TIMEOUT 5  /* a bounded device wait gave up (serving kernel) */
 #define LBM_ERR_STATE 6    /* call not allowed in the current state */
 
@@ -151,6 +152,9 @@ typedef struct lbm_stats {
     int64_t d2h_bytes;       /* bytes copied device -> host by API calls */
     int64_t timeouts;        /* non-zero: a kernel gave up a bounded wait (the
                                 step's results are invalid; LBM_ERR_TIMEOUT) */
+    int64_t unstable;        /* non-zero: a NaN or |u| > 0.3 was seen at a boundary
+                                node, or a force was not finite (LBM_ERR_UNSTABLE);
+                                domains without bodies are not checked */
 } lbm_stats;
 
 typedef struct lbm_domain lbm_domain;

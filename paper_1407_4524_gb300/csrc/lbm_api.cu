@@ -286,7 +286,8 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
         }
         double umax = std::sqrt(B.U[0] * B.U[0] + B.U[1] * B.U[1] + B.U[2] * B.U[2]) +
                       B.R * std::sqrt(B.W[0] * B.W[0] + B.W[1] * B.W[1] + B.W[2] * B.W[2]);
-        if (umax > 0.5) return fail(LBM_ERR_ARG, "body surface may move at most 0.5 cells per step");
+        if (umax > 0.25) // keeps the fluid next to it below the |u| = 0.3 stability check
+            return fail(LBM_ERR_ARG, "body surface may move at most 0.25 cells per step");
         for (int m = 0; m < k; ++m) {
             double d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
@@ -868,9 +869,12 @@ int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
     if (D->nb == 0 || count == 0) return LBM_OK;
     CK(cudaStreamSynchronize(D->s));
     {
-        unsigned long long flag = 0;
-        CK(cudaMemcpy(&flag, D->counters + 6, sizeof(flag), cudaMemcpyDeviceToHost));
-        if (flag) return fail(LBM_ERR_TIMEOUT, "a stream-collide block gave up waiting for its staged rows");
+        unsigned long long flags[2] = {0, 0}; // unstable, timeout
+        CK(cudaMemcpy(flags, D->counters + 5, sizeof(flags), cudaMemcpyDeviceToHost));
+        if (flags[1]) return fail(LBM_ERR_TIMEOUT, "a stream-collide block gave up waiting for its staged rows");
+        if (flags[0])
+            return fail(LBM_ERR_UNSTABLE, "the solve went unstable (NaN or |u| > 0.3 at a boundary node, or a "
+                                          "non-finite force)");
     }
     const size_t row = (size_t)D->nb * SERIES_ROW;
     int64_t done = 0;
@@ -939,6 +943,7 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     out->uncovered = (int64_t)c[2];
     out->device_bytes = (int64_t)D->bytes;
     out->timeouts = (int64_t)c[6];
+    out->unstable = (int64_t)c[5];
     out->h2d_bytes = D->h2d;
     out->d2h_bytes = D->d2h;
     if (D->nb && D->prec != LBM_FP64 && D->t > 0) {

@@ -93,6 +93,10 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
         uF[0] = j0 * inv;
         uF[1] = j1 * inv;
         uF[2] = j2 * inv;
+        // stability check at the boundary nodes: a NaN or |u| > 0.3 marks the
+        // solve unstable (counters[5]; the host reports LBM_ERR_UNSTABLE)
+        const float usq = uF[0] * uF[0] + uF[1] * uF[1] + uF[2] * uF[2];
+        if (lane == 0 && !(usq < 0.09f)) atomicOr(&sb.counters[5], 1ull);
     }
     const float fb = __shfl_sync(0xffffffffu, fo, ib); // fhat_ib(x, t)
     float fi = 0.0f;

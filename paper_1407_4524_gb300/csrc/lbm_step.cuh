@@ -64,7 +64,8 @@ struct StepBufs {
     double *imp;
     double *series;
     unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered,
-                                  // [3] links of this step, [4] links of the last step
+                                  // [3] links of this step, [4] links of the last step,
+                                  // [5] unstable flag, [6] timeout flag
     unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
 };
@@ -1061,6 +1062,7 @@ template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &
             *a = 0ull;
         }
         row[k < 6 ? k : k + 6] = acc;
+        if (!isfinite(acc)) atomicOr(&sb.counters[5], 1ull); // FP64 mode: a non-finite force marks the solve unstable
     }
     if (!B.moving && threadIdx.x < 6) row[6 + threadIdx.x] = 0.0;
 }

@@ -60,7 +60,7 @@ class lbm_batch_desc(C.Structure):
 class lbm_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("step", "cells", "fluid_cells", "links", "fallback_links",
                                           "covered", "uncovered", "device_bytes", "h2d_bytes", "d2h_bytes",
-                                          "timeouts")]
+                                          "timeouts", "unstable")]
 
 
 class LbmError(RuntimeError):

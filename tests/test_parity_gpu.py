@@ -215,3 +215,23 @@ def test_staged_rows_bitwise(monkeypatch, dim, name, prec):
     assert np.array_equal(out["1"][0][:, fl], out["0"][0][:, fl])
     if out["1"][1] is not None:
         assert np.array_equal(out["1"][1], out["0"][1])
+
+
+def test_unstable_solve_is_reported():
+    """A flow beyond the stability check (|u| > 0.3 at a boundary node) makes
+    the force/torque read of that solve fail with LBM_ERR_UNSTABLE."""
+    from paper_1407_4524_gb300 import lbm
+    for prec in ("fp32", "fp16"):
+        spec = dict(lattice="D2Q9", n=(64, 32), tau=0.51, u0=(0.35, 0.0), precision=prec,
+                    bodies=[dict(shape="cylinder", R=5.0, X0=(32.3, 16.2))])
+        dom = lbm.Domain(spec, device=0)
+        dom.step(3)
+        assert dom.stats()["unstable"] == 1
+        with pytest.raises(lbm.LbmError, match="LBM_ERR_UNSTABLE"):
+            dom.force_torque("static")
+        dom.close()
+    calm = dict(CASES_2D["channel_cylinder"], precision="fp32")
+    dom = lbm.Domain(calm, device=0)
+    dom.step(20)
+    assert dom.stats()["unstable"] == 0
+    dom.close()

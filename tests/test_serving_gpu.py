@@ -168,3 +168,23 @@ def test_serving_loop_matches_sequential():
     for r in reqs:
         assert np.array_equal(ser_b[r["id"]], ser_s[r["id"]])
     assert sb["p50_s"] > 0 and sb["p99_s"] >= sb["p50_s"]
+
+
+def test_unstable_solve_is_isolated():
+    """One solve going unstable is reported for that slot only; the others are
+    unaffected (bit-identical to alone)."""
+    from paper_1407_4524_gb300 import lbm
+    good = _mix()[2]
+    bad = dict(lattice="D2Q9", n=(64, 32), tau=0.51, u0=(0.35, 0.0), precision="fp32", steps=40,
+               bodies=[dict(shape="cylinder", R=5.0, X0=(32.3, 16.2))])
+    batch = lbm.Batch(1 << 30, max_slots=4, ticks_per_launch=16)
+    sg, sb = batch.admit(good), batch.admit(bad)
+    done = set()
+    while len(done) < 2:
+        batch.run(2)
+        done.update(batch.poll())
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_UNSTABLE"):
+        batch.force_torque(sb, "static")
+    ref, _ = _alone(good)
+    assert np.array_equal(batch.force_torque(sg, "static"), ref["static"])
+    batch.close()
