@@ -601,6 +601,10 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
         // the default)
         const char *es = std::getenv("LBM_STAGED");
         p.staged = (es && es[0] == '1') ? 1 : 0;
+        // LBM_STAGED_TEST_EXPIRE=1 (tests only): the staged kernel's waits
+        // expire, which must surface as LBM_ERR_TIMEOUT
+        const char *ex = std::getenv("LBM_STAGED_TEST_EXPIRE");
+        p.stage_expire_test = (ex && ex[0] == '1') ? 1 : 0;
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
         p.nsm = sms;

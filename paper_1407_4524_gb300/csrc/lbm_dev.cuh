@@ -137,6 +137,7 @@ struct Params {
     int nonper;  // 1 if any axis is non-periodic
     int exact;   // FP64 mode: link geometry in FP64 (else FP32)
     int staged;  // reduced precision: stream-collide from rows staged in shared memory
+    int stage_expire_test; // test hook: the staged kernel issues no copy, so its waits expire
     int nsm;     // multiprocessors of the device
     long long series_cap;
     long long me_stride; // ME contribution arrays are [ME_PER_LINK][me_stride]

@@ -19,9 +19,9 @@
 //
 // Requirements (checked by the launcher): nx * sizeof(S) a multiple of 16
 // bytes (so every row and every window edge is 16-byte aligned), reduced
-// precision.  Every wait on an mbarrier is bounded; on expiry the block
-// records LBM_TIMEOUT_FLAG in counters[6], waits (bounded) for its own copies
-// and returns.
+// precision.  Every wait on an mbarrier is bounded (one second); on expiry
+// the block records LBM_TIMEOUT_FLAG in counters[6], waits (bounded) for its
+// own copies and returns.
 #pragma once
 
 #include "lbm_step.cuh"
@@ -31,7 +31,8 @@ namespace lbm {
 constexpr int STAGE_SEG = 256;        // nodes per segment (threads per block) at most
 constexpr int STAGE_BLOCKS_PER_SM = 4;
 constexpr unsigned long long LBM_TIMEOUT_FLAG = 1ull;
-constexpr long long STAGE_WAIT_LIMIT = 1ll << 22; // try_wait polls before giving up
+constexpr unsigned long long STAGE_WAIT_NS = 1000000000ull; // a wait gives up after one second
+constexpr long long STAGE_WAIT_ROUNDS = 1ll << 24;             // and after this many poll rounds at most
 
 __device__ __forceinline__ unsigned smem_u32(const void *ptr) {
     return (unsigned)__cvta_generic_to_shared(ptr);
@@ -59,10 +60,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0u;
 }
 
-// bounded wait for the phase of the given parity; false if it never completed
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase of the given parity (one second, and a round
+// count); false if it never completed
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (long long k = 0; k < STAGE_WAIT_LIMIT; ++k)
-        if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long r = 0; r < STAGE_WAIT_ROUNDS; ++r) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > STAGE_WAIT_NS) return false;
+    }
     return false;
 }
 
@@ -103,6 +116,9 @@ __device__ __forceinline__ void stage_issue(const Params &p, const S *__restrict
     const unsigned total = (unsigned)L::Q * (row_bytes + (wrap_lo ? chunk : 0u) + (wrap_hi ? chunk : 0u));
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
+    // test hook: register the bytes but issue no copy, so that the wait on
+    // this stage expires (the timeout path is exercised without a fault)
+    if (p.stage_expire_test) return;
     if (lane < L::Q) {
         const int i = lane;
         int ym, yp, zm, zp;

@@ -235,3 +235,25 @@ def test_unstable_solve_is_reported():
     dom.step(20)
     assert dom.stats()["unstable"] == 0
     dom.close()
+
+
+def test_staged_wait_expiry_is_reported(monkeypatch):
+    """The staged kernel's mbarrier waits are bounded (one second): with the
+    test hook its stages never fill, every block gives up, and the solve's
+    reads return LBM_ERR_TIMEOUT; the context stays usable."""
+    from paper_1407_4524_gb300 import lbm
+    spec = dict(CASES_2D["channel_cylinder_64"], precision="fp32")
+    monkeypatch.setenv("LBM_STAGED", "1")
+    monkeypatch.setenv("LBM_STAGED_TEST_EXPIRE", "1")
+    dom = lbm.Domain(spec, device=0)
+    dom.step(1)
+    assert dom.stats()["timeouts"] == 1
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_TIMEOUT"):
+        dom.force_torque("static")
+    dom.close()
+    monkeypatch.delenv("LBM_STAGED_TEST_EXPIRE")
+    dom = lbm.Domain(spec, device=0)  # same process, same context: works
+    dom.step(5)
+    assert dom.stats()["timeouts"] == 0
+    assert np.isfinite(dom.force_torque("static")).all()
+    dom.close()
