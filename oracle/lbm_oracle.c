@@ -24,6 +24,8 @@
  *   5. prescribed body motion, covered / uncovered node sets A+ and A-,
  *      impulsive terms (Eqs. ForceInMovement, TorqueInMovement) and the
  *      refill of uncovered nodes (Sec. 3, discussion after Eq. ForceInMovement)
+ *   6. free bodies: forward-Euler Newton-Euler update of their velocity from
+ *      the step's lattice-frame force and torque, weight and buoyancy
  *
  * Floating point: everything is FP64, loops run in cell order
  * ((z*ny + y)*nx + x) and direction order, and every formula is written as a
@@ -70,18 +72,20 @@ typedef struct {
     double u_in;
     double g[3];
     double u0[3];
+    double gravity[3]; /* acceleration of the free bodies (weight less buoyancy) */
 } or_desc;
 
 typedef struct {
     int shape;    /* OR_SHAPE_* */
     int halfway;  /* 1: every link of this body takes Delta = 1/2 */
     int invert;   /* 1: the solid is OUTSIDE the surface (test geometry) */
-    int pad;
+    int free;     /* 1: moved by the flow force and torque (Newton-Euler), else prescribed */
     double R;
     double X0[3]; /* centre at step t0 */
     double U[3];  /* translation velocity (lattice units per step) */
     double W[3];  /* angular velocity */
     long long t0;
+    double density_ratio; /* free bodies: body density / rho0 */
 } or_body;
 
 typedef struct {
@@ -742,6 +746,38 @@ static int one_step(or_dom *o)
         o->solid_next = tmp;
     }
 
+    /* 6: free bodies -- Newton's and Euler's equations integrated by forward
+     * Euler (the paper's test section): the pose advances with U(t) (so the
+     * A+/A- sets of this step were explicit), then the lattice-frame force and
+     * torque of step t (Eqs. ForceInMovement / TorqueInMovement: static plus
+     * impulsive terms), with weight less buoyancy (rho_b - rho0) V g, give
+     * U(t+1) and W(t+1).  V: pi R^2 nz (cylinder), 4/3 pi R^3 (sphere); the
+     * moment of inertia about the centre M R^2 / 2 (cylinder, about z) or
+     * 2/5 M R^2 (sphere). */
+    for (int bi = 0; bi < o->nb; ++bi) {
+        or_body *b = &o->b[bi];
+        if (!b->free) continue;
+        const double *Rw = row + (size_t)bi * OR_ROW;
+        const double PI = 3.14159265358979323846;
+        double V = b->shape == OR_SHAPE_SPHERE ? 4.0 / 3.0 * PI * b->R * b->R * b->R
+                                               : PI * b->R * b->R * (double)o->n[2];
+        double M = b->density_ratio * o->d.rho0 * V;
+        double I = b->shape == OR_SHAPE_SPHERE ? 0.4 * M * b->R * b->R : 0.5 * M * b->R * b->R;
+        double X1[3];
+        pose(b, t + 1, X1);
+        for (int a = 0; a < 3; ++a) b->X0[a] = X1[a];
+        b->t0 = t + 1;
+        for (int a = 0; a < 3; ++a) {
+            double F = Rw[a] + Rw[6 + a];
+            b->U[a] = b->U[a] + (F + (b->density_ratio - 1.0) * o->d.rho0 * V * o->d.gravity[a]) / M;
+        }
+        if (b->shape == OR_SHAPE_SPHERE) {
+            for (int a = 0; a < 3; ++a) b->W[a] = b->W[a] + (Rw[3 + a] + Rw[9 + a]) / I;
+        } else {
+            b->W[2] = b->W[2] + (Rw[5] + Rw[11]) / I;
+        }
+    }
+
     double *tmp = o->f;
     o->f = o->fnew;
     o->fnew = tmp;
@@ -766,6 +802,22 @@ long long or_fallbacks(const or_dom *o) { return o ? o->n_fallback : -1; }
 
 /* series rows [first, first+count) of every body: out[count][nb][18] with
  * Fs Ts (static form), Fi Ti (impulsive terms), Fm Tm (moving frame) */
+/* body state at the current step t: X(t), U(t), W(t) (9 doubles per body) */
+int or_get_bodies(const or_dom *o, double *out)
+{
+    if (!o || (o->nb && !out)) return OR_ERR_ARG;
+    for (int bi = 0; bi < o->nb; ++bi) {
+        double X[3];
+        pose(&o->b[bi], o->t, X);
+        for (int a = 0; a < 3; ++a) {
+            out[9 * bi + a] = X[a];
+            out[9 * bi + 3 + a] = o->b[bi].U[a];
+            out[9 * bi + 6 + a] = o->b[bi].W[a];
+        }
+    }
+    return OR_OK;
+}
+
 int or_get_series(const or_dom *o, long long first, long long count, double *out)
 {
     if (!o || !out || first < 0 || count < 0 || first + count > o->nrec) return OR_ERR_ARG;

@@ -28,15 +28,15 @@ class _Desc(C.Structure):
         ("eq", C.c_int), ("edge", C.c_int * 6), ("inlet_parabolic", C.c_int),
         ("has_force", C.c_int), ("refill", C.c_int),
         ("tau", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double),
-        ("g", C.c_double * 3), ("u0", C.c_double * 3),
+        ("g", C.c_double * 3), ("u0", C.c_double * 3), ("gravity", C.c_double * 3),
     ]
 
 
 class _Body(C.Structure):
     _fields_ = [
-        ("shape", C.c_int), ("halfway", C.c_int), ("invert", C.c_int), ("pad", C.c_int),
+        ("shape", C.c_int), ("halfway", C.c_int), ("invert", C.c_int), ("free", C.c_int),
         ("R", C.c_double), ("X0", C.c_double * 3), ("U", C.c_double * 3),
-        ("W", C.c_double * 3), ("t0", C.c_longlong),
+        ("W", C.c_double * 3), ("t0", C.c_longlong), ("density_ratio", C.c_double),
     ]
 
 
@@ -76,7 +76,7 @@ def _load():
     lib.or_fallbacks.restype = C.c_longlong
     lib.or_fallbacks.argtypes = [P]
     lib.or_get_series.argtypes = [P, C.c_longlong, C.c_longlong, P]
-    for name in ("or_get_f", "or_get_fhat", "or_get_macro", "or_get_solid", "or_get_edge_me"):
+    for name in ("or_get_f", "or_get_fhat", "or_get_macro", "or_get_solid", "or_get_edge_me", "or_get_bodies"):
         getattr(lib, name).argtypes = [P, P]
     lib.or_links.restype = C.c_longlong
     lib.or_links.argtypes = [P, C.c_int, C.c_longlong, P, P, P]
@@ -121,6 +121,8 @@ def _body_struct(b) -> _Body:
     for k in range(3):
         s.W[k] = float(W[k])
     s.t0 = int(b.get("t0", 0))
+    s.free = int(bool(b.get("free", False)))
+    s.density_ratio = float(b.get("density_ratio", 1.0))
     return s
 
 
@@ -131,8 +133,9 @@ class Oracle:
     Optional: ``rho0``, ``eq`` ("incomp"/"standard"), ``edges`` (per axis
     "periodic" | (lo, hi) kinds among "wall", "inlet", "outlet"), ``inlet``
     ({"profile": "uniform"/"parabolic", "u": ...}), ``force``, ``u0``,
-    ``refill`` ("uB"/"ubar"), ``bodies`` (list of dicts: shape, R, X0, U, W,
-    halfway, invert, t0).
+    ``refill`` ("uB"/"ubar"), ``gravity`` (acceleration of free bodies),
+    ``bodies`` (list of dicts: shape, R, X0, U, W, halfway, invert, t0, free,
+    density_ratio).
     """
 
     def __init__(self, spec: dict):
@@ -156,6 +159,9 @@ class Oracle:
         for k in range(3):
             d.u0[k] = float(u0[k]) if k < len(u0) else 0.0
         d.refill = {"uB": 0, "ubar": 1}[spec.get("refill", "uB")]
+        gv = tuple(spec.get("gravity", (0.0, 0.0, 0.0)))
+        for k in range(3):
+            d.gravity[k] = float(gv[k]) if k < len(gv) else 0.0
         d.tau = float(spec["tau"])
         d.rho0 = float(spec.get("rho0", 1.0))
         h = lib.or_create(C.byref(d))
@@ -224,6 +230,13 @@ class Oracle:
         out = np.empty(self.N, dtype=np.int32)
         self.lib.or_get_solid(self.h, out.ctypes.data)
         return self._grid(out, ())
+
+    def body_state(self) -> np.ndarray:
+        """[n_bodies, 9]: X(t), U(t), W(t)"""
+        nb = len(self.bodies)
+        out = np.zeros(max(nb, 1) * 9)
+        self.lib.or_get_bodies(self.h, out.ctypes.data)
+        return out.reshape(-1, 9)[:nb]
 
     def edge_me(self) -> np.ndarray:
         out = np.empty(6)
