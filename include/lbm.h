@@ -125,18 +125,32 @@ typedef struct lbm_domain_desc {
     lbm_alloc_fn alloc;      /* optional device allocator (NULL -> cudaMalloc) */
     lbm_free_fn free;        /* matching free */
     void *alloc_ctx;         /* passed through to alloc / free */
+    double gravity[3];       /* acceleration of the free bodies: each feels its
+                                weight less buoyancy, (rho_b - rho0) V gravity */
 } lbm_domain_desc;
 
 typedef struct lbm_body {
     int shape;       /* LBM_SHAPE_* */
     int halfway;     /* 1: every cut link of the body takes Delta = 1/2 */
-    int reserved[2]; /* must be 0 */
+    int free_body;   /* 0: prescribed motion; 1: free -- moved by the flow (below) */
+    int reserved;    /* must be 0 */
     double R;        /* radius */
     double X0[3];    /* centre at step t0 */
-    double U[3];     /* translation velocity: X(t) = X0 + (t - t0) U */
-    double W[3];     /* angular velocity (2-D: W[2]) */
+    double U[3];     /* translation velocity: X(t) = X0 + (t - t0) U (free: initial) */
+    double W[3];     /* angular velocity (2-D: W[2]) (free: initial) */
     int64_t t0;      /* step at which the body is at X0 */
+    double density_ratio; /* free bodies: body density / rho0 (> 0) */
 } lbm_body;
+/* Free bodies follow Newton's and Euler's equations by forward Euler, as the
+ * paper's sedimentation tests do: in step t the body moves with U(t), W(t)
+ * (so the covered / uncovered sets of the step are explicit), then
+ *   U(t+1) = U(t) + (F(t) + (rho_b - rho0) V gravity) / M,  M = rho_b V
+ *   W(t+1) = W(t) + T(t) / I
+ * with F, T the lattice-frame force and torque of step t (Eqs. ForceInMovement,
+ * TorqueInMovement: static plus impulsive terms), V = pi R^2 nz (cylinder) or
+ * 4/3 pi R^3 (sphere), I = M R^2 / 2 (cylinder, about z) or 2/5 M R^2 (sphere).
+ * A free body that comes within 2 cells of a non-periodic face or whose
+ * surface speed exceeds 0.25 makes the series reads return LBM_ERR_STATE. */
 
 typedef struct lbm_stats {
     int64_t step;            /* current time step t */
@@ -234,6 +248,10 @@ int lbm_get_populations(lbm_domain *dom, double *out);
  * Output, layout and synchronisation as lbm_get_populations. */
 #define LBM_NOALLOC_MAX_VALUES 4194304
 int lbm_get_populations_noalloc(lbm_domain *dom, double *out);
+
+/* Body state at the current step: out[n_bodies][9] = X(t), U(t), W(t).
+ * Synchronises.  (Free bodies: their integrated motion.) */
+int lbm_get_body_state(lbm_domain *dom, double *out);
 
 /* Owning body index of every node at the current step (-1: fluid),
  * out[nz][ny][nx].  Synchronises. */

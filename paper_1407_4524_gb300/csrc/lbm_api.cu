@@ -83,7 +83,7 @@ struct lbm_domain {
     uint16_t *owner[2] = {nullptr, nullptr};
     unsigned long long *counters = nullptr;
     // bodies
-    int nb = 0, n_moving = 0;
+    int nb = 0, n_moving = 0, n_free = 0;
     std::vector<lbm_body> hb;
     std::vector<BodyDev> hbd;
     std::vector<void *> body_allocs;
@@ -197,12 +197,13 @@ void free_body_buffers(lbm_domain *D) {
     D->bn_static_cap = D->bn_mov_cap = 0;
     D->lists_dirty = true;
     D->prep_dirty = true;
-    D->nb = D->n_moving = 0;
+    D->nb = D->n_moving = D->n_free = 0;
     D->nchunk_all = D->nchunk_mov = 0;
     D->link_cap_total = D->apm_cap_total = 0;
 }
 
 bool is_moving(const lbm_body &b) {
+    if (b.free_body) return true; // its velocity is set by the flow
     for (int k = 0; k < 3; ++k)
         if (b.U[k] != 0.0 || b.W[k] != 0.0) return true;
     return false;
@@ -238,6 +239,8 @@ void body_params(const lbm_domain *D, const lbm_body &b, BodyDev &o) {
         o.W[k] = b.W[k];
     }
     o.t0 = b.t0;
+    o.free = b.free_body ? 1 : 0;
+    o.density_ratio = b.density_ratio;
     const int n[3] = {D->p.nx, D->p.ny, D->p.nz};
     for (int a = 0; a < 3; ++a) {
         int e = 2 * (int)std::ceil(b.R) + 2 * REGION_MARGIN + 5;
@@ -264,7 +267,10 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
         if (B.shape == LBM_SHAPE_SPHERE && D->Q == 9)
             return fail(LBM_ERR_ARG, "body " + std::to_string(k) + ": spheres need D3Q19 (use a cylinder in 2-D)");
         if (!(B.R > 0.0) || !std::isfinite(B.R)) return fail(LBM_ERR_ARG, "body radius must be positive");
-        if (B.reserved[0] || B.reserved[1]) return fail(LBM_ERR_ARG, "reserved body fields must be 0");
+        if (B.reserved) return fail(LBM_ERR_ARG, "reserved body fields must be 0");
+        if (B.free_body != 0 && B.free_body != 1) return fail(LBM_ERR_ARG, "free_body must be 0 or 1");
+        if (B.free_body && !(B.density_ratio > 0.0 && std::isfinite(B.density_ratio)))
+            return fail(LBM_ERR_ARG, "a free body needs a positive density ratio");
         if (B.halfway != 0 && B.halfway != 1) return fail(LBM_ERR_ARG, "halfway must be 0 or 1");
         for (int a = 0; a < 3; ++a) {
             if (a == 2 && (B.shape == LBM_SHAPE_CYLINDER)) continue;
@@ -280,7 +286,7 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
                 if (B.X0[a] - B.R < 3.0 || B.X0[a] + B.R > nn[a] - 4.0)
                     return fail(LBM_ERR_ARG, "body " + std::to_string(k) +
                                                  " must keep 3 cells from non-periodic faces");
-                if (B.U[a] != 0.0)
+                if (B.U[a] != 0.0 && !B.free_body)
                     return fail(LBM_ERR_ARG, "bodies may not translate along a non-periodic axis");
             }
         }
@@ -396,6 +402,8 @@ int upload_bodies(lbm_domain *D) {
         }
     }
     D->n_moving = (int)mov.size();
+    D->n_free = 0;
+    for (int b = 0; b < D->nb; ++b) D->n_free += D->hbd[b].free ? 1 : 0;
     D->nchunk_all = (int)all.size();
     D->nchunk_mov = (int)mv.size();
     CK(cudaMemcpyAsync(D->dbodies, D->hbd.data(), sizeof(BodyDev) * D->nb, cudaMemcpyHostToDevice, D->s));
@@ -454,6 +462,7 @@ int do_step(lbm_domain *D) {
         D->ev_used += 2;
     }
     if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->t, D->counters, D->s));
     D->t += 1;
     return LBM_OK;
 }
@@ -505,6 +514,7 @@ int do_step_overlapped(lbm_domain *D) {
     ba.poses = D->poses;
     CK(launch_bnd(Q, prec, D->p, ba, sb, D->side_serial ? D->bnd_grid_full : D->bnd_grid, ss));
     CK(launch_finish(Q, prec, D->p, sb, ss));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->t, D->counters, ss));
     if (!D->side_serial) CK(cudaEventRecord(D->ev_side, D->s2));
     if (D->timing) {
         if (D->ev_used + 2 > D->ev.size()) {
@@ -620,6 +630,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     for (int k = 0; k < 3; ++k) {
         p.g[k] = d.has_force ? d.force[k] : 0.0;
         p.gf[k] = (float)p.g[k];
+        p.gravity[k] = d.gravity[k];
     }
     p.omegaf = (float)p.omega;
     p.rho0f = (float)d.rho0;
@@ -811,6 +822,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
 
 int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if (!D || !hb || n != D->nb) return fail(LBM_ERR_ARG, "update needs the same number of bodies");
+    if (D->n_free) return fail(LBM_ERR_STATE, "free bodies move with the flow; their kinematics cannot be set");
     for (int b = 0; b < n; ++b) {
         const lbm_body &o = D->hb[b], &v = hb[b];
         if (o.shape != v.shape || o.R != v.R || o.halfway != v.halfway)
@@ -873,12 +885,15 @@ int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
     if (D->nb == 0 || count == 0) return LBM_OK;
     CK(cudaStreamSynchronize(D->s));
     {
-        unsigned long long flags[2] = {0, 0}; // unstable, timeout
+        unsigned long long flags[3] = {0, 0, 0}; // unstable, timeout, free body out of range
         CK(cudaMemcpy(flags, D->counters + 5, sizeof(flags), cudaMemcpyDeviceToHost));
         if (flags[1]) return fail(LBM_ERR_TIMEOUT, "a stream-collide block gave up waiting for its staged rows");
         if (flags[0])
             return fail(LBM_ERR_UNSTABLE, "the solve went unstable (NaN or |u| > 0.3 at a boundary node, or a "
                                           "non-finite force)");
+        if (flags[2])
+            return fail(LBM_ERR_STATE, "a free body came within 2 cells of a non-periodic face or moved faster "
+                                       "than 0.25 at its surface");
     }
     const size_t row = (size_t)D->nb * SERIES_ROW;
     int64_t done = 0;
@@ -921,6 +936,25 @@ int lbm_get_populations(lbm_domain *D, double *out) {
     if (e == cudaSuccess) e = cudaMemcpy(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost);
     D->release(tmp);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("populations: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_get_body_state(lbm_domain *D, double *out) {
+    if (!D || (D->nb && !out)) return fail(LBM_ERR_ARG, "invalid arguments");
+    if (D->nb == 0) return LBM_OK;
+    std::vector<BodyDev> hb((size_t)D->nb);
+    CK(cudaStreamSynchronize(D->s));
+    CK(cudaMemcpy(hb.data(), D->dbodies, sizeof(BodyDev) * D->nb, cudaMemcpyDeviceToHost));
+    D->d2h += (long long)(sizeof(BodyDev) * D->nb);
+    for (int b = 0; b < D->nb; ++b) {
+        const double dt = (double)(D->t - hb[b].t0);
+        for (int a = 0; a < 3; ++a) {
+            volatile double step = dt * hb[b].U[a]; // no contraction with the add below
+            out[9 * b + a] = hb[b].X0[a] + step;
+            out[9 * b + 3 + a] = hb[b].U[a];
+            out[9 * b + 6 + a] = hb[b].W[a];
+        }
+    }
     return LBM_OK;
 }
 
@@ -1002,6 +1036,7 @@ int lbm_launches_per_step(const lbm_domain *D, int *out) {
         *out = 3 + (D->n_moving ? 3 : (D->prep_dirty ? 1 : 0)); // bulk, bnd, finish (+ prep, geometry)
     else
         *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
+    if (D->n_free) *out += 1; // free-body update
     return LBM_OK;
 }
 

@@ -143,6 +143,7 @@ struct Params {
     long long me_stride; // ME contribution arrays are [ME_PER_LINK][me_stride]
     double tau, omega, rho0, u_in;
     double g[3];
+    double gravity[3]; // acceleration of the free bodies
     float omegaf, rho0f, u_inf;
     float inv_rho0f;  // 1 / rho0f (correctly rounded, as the device division)
     float keepf;      // 1 - omegaf
@@ -162,6 +163,8 @@ struct BodyDev {
     long long apm_off, apm_cap;   // segment in the covered/uncovered list
     int ext[3];                   // region extents (cells) per axis
     int chunk_base;               // first geometry chunk of this body
+    int free;                     // moved by the flow force and torque (Newton-Euler)
+    double density_ratio;         // free bodies: body density / rho0
 };
 
 // ------------------------------------------------------- FP64 geometry ------

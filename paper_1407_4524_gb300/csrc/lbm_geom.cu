@@ -610,6 +610,57 @@ static cudaError_t import_t(int prec, const Params &p, const double *in, void *p
     return cudaGetLastError();
 }
 
+// Free bodies (one thread per body), after the force/torque row of step t is
+// complete: the pose advances with U(t) -- the motion the step's A+/A- sets
+// were built from --, then forward Euler gives U(t+1) and W(t+1) from the
+// lattice-frame force and torque (Eqs. ForceInMovement, TorqueInMovement:
+// static plus impulsive terms), weight less buoyancy (rho_b - rho0) V g and
+// M = rho_b V, I = M R^2/2 (cylinder, about z) or 2/5 M R^2 (sphere).  The
+// body record keeps X0 = X(t+1), t0 = t+1, so pose(t+1), pose(t+2) follow.
+// A body within 2 cells of a non-periodic face, or faster than 0.25 at its
+// surface, sets counters[7].
+__global__ void k_free(Params p, BodyDev *bodies, const double *series, long long t, unsigned long long *counters) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nb) return;
+    BodyDev &B = bodies[b];
+    if (!B.free) return;
+    const double *Rw = series + ((t % p.series_cap) * p.nb + b) * SERIES_ROW;
+    const double PI = 3.14159265358979323846;
+    const double V = B.shape == 1 ? 4.0 / 3.0 * PI * B.R * B.R * B.R : PI * B.R * B.R * (double)p.nz;
+    const double M = B.density_ratio * p.rho0 * V;
+    const double I = B.shape == 1 ? 0.4 * M * B.R * B.R : 0.5 * M * B.R * B.R;
+    double X1[3];
+    pose(B, t + 1, X1);
+    for (int a = 0; a < 3; ++a) B.X0[a] = X1[a];
+    B.t0 = t + 1;
+    for (int a = 0; a < 3; ++a) {
+        const double F = Rw[a] + Rw[6 + a];
+        B.U[a] = B.U[a] + (F + (B.density_ratio - 1.0) * p.rho0 * V * p.gravity[a]) / M;
+    }
+    if (B.shape == 1) {
+        for (int a = 0; a < 3; ++a) B.W[a] = B.W[a] + (Rw[3 + a] + Rw[9 + a]) / I;
+    } else {
+        B.W[2] = B.W[2] + (Rw[5] + Rw[11]) / I;
+    }
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) {
+        if (p.per[a] || (a == 2 && B.shape == 0)) continue;
+        const double n = (double)axis_len(p, a);
+        if (X1[a] - B.R < 2.0 || X1[a] + B.R > n - 3.0) bad = true;
+    }
+    const double us = sqrt(B.U[0] * B.U[0] + B.U[1] * B.U[1] + B.U[2] * B.U[2]) +
+                      B.R * sqrt(B.W[0] * B.W[0] + B.W[1] * B.W[1] + B.W[2] * B.W[2]);
+    if (!(us <= 0.25)) bad = true;
+    if (bad) atomicOr(&counters[7], 1ull);
+}
+
+cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, long long t,
+                        unsigned long long *counters, cudaStream_t s) {
+    if (p.nb == 0) return cudaSuccess;
+    k_free<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, series, t, counters);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s) {
     return Q == 9 ? export_t<Lat<9>>(prec, p, pop, out, s) : export_t<Lat<19>>(prec, p, pop, out, s);
 }

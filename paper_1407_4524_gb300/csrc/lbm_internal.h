@@ -124,6 +124,10 @@ cudaError_t launch_bfinish(SolveDev *solves, const int *slots, int nslots, cudaS
 // boundary-node lists of step t from scratch (all bodies)
 cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 
+// free bodies: Newton-Euler update after the force/torque row of step t
+cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, long long t,
+                        unsigned long long *counters, cudaStream_t s);
+
 // population export: fhat as FP64 f (adds w back for the shifted modes)
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);
 cudaError_t launch_import(int Q, int prec, const Params &p, const double *in, void *pop, cudaStream_t s);

@@ -39,13 +39,15 @@ class lbm_domain_desc(C.Structure):
         ("device", C.c_int), ("tau", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double),
         ("force", C.c_double * 3), ("u0", C.c_double * 3), ("series_capacity", C.c_int64),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+        ("gravity", C.c_double * 3),
     ]
 
 
 class lbm_body(C.Structure):
     _fields_ = [
-        ("shape", C.c_int), ("halfway", C.c_int), ("reserved", C.c_int * 2), ("R", C.c_double),
-        ("X0", C.c_double * 3), ("U", C.c_double * 3), ("W", C.c_double * 3), ("t0", C.c_int64),
+        ("shape", C.c_int), ("halfway", C.c_int), ("free_body", C.c_int), ("reserved", C.c_int),
+        ("R", C.c_double), ("X0", C.c_double * 3), ("U", C.c_double * 3), ("W", C.c_double * 3),
+        ("t0", C.c_int64), ("density_ratio", C.c_double),
     ]
 
 
@@ -95,6 +97,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_get_series.argtypes = [P, C.c_int64, C.c_int64, P]
     lib.lbm_get_populations.argtypes = [P, P]
     lib.lbm_get_solid.argtypes = [P, P]
+    lib.lbm_get_body_state.argtypes = [P, P]
     lib.lbm_get_stats.argtypes = [P, C.POINTER(lbm_stats)]
     lib.lbm_time.restype = C.c_int64
     lib.lbm_time.argtypes = [P]
@@ -149,6 +152,8 @@ def body_struct(b: dict) -> lbm_body:
     for k in range(3):
         s.X0[k], s.U[k], s.W[k] = float(X0[k]), float(U[k]), float(W[k])
     s.t0 = int(b.get("t0", 0))
+    s.free_body = int(bool(b.get("free", False)))
+    s.density_ratio = float(b.get("density_ratio", 1.0))
     return s
 
 
@@ -181,6 +186,9 @@ def domain_desc(spec: dict, device: int = 0, series_capacity: int = 0):
         d.u0[j] = float(u0[j]) if j < len(u0) else 0.0
     d.tau = float(spec["tau"])
     d.rho0 = float(spec.get("rho0", 1.0))
+    gv = tuple(spec.get("gravity", (0.0, 0.0, 0.0)))
+    for j in range(3):
+        d.gravity[j] = float(gv[j]) if j < len(gv) else 0.0
     d.device = int(device)
     d.series_capacity = int(series_capacity or spec.get("series_capacity", 0) or 0)
     return d, q, n
@@ -304,6 +312,14 @@ class Domain:
         _check(self.lib.lbm_get_populations(self.h, out.ctypes.data))
         nx, ny, nz = self.shape
         return out.reshape(self.q, nz, ny, nx)
+
+    def body_state(self) -> np.ndarray:
+        """[n_bodies, 9]: X(t), U(t), W(t)"""
+        nb = len(self.bodies)
+        out = np.zeros(max(nb, 1) * 9)
+        if nb:
+            _check(self.lib.lbm_get_body_state(self.h, out.ctypes.data))
+        return out.reshape(-1, 9)[:nb]
 
     def solid(self) -> np.ndarray:
         out = np.empty(self.N, dtype=np.int32)
