@@ -61,6 +61,8 @@ def _workload(name: str, precision: str, n=None, bodies=None):
         return W.moving_cylinders_2d(precision=precision)
     if name == "channel_cylinder_2d":
         return W.channel_cylinder_2d(precision=precision)
+    if name == "sedimenting_disc_2d":
+        return W.sedimenting_disc_2d(precision=precision)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -284,8 +286,10 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
+    has_free = any(b.get("free", False) for b in bodies)
     for _ in range(e2e_steps):
-        dom.update_bodies(bodies)
+        if not has_free:  # free bodies take their kinematics from the flow: nothing to upload
+            dom.update_bodies(bodies)
         dom.step(1)
         dom.lib.lbm_get_force_torque(dom.h, dom.t - 1, 1, 0, out.ctypes.data)
     torch.cuda.synchronize()

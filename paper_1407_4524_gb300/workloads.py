@@ -74,6 +74,29 @@ def sphere_channel_3d(precision: str = "fp32") -> dict:
     )
 
 
+def sedimenting_disc_2d(precision: str = "fp64", density_ratio: float = 1.01, steps: int = 20000) -> dict:
+    """The paper's sedimenting disc in lattice units: D2Q9 135 x 1073, tau 0.6,
+    walls on every face, a free disc of diameter d = W/4 falling under gravity.
+    Physical data: W = 4 mm (135 nodes), H = 8 W, d = 1 mm, water (rho 1000,
+    nu 1e-6 m^2/s), g = 9.81 m/s^2; nu_lattice = (tau - 1/2)/3 fixes the time
+    step dt = nu_lattice dx^2 / nu, so g_lattice = g dt^2 / dx.  The centre
+    starts 25 mm above the bottom and 0.76 mm off the channel axis."""
+    nx, ny, tau = 135, 1073, 0.6
+    dx = 4e-3 / nx
+    nu_l = (tau - 0.5) / 3.0
+    dt = nu_l * dx * dx / 1e-6
+    g_l = 9.81 * dt * dt / dx
+    R = 0.5e-3 / dx
+    x0 = 0.5 * (nx - 1) + 7.6e-4 / dx
+    y0 = 25e-3 / dx
+    return dict(
+        name="sedimenting_disc_2d", lattice="D2Q9", n=(nx, ny), tau=tau,
+        edges={"x": ("wall", "wall"), "y": ("wall", "wall")}, gravity=(0.0, -g_l),
+        bodies=[dict(shape="cylinder", R=R, X0=(x0, y0), free=True, density_ratio=float(density_ratio))],
+        precision=precision, steps=steps,
+    )
+
+
 def _unit_vector(rng) -> np.ndarray:
     v = rng.standard_normal(3)
     return v / np.linalg.norm(v)

@@ -4,6 +4,8 @@
   populations and force/torque series;
 * moving cylinders, D2Q9 512x256: FP64 (bit-identical) and FP32 over 300 steps;
 * sphere channel, D3Q19 256x128x128: FP64 / FP32 / FP16 over 3 steps;
+* sedimenting disc, D2Q9 135x1073 with a free disc: FP64 (bit-identical,
+  trajectory included) and FP32 over 400 steps;
 * 64-sphere box, D3Q19 512x256x256, FP32 -- exactly the benchmark's launch
   configuration: the force/torque of sampled moving spheres is checked
   against the oracle run on a periodic sub-box around each sphere.  The fluid
@@ -148,3 +150,29 @@ def test_sphere_swarm_full_size_sampled(oracle_mod):
         out[str(i)] = errs
         assert max(errs.values()) <= TOL_RED_FT, (i, errs)
     _report("sphere_swarm_3d_fp32_sampled_4", out)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sedimenting_disc_full_size(oracle_mod, prec):
+    """The paper's sedimenting disc (D2Q9 135x1073, walls, free disc,
+    r_rho = 1.01) over 400 steps: FP64 bit-identical series and trajectory;
+    FP32 within tolerance."""
+    from paper_1407_4524_gb300 import lbm, workloads as W
+    spec = W.sedimenting_disc_2d(prec)
+    steps = 400
+    dom = lbm.Domain(spec, device=0)
+    dom.step(steps)
+    ref = oracle_mod.Oracle(spec)
+    ref.step(steps)
+    st, st_ref = dom.body_state(), ref.body_state()
+    assert st_ref[0, 4] < 0  # it falls
+    if prec == "fp64":
+        assert np.array_equal(dom.series(), ref.series())
+        assert np.array_equal(st, st_ref)
+        err = 0.0
+    else:
+        err = ft_rel_error(dom.force_torque("lattice"), ref.force_torque("lattice"), spec)
+        assert err <= TOL_RED_FT
+        assert np.abs(st[:, :3] - st_ref[:, :3]).max() <= 1e-6
+    _report(f"sedimenting_disc_2d_{prec}_{steps}", {"lattice_ft_rel": err, "uy_final": float(st_ref[0, 4]),
+                                                     "dy": float(st_ref[0, 1] - spec["bodies"][0]["X0"][1])})
