@@ -56,6 +56,7 @@
 
 #define OR_SHAPE_CYLINDER 0 /* disc in the x-y plane, infinite along z */
 #define OR_SHAPE_SPHERE 1
+#define OR_SHAPE_ELLIPSE 2 /* ellipse in the x-y plane (semi-axes R, R2), infinite along z */
 
 #define OR_ROW 18 /* Fs Ts Fi Ti Fm Tm, 3 components each */
 
@@ -86,6 +87,8 @@ typedef struct {
     double W[3];  /* angular velocity */
     long long t0;
     double density_ratio; /* free bodies: body density / rho0 */
+    double R2;            /* ellipse: the second semi-axis (along the body's y axis) */
+    double theta0;        /* ellipse: angle of the body's x axis at step t0 */
 } or_body;
 
 typedef struct {
@@ -169,6 +172,66 @@ static void pose(const or_body *b, long long t, double X[3])
     for (int k = 0; k < 3; ++k) X[k] = b->X0[k] + dt * b->U[k];
 }
 
+/* orientation about z at step t: theta(t) = theta0 + (t - t0) W_z */
+static double orient(const or_body *b, long long t)
+{
+    double dt = (double)(t - b->t0);
+    return b->theta0 + dt * b->W[2];
+}
+
+/*
+ * sin and cos by the Cody-Waite reduction (Cody & Waite, "Software Manual for
+ * the Elementary Functions", 1980): k = nearest integer to x 2/pi, r = x - k pi/2
+ * with pi/2 split into three parts (the first two of 33 significant bits, so
+ * k P1 and k P2 are exact for |k| < 2^20), then the Taylor series of sin and
+ * cos on |r| <= pi/4 (terms to r^19 / r^18: truncation below 1e-19) in
+ * Horner form, and the quadrant of k.  Written out here so that the result is
+ * the same on every machine (the library evaluates the same formula).
+ */
+static void sincos_cw(double x, double *s_out, double *c_out)
+{
+    const double P1 = 0x1.921fb544p+0;
+    const double P2 = 0x1.0b4611a6p-34;
+    const double P3 = 0x1.3198a2e037073p-69;
+    double kf = nearbyint(x * 0.6366197723675814);
+    double r = ((x - kf * P1) - kf * P2) - kf * P3;
+    double r2 = r * r;
+    double ps = 8.22063524662433e-18;
+    ps = ps * r2 - 2.8114572543455206e-15;
+    ps = ps * r2 + 7.647163731819816e-13;
+    ps = ps * r2 - 1.6059043836821613e-10;
+    ps = ps * r2 + 2.505210838544172e-08;
+    ps = ps * r2 - 2.7557319223985893e-06;
+    ps = ps * r2 + 0.0001984126984126984;
+    ps = ps * r2 - 0.008333333333333333;
+    ps = ps * r2 + 0.16666666666666666;
+    double sr = r - r * r2 * ps; /* r - r^3/3! + ... */
+    double pc = 1.5619206968586225e-16;
+    pc = pc * r2 - 4.779477332387385e-14;
+    pc = pc * r2 + 1.1470745597729725e-11;
+    pc = pc * r2 - 2.08767569878681e-09;
+    pc = pc * r2 + 2.755731922398589e-07;
+    pc = pc * r2 - 2.48015873015873e-05;
+    pc = pc * r2 + 0.001388888888888889;
+    pc = pc * r2 - 0.041666666666666664;
+    pc = pc * r2 + 0.5;
+    double cr = 1.0 - r2 * pc; /* 1 - r^2/2! + ... */
+    long q = (long)kf & 3;
+    if (q == 0) {
+        *s_out = sr;
+        *c_out = cr;
+    } else if (q == 1) {
+        *s_out = cr;
+        *c_out = -sr;
+    } else if (q == 2) {
+        *s_out = -sr;
+        *c_out = -cr;
+    } else {
+        *s_out = -cr;
+        *c_out = sr;
+    }
+}
+
 static void disp(const or_dom *o, const double X[3], int x, int y, int z, double r[3])
 {
     r[0] = axis_disp(o, 0, (double)x, X[0]);
@@ -191,25 +254,56 @@ static void body_velocity(const or_body *b, const double r[3], double v[3])
     for (int k = 0; k < 3; ++k) v[k] = b->U[k] + wr[k];
 }
 
-static int inside(const or_body *b, const double r[3])
+/* coordinates of an offset in the ellipse's own axes (orientation co, si) */
+static void body_axes(double co, double si, const double v[3], double *xi, double *eta)
 {
-    double s = r[0] * r[0] + r[1] * r[1];
-    if (b->shape == OR_SHAPE_SPHERE) s = s + r[2] * r[2];
-    int in = s <= b->R * b->R;
+    *xi = co * v[0] + si * v[1];
+    *eta = co * v[1] - si * v[0];
+}
+
+/* r: offset from the centre; co, si: cos and sin of the body's orientation */
+static int inside(const or_body *b, const double r[3], double co, double si)
+{
+    int in;
+    if (b->shape == OR_SHAPE_ELLIPSE) {
+        double xi, eta;
+        body_axes(co, si, r, &xi, &eta);
+        double qx = xi / b->R, qy = eta / b->R2;
+        in = qx * qx + qy * qy <= 1.0;
+    } else {
+        double s = r[0] * r[0] + r[1] * r[1];
+        if (b->shape == OR_SHAPE_SPHERE) s = s + r[2] * r[2];
+        in = s <= b->R * b->R;
+    }
     return b->invert ? !in : in;
 }
 
 /*
  * Fractional distance Delta = |x_F - x_B| / |x_F - x_A| (Sec. 2.1): the
  * root s in (0,1] of |d - s c|^2 = R^2 with d = x_F - X (fluid node relative
- * to the centre) and c = c_i, so that x_B = x_F - Delta c_i.
+ * to the centre) and c = c_i, so that x_B = x_F - Delta c_i.  For an ellipse
+ * the same quadratic in the scaled body axes (the surface is the unit circle
+ * there).
  */
-static double link_delta(const or_body *b, const double d[3], const int ci[3])
+static double link_delta(const or_body *b, const double d[3], const int ci[3], double co, double si)
 {
     if (b->halfway) return 0.5;
     double cx = ci[0], cy = ci[1], cz = ci[2];
     double a, bb, cc;
-    if (b->shape == OR_SHAPE_SPHERE) {
+    if (b->shape == OR_SHAPE_ELLIPSE) {
+        /* |d' - s c'|^2 in the metric diag(1/R^2, 1/R2^2) of the body's axes */
+        const double cv[3] = {cx, cy, cz};
+        double dx, dy, kx, ky;
+        body_axes(co, si, d, &dx, &dy);
+        body_axes(co, si, cv, &kx, &ky);
+        dx = dx / b->R;
+        dy = dy / b->R2;
+        kx = kx / b->R;
+        ky = ky / b->R2;
+        a = kx * kx + ky * ky;
+        bb = dx * kx + dy * ky;
+        cc = (dx * dx + dy * dy) - 1.0;
+    } else if (b->shape == OR_SHAPE_SPHERE) {
         a = cx * cx + cy * cy + cz * cz;
         bb = d[0] * cx + d[1] * cy + d[2] * cz;
         cc = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - b->R * b->R;
@@ -407,15 +501,16 @@ static void rasterise(or_dom *o, long long t, int *owner)
     for (long x = 0; x < o->N; ++x) owner[x] = -1;
     for (int bi = 0; bi < o->nb; ++bi) {
         const or_body *b = &o->b[bi];
-        double X[3];
+        double X[3], so, co;
         pose(b, t, X);
+        sincos_cw(orient(b, t), &so, &co);
         if (b->invert) { /* solid outside: test the whole lattice */
             for (int z = 0; z < o->n[2]; ++z)
                 for (int y = 0; y < o->n[1]; ++y)
                     for (int x = 0; x < o->n[0]; ++x) {
                         double r[3];
                         disp(o, X, x, y, z, r);
-                        if (inside(b, r)) owner[cell(o, x, y, z)] = bi;
+                        if (inside(b, r, co, so)) owner[cell(o, x, y, z)] = bi;
                     }
             continue;
         }
@@ -446,7 +541,7 @@ static void rasterise(or_dom *o, long long t, int *owner)
                     if (!ok) continue;
                     double r[3];
                     disp(o, X, p[0], p[1], p[2], r);
-                    if (inside(b, r)) owner[cell(o, p[0], p[1], p[2])] = bi;
+                    if (inside(b, r, co, so)) owner[cell(o, p[0], p[1], p[2])] = bi;
                 }
     }
 }
@@ -596,10 +691,11 @@ static int one_step(or_dom *o)
                         v = o->fhat[(long)i * N + s];
                     } else if (k == K_BODY) {
                         const or_body *b = &o->b[body];
-                        double X[3], d[3], uB[3], rB[3];
+                        double X[3], d[3], uB[3], rB[3], so, co;
                         pose(b, t, X);
+                        sincos_cw(orient(b, t), &so, &co);
                         disp(o, X, x, y, z, d);
-                        double delta = link_delta(b, d, o->c[i]);
+                        double delta = link_delta(b, d, o->c[i], co, so);
                         for (int a = 0; a < 3; ++a) rB[a] = d[a] - delta * o->c[i][a];
                         body_velocity(b, rB, uB);
                         v = wall_value(o, xc, x, y, z, i, delta, uB, &fallback);
@@ -647,10 +743,11 @@ static int one_step(or_dom *o)
                         continue;
                     }
                     const or_body *b = &o->b[body];
-                    double X[3], d[3], rB[3], v[3], pm[3];
+                    double X[3], d[3], rB[3], v[3], pm[3], so, co;
                     pose(b, t, X);
+                    sincos_cw(orient(b, t), &so, &co);
                     disp(o, X, x, y, z, d);
-                    double delta = link_delta(b, d, c);
+                    double delta = link_delta(b, d, c, co, so);
                     for (int a = 0; a < 3; ++a) rB[a] = d[a] - delta * c[a];
                     body_velocity(b, rB, v);
                     double *R = row + (size_t)body * OR_ROW;
@@ -759,13 +856,23 @@ static int one_step(or_dom *o)
         if (!b->free) continue;
         const double *Rw = row + (size_t)bi * OR_ROW;
         const double PI = 3.14159265358979323846;
-        double V = b->shape == OR_SHAPE_SPHERE ? 4.0 / 3.0 * PI * b->R * b->R * b->R
-                                               : PI * b->R * b->R * (double)o->n[2];
+        double V, I;
+        if (b->shape == OR_SHAPE_SPHERE) {
+            V = 4.0 / 3.0 * PI * b->R * b->R * b->R;
+        } else if (b->shape == OR_SHAPE_ELLIPSE) {
+            V = PI * b->R * b->R2 * (double)o->n[2];
+        } else {
+            V = PI * b->R * b->R * (double)o->n[2];
+        }
         double M = b->density_ratio * o->d.rho0 * V;
-        double I = b->shape == OR_SHAPE_SPHERE ? 0.4 * M * b->R * b->R : 0.5 * M * b->R * b->R;
+        if (b->shape == OR_SHAPE_SPHERE) I = 0.4 * M * b->R * b->R;
+        else if (b->shape == OR_SHAPE_ELLIPSE) I = 0.25 * M * (b->R * b->R + b->R2 * b->R2);
+        else I = 0.5 * M * b->R * b->R;
         double X1[3];
         pose(b, t + 1, X1);
+        double th1 = orient(b, t + 1);
         for (int a = 0; a < 3; ++a) b->X0[a] = X1[a];
+        b->theta0 = th1;
         b->t0 = t + 1;
         for (int a = 0; a < 3; ++a) {
             double F = Rw[a] + Rw[6 + a];
@@ -802,6 +909,9 @@ long long or_fallbacks(const or_dom *o) { return o ? o->n_fallback : -1; }
 
 /* series rows [first, first+count) of every body: out[count][nb][18] with
  * Fs Ts (static form), Fi Ti (impulsive terms), Fm Tm (moving frame) */
+/* test hook: the sin / cos the oracle uses for body orientations */
+void or_sincos(double x, double *s, double *c) { sincos_cw(x, s, c); }
+
 /* body state at the current step t: X(t), U(t), W(t) (9 doubles per body) */
 int or_get_bodies(const or_dom *o, double *out)
 {
@@ -891,12 +1001,13 @@ long long or_links(const or_dom *o, int bi, long long cap, long long *cells, int
                     int body;
                     if (classify(o, x, y, z, i, &s, &body) != K_BODY || body != bi) continue;
                     if (cnt < cap) {
-                        double X[3], d[3];
+                        double X[3], d[3], so, co;
                         pose(&o->b[bi], o->t, X);
+                        sincos_cw(orient(&o->b[bi], o->t), &so, &co);
                         disp(o, X, x, y, z, d);
                         if (cells) cells[cnt] = xc;
                         if (dirs) dirs[cnt] = i;
-                        if (deltas) deltas[cnt] = link_delta(&o->b[bi], d, o->c[i]);
+                        if (deltas) deltas[cnt] = link_delta(&o->b[bi], d, o->c[i], co, so);
                     }
                     cnt++;
                 }

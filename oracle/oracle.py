@@ -19,7 +19,7 @@ _lib = None
 SERIES_FIELDS = ("Fs", "Ts", "Fi", "Ti", "Fm", "Tm")
 
 _EDGE = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
-_SHAPE = {"cylinder": 0, "sphere": 1}
+_SHAPE = {"cylinder": 0, "sphere": 1, "ellipse": 2}
 
 
 class _Desc(C.Structure):
@@ -37,6 +37,7 @@ class _Body(C.Structure):
         ("shape", C.c_int), ("halfway", C.c_int), ("invert", C.c_int), ("free", C.c_int),
         ("R", C.c_double), ("X0", C.c_double * 3), ("U", C.c_double * 3),
         ("W", C.c_double * 3), ("t0", C.c_longlong), ("density_ratio", C.c_double),
+        ("R2", C.c_double), ("theta0", C.c_double),
     ]
 
 
@@ -81,8 +82,18 @@ def _load():
     lib.or_links.restype = C.c_longlong
     lib.or_links.argtypes = [P, C.c_int, C.c_longlong, P, P, P]
     lib.or_lattice.argtypes = [C.c_int, P, P, P]
+    lib.or_sincos.argtypes = [C.c_double, P, P]
     _lib = lib
     return lib
+
+
+def sincos(x: float):
+    """the oracle's own sin and cos (used for body orientations)"""
+    lib = _load()
+    s = C.c_double()
+    c = C.c_double()
+    lib.or_sincos(float(x), C.byref(s), C.byref(c))
+    return s.value, c.value
 
 
 def lattice_tables(q: int):
@@ -123,6 +134,8 @@ def _body_struct(b) -> _Body:
     s.t0 = int(b.get("t0", 0))
     s.free = int(bool(b.get("free", False)))
     s.density_ratio = float(b.get("density_ratio", 1.0))
+    s.R2 = float(b.get("R2", b["R"]))
+    s.theta0 = float(b.get("theta0", 0.0))
     return s
 
 
@@ -135,7 +148,7 @@ class Oracle:
     ({"profile": "uniform"/"parabolic", "u": ...}), ``force``, ``u0``,
     ``refill`` ("uB"/"ubar"), ``gravity`` (acceleration of free bodies),
     ``bodies`` (list of dicts: shape, R, X0, U, W, halfway, invert, t0, free,
-    density_ratio).
+    density_ratio; ellipses: shape "ellipse", R and R2 the semi-axes, theta0).
     """
 
     def __init__(self, spec: dict):
