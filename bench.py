@@ -63,6 +63,8 @@ def _workload(name: str, precision: str, n=None, bodies=None):
         return W.channel_cylinder_2d(precision=precision)
     if name == "sedimenting_disc_2d":
         return W.sedimenting_disc_2d(precision=precision)
+    if name == "sedimenting_ellipse_2d":
+        return W.sedimenting_ellipse_2d(precision=precision)
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -89,6 +89,8 @@ extern "C" {
 
 #define LBM_SHAPE_CYLINDER 0 /* disc in the x-y plane (infinite along z in 3-D) */
 #define LBM_SHAPE_SPHERE 1
+#define LBM_SHAPE_ELLIPSE 2  /* ellipse in the x-y plane, semi-axes R and R2,
+                                orientation theta (infinite along z in 3-D) */
 
 /* Which force/torque form lbm_get_force_torque returns. */
 #define LBM_FT_STATIC 0    /* Eqs. flow_force_2 / flow_torque_2 */
@@ -140,6 +142,9 @@ typedef struct lbm_body {
     double W[3];     /* angular velocity (2-D: W[2]) (free: initial) */
     int64_t t0;      /* step at which the body is at X0 */
     double density_ratio; /* free bodies: body density / rho0 (> 0) */
+    double R2;       /* LBM_SHAPE_ELLIPSE: second semi-axis, 0 < R2 <= R */
+    double theta0;   /* LBM_SHAPE_ELLIPSE: angle of the R axis to x at step t0;
+                        theta(t) = theta0 + (t - t0) W[2] */
 } lbm_body;
 /* Free bodies follow Newton's and Euler's equations by forward Euler, as the
  * paper's sedimentation tests do: in step t the body moves with U(t), W(t)

@@ -241,10 +241,12 @@ void body_params(const lbm_domain *D, const lbm_body &b, BodyDev &o) {
     o.t0 = b.t0;
     o.free = b.free_body ? 1 : 0;
     o.density_ratio = b.density_ratio;
+    o.R2 = b.shape == LBM_SHAPE_ELLIPSE ? b.R2 : b.R;
+    o.theta0 = b.shape == LBM_SHAPE_ELLIPSE ? b.theta0 : 0.0;
     const int n[3] = {D->p.nx, D->p.ny, D->p.nz};
     for (int a = 0; a < 3; ++a) {
         int e = 2 * (int)std::ceil(b.R) + 2 * REGION_MARGIN + 5;
-        if ((a == 2 && b.shape == LBM_SHAPE_CYLINDER) || e >= n[a]) e = n[a];
+        if ((a == 2 && along_z(b.shape)) || e >= n[a]) e = n[a];
         o.ext[a] = e;
     }
     long long vol = (long long)o.ext[0] * o.ext[1] * o.ext[2];
@@ -262,8 +264,10 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
     const int nn[3] = {D->p.nx, D->p.ny, D->p.nz};
     for (int k = 0; k < n; ++k) {
         const lbm_body &B = b[k];
-        if (B.shape != LBM_SHAPE_CYLINDER && B.shape != LBM_SHAPE_SPHERE)
+        if (B.shape != LBM_SHAPE_CYLINDER && B.shape != LBM_SHAPE_SPHERE && B.shape != LBM_SHAPE_ELLIPSE)
             return fail(LBM_ERR_ARG, "body " + std::to_string(k) + ": unknown shape");
+        if (B.shape == LBM_SHAPE_ELLIPSE && !(B.R2 > 0.0 && B.R2 <= B.R && std::isfinite(B.theta0)))
+            return fail(LBM_ERR_ARG, "an ellipse needs 0 < R2 <= R and a finite theta0");
         if (B.shape == LBM_SHAPE_SPHERE && D->Q == 9)
             return fail(LBM_ERR_ARG, "body " + std::to_string(k) + ": spheres need D3Q19 (use a cylinder in 2-D)");
         if (!(B.R > 0.0) || !std::isfinite(B.R)) return fail(LBM_ERR_ARG, "body radius must be positive");
@@ -273,7 +277,7 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
             return fail(LBM_ERR_ARG, "a free body needs a positive density ratio");
         if (B.halfway != 0 && B.halfway != 1) return fail(LBM_ERR_ARG, "halfway must be 0 or 1");
         for (int a = 0; a < 3; ++a) {
-            if (a == 2 && (B.shape == LBM_SHAPE_CYLINDER)) continue;
+            if (a == 2 && along_z(B.shape)) continue;
             if (!std::isfinite(B.X0[a]) || !std::isfinite(B.U[a]) || !std::isfinite(B.W[a]))
                 return fail(LBM_ERR_ARG, "body state must be finite");
             if (D->p.per[a]) {
@@ -297,7 +301,7 @@ int validate_bodies(const lbm_domain *D, const lbm_body *b, int n) {
         for (int m = 0; m < k; ++m) {
             double d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
-                if (a == 2 && (B.shape == LBM_SHAPE_CYLINDER || b[m].shape == LBM_SHAPE_CYLINDER)) continue;
+                if (a == 2 && (along_z(B.shape) || along_z(b[m].shape))) continue;
                 double v = min_image(B.X0[a] + (0 - B.t0) * B.U[a] - (b[m].X0[a] + (0 - b[m].t0) * b[m].U[a]),
                                      nn[a], D->p.per[a] != 0);
                 d2 += v * v;
@@ -831,7 +835,7 @@ int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
             double xo = o.X0[a] + (double)(D->t - o.t0) * o.U[a];
             double xv = v.X0[a] + (double)(D->t - v.t0) * v.U[a];
             if (std::fabs(xo - xv) > 1e-9) return fail(LBM_ERR_ARG, "the pose at the current step may not jump");
-            if (!D->p.per[a] && v.U[a] != 0.0 && !(a == 2 && v.shape == LBM_SHAPE_CYLINDER))
+            if (!D->p.per[a] && v.U[a] != 0.0 && !(a == 2 && along_z(v.shape)))
                 return fail(LBM_ERR_ARG, "bodies may not translate along a non-periodic axis");
         }
     }

@@ -118,7 +118,9 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
             }
             d[q] = (float)kk - (float)Pf[3 + q];
         }
-        const float dl = link_delta_f(Bi.halfway, Bi.shape, (float)Bi.R, d, cxi, cyi, czi);
+        const double *Po = a.poses + (long long)bi * POSE_STRIDE + 18; // orientation at t
+        const float dl = link_delta_f(Bi.halfway, Bi.shape, (float)Bi.R, (float)Bi.R2, (float)Po[0], (float)Po[1],
+                                      d, cxi, cyi, czi);
         const float rb[3] = {d[0] - dl * cxi, d[1] - dl * cyi, d[2] - dl * czi};
         const float W0 = (float)Bi.W[0], W1 = (float)Bi.W[1], W2 = (float)Bi.W[2];
         const float uB[3] = {(float)Bi.U[0] + (W1 * rb[2] - W2 * rb[1]),

@@ -165,7 +165,67 @@ struct BodyDev {
     int chunk_base;               // first geometry chunk of this body
     int free;                     // moved by the flow force and torque (Newton-Euler)
     double density_ratio;         // free bodies: body density / rho0
+    double R2;                    // ellipse: second semi-axis (R is the first, R >= R2)
+    double theta0;                // ellipse: orientation about z at step t0
 };
+
+// shape codes: 0 cylinder (x-y disc, along z), 1 sphere, 2 ellipse (x-y, along z)
+__host__ __device__ inline bool along_z(int shape) { return shape != 1; }
+
+// orientation about z at step t: theta(t) = theta0 + (t - t0) W_z
+__device__ __forceinline__ double orient(const BodyDev &b, long long t) {
+    double dt = (double)(t - b.t0);
+    return b.theta0 + dt * b.W[2];
+}
+
+// sin and cos by the Cody-Waite reduction (Cody & Waite, "Software Manual for
+// the Elementary Functions", 1980): k = nearest integer to x 2/pi, r = x - k pi/2
+// with pi/2 in three parts (the first two of 33 significant bits, so k P1 and
+// k P2 are exact for |k| < 2^20), Taylor series of sin and cos on |r| <= pi/4
+// to r^19 / r^18 in Horner form, then the quadrant.  The same formula is
+// evaluated everywhere so that orientations agree bit for bit.
+__device__ __forceinline__ void sincos_cw(double x, double &s_out, double &c_out) {
+    const double P1 = 0x1.921fb544p+0;
+    const double P2 = 0x1.0b4611a6p-34;
+    const double P3 = 0x1.3198a2e037073p-69;
+    const double kf = nearbyint(x * 0.6366197723675814);
+    const double r = ((x - kf * P1) - kf * P2) - kf * P3;
+    const double r2 = r * r;
+    double ps = 8.22063524662433e-18;
+    ps = ps * r2 - 2.8114572543455206e-15;
+    ps = ps * r2 + 7.647163731819816e-13;
+    ps = ps * r2 - 1.6059043836821613e-10;
+    ps = ps * r2 + 2.505210838544172e-08;
+    ps = ps * r2 - 2.7557319223985893e-06;
+    ps = ps * r2 + 0.0001984126984126984;
+    ps = ps * r2 - 0.008333333333333333;
+    ps = ps * r2 + 0.16666666666666666;
+    const double sr = r - r * r2 * ps;
+    double pc = 1.5619206968586225e-16;
+    pc = pc * r2 - 4.779477332387385e-14;
+    pc = pc * r2 + 1.1470745597729725e-11;
+    pc = pc * r2 - 2.08767569878681e-09;
+    pc = pc * r2 + 2.755731922398589e-07;
+    pc = pc * r2 - 2.48015873015873e-05;
+    pc = pc * r2 + 0.001388888888888889;
+    pc = pc * r2 - 0.041666666666666664;
+    pc = pc * r2 + 0.5;
+    const double cr = 1.0 - r2 * pc;
+    const long long q = (long long)kf & 3;
+    if (q == 0) {
+        s_out = sr;
+        c_out = cr;
+    } else if (q == 1) {
+        s_out = cr;
+        c_out = -sr;
+    } else if (q == 2) {
+        s_out = -sr;
+        c_out = -cr;
+    } else {
+        s_out = -cr;
+        c_out = sr;
+    }
+}
 
 // ------------------------------------------------------- FP64 geometry ------
 // These follow one fixed expression each; they are shared by all precision
@@ -218,18 +278,44 @@ __device__ __forceinline__ void body_velocity(const BodyDev &b, const double r[3
     for (int k = 0; k < 3; ++k) v[k] = b.U[k] + wr[k];
 }
 
-__device__ __forceinline__ bool inside(const BodyDev &b, const double r[3]) {
+// coordinates of an offset in an ellipse's own axes (orientation co, si)
+__device__ __forceinline__ void body_axes(double co, double si, double v0, double v1, double &xi, double &eta) {
+    xi = co * v0 + si * v1;
+    eta = co * v1 - si * v0;
+}
+
+// r: offset from the centre; co, si: cos and sin of the orientation (ellipse)
+__device__ __forceinline__ bool inside(const BodyDev &b, const double r[3], double co, double si) {
+    if (b.shape == 2) {
+        double xi, eta;
+        body_axes(co, si, r[0], r[1], xi, eta);
+        const double qx = xi / b.R, qy = eta / b.R2;
+        return qx * qx + qy * qy <= 1.0;
+    }
     double s = r[0] * r[0] + r[1] * r[1];
     if (b.shape == 1) s = s + r[2] * r[2];
     return s <= b.R * b.R;
 }
 
-// Delta of Sec. 2.1: root s in (0,1] of |d - s c|^2 = R^2 (x_F outside)
-__device__ __forceinline__ double link_delta(const BodyDev &b, const double d[3], int cxi, int cyi, int czi) {
+// Delta of Sec. 2.1: root s in (0,1] of |d - s c|^2 = R^2 (x_F outside); for
+// an ellipse the same quadratic in the scaled body axes
+__device__ __forceinline__ double link_delta(const BodyDev &b, const double d[3], int cxi, int cyi, int czi,
+                                             double co, double si) {
     if (b.halfway) return 0.5;
     double cx = cxi, cy = cyi, cz = czi;
     double a, bb, cc;
-    if (b.shape == 1) {
+    if (b.shape == 2) {
+        double dx, dy, kx, ky;
+        body_axes(co, si, d[0], d[1], dx, dy);
+        body_axes(co, si, cx, cy, kx, ky);
+        dx = dx / b.R;
+        dy = dy / b.R2;
+        kx = kx / b.R;
+        ky = ky / b.R2;
+        a = kx * kx + ky * ky;
+        bb = dx * kx + dy * ky;
+        cc = (dx * dx + dy * dy) - 1.0;
+    } else if (b.shape == 1) {
         a = cx * cx + cy * cy + cz * cz;
         bb = d[0] * cx + d[1] * cy + d[2] * cz;
         cc = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - b.R * b.R;
@@ -248,12 +334,18 @@ __device__ __forceinline__ double link_delta(const BodyDev &b, const double d[3]
 }
 
 // FP32 link distance (reduced-precision modes): same formula as link_delta
-__device__ __forceinline__ float link_delta_f(int halfway, int shape, float R, const float d[3], int cxi, int cyi,
-                                              int czi) {
+__device__ __forceinline__ float link_delta_f(int halfway, int shape, float R, float R2, float co, float si,
+                                              const float d[3], int cxi, int cyi, int czi) {
     if (halfway) return 0.5f;
     float cx = cxi, cy = cyi, cz = czi;
     float a, bb, cc;
-    if (shape == 1) {
+    if (shape == 2) {
+        float dx = (co * d[0] + si * d[1]) / R, dy = (co * d[1] - si * d[0]) / R2;
+        float kx = (co * cx + si * cy) / R, ky = (co * cy - si * cx) / R2;
+        a = kx * kx + ky * ky;
+        bb = dx * kx + dy * ky;
+        cc = (dx * dx + dy * dy) - 1.0f;
+    } else if (shape == 1) {
         a = cx * cx + cy * cy + cz * cz;
         bb = d[0] * cx + d[1] * cy + d[2] * cz;
         cc = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - R * R;
@@ -275,8 +367,12 @@ struct Frame {
     int xi[3];
     float fr[3];
     double Xw[3];
+    double co, si;   // orientation (ellipse)
+    float cof, sif;
 };
 
+// Xw points at the wrapped pose of t or t+1 in a poses record; the matching
+// orientation (cos, sin) sits 15 entries further (see POSE_STRIDE)
 __device__ __forceinline__ void make_frame(const double Xw[3], Frame &f) {
     for (int a = 0; a < 3; ++a) {
         double fl = floor(Xw[a]);
@@ -284,6 +380,10 @@ __device__ __forceinline__ void make_frame(const double Xw[3], Frame &f) {
         f.fr[a] = (float)(Xw[a] - fl);
         f.Xw[a] = Xw[a];
     }
+    f.co = Xw[15];
+    f.si = Xw[16];
+    f.cof = (float)f.co;
+    f.sif = (float)f.si;
 }
 
 __device__ __forceinline__ void frame_disp_f(const Params &p, const Frame &f, int x, int y, int z, float d[3]) {
@@ -306,16 +406,31 @@ __device__ __forceinline__ bool inside_screened(const Params &p, const BodyDev &
                                                 int z) {
     float d[3];
     frame_disp_f(p, f, x, y, z, d);
-    float s = d[0] * d[0] + d[1] * d[1];
-    if (B.shape == 1) s += d[2] * d[2];
-    const float R2 = (float)(B.R * B.R);
-    const float band = 1e-4f * R2 + 0.05f;
-    if (s < R2 - band) return true;
-    if (s > R2 + band) return false;
+    float s, R2;
+    if (B.shape == 2) { // scaled to the first semi-axis: the unit ellipse times R^2
+        const float xi = f.cof * d[0] + f.sif * d[1], eta = f.cof * d[1] - f.sif * d[0];
+        const float k = (float)(B.R / B.R2);
+        s = xi * xi + (k * eta) * (k * eta);
+        R2 = (float)(B.R * B.R);
+        const float band = (1e-4f * R2 + 0.05f) * k * k;
+        if (s < R2 - band) return true;
+        if (s > R2 + band) return false;
+    } else {
+        s = d[0] * d[0] + d[1] * d[1];
+        if (B.shape == 1) s += d[2] * d[2];
+        R2 = (float)(B.R * B.R);
+        const float band = 1e-4f * R2 + 0.05f;
+        if (s < R2 - band) return true;
+        if (s > R2 + band) return false;
+    }
     double r[3];
     disp(p, f.Xw, x, y, z, r);
-    return inside(B, r);
+    return inside(B, r, f.co, f.si);
 }
+
+// radial band of the surface: inner and outer radius (the semi-axes of an ellipse)
+__device__ __forceinline__ float body_rin(const BodyDev &B) { return (float)(B.shape == 2 ? B.R2 : B.R); }
+__device__ __forceinline__ float body_rout(const BodyDev &B) { return (float)B.R; }
 
 __device__ __forceinline__ int wrap_axis(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -349,15 +464,16 @@ __device__ __forceinline__ int region_axis(int k, int lo, int len, int n, int pe
     return s0 + k;
 }
 
-// per body and step: X(t), Xw(t), X(t+1), Xw(t+1) (Xw wrapped into [0, L)),
-// floor(Xw(t)) and Xw(t) - floor(Xw(t))
-constexpr int POSE_STRIDE = 18;
+// per body and step: X(t) [0], Xw(t) [3], X(t+1) [6], Xw(t+1) [9] (Xw
+// wrapped into [0, L)), floor(Xw(t)) [12] and Xw(t) - floor(Xw(t)) [15],
+// cos, sin of the orientation at t [18] and at t+1 [24] (15 after Xw)
+constexpr int POSE_STRIDE = 26;
 
 // region of a body covering its poses at t and t+1, dilated by `margin`
 __device__ __forceinline__ void region_lo(const Params &p, const BodyDev &b, const double *P, int margin, int lo[3]) {
     for (int a = 0; a < 3; ++a) {
         int n = axis_len(p, a);
-        bool full = (a == 2 && b.shape == 0) || b.ext[a] >= n;
+        bool full = (a == 2 && along_z(b.shape)) || b.ext[a] >= n;
         if (full) {
             lo[a] = 0;
             continue;

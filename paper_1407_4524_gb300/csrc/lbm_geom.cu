@@ -146,6 +146,13 @@ __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, 
         wrap_pose(p, P, P + 3);
         pose(bodies[b], t + 1, P + 6);
         wrap_pose(p, P + 6, P + 9);
+        if (bodies[b].shape == 2) {
+            sincos_cw(orient(bodies[b], t), P[19], P[18]);
+            sincos_cw(orient(bodies[b], t + 1), P[25], P[24]);
+        } else {
+            P[18] = P[24] = 1.0;
+            P[19] = P[25] = 0.0;
+        }
         for (int a = 0; a < 3; ++a) {
             P[12 + a] = floor(P[3 + a]);
             P[15 + a] = P[3 + a] - P[12 + a];
@@ -182,13 +189,13 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_a(Params p, GeomArgs g) {
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     const uint16_t me = (uint16_t)(b + 1);
-    const float R = (float)B.R;
+    const float Rin = body_rin(B), Rout = body_rout(B);
     int flags = 0;
     for (int j = 0; j < GEOM_CELLS; ++j) {
         RegionCell rc = region_cell(p, B, lo, cm.y, j);
         if (!rc.valid) continue;
         const float dist = frame_dist(p, B, F, rc);
-        if (dist < R - 2.0f || dist > R + 2.0f) continue;
+        if (dist < Rin - 2.0f || dist > Rout + 2.0f) continue;
         const bool in_t = g.owner_t[rc.cell] == me;
         const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
         if (in1) g.owner_t1[rc.cell] = me;
@@ -216,14 +223,14 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     const int first = blockIdx.x - cm.y; // first chunk of this body
-    const float R = (float)B.R;
+    const float Rin = body_rin(B), Rout = body_rout(B);
     unsigned apm_mask = 0, apm_sign = 0;
     int nl = 0;
     for (int j = 0; j < GEOM_CELLS; ++j) {
         RegionCell rc = region_cell(p, B, lo, cm.y, j);
         if (!rc.valid) continue;
         const float dist = frame_dist(p, B, F, rc);
-        if (g.do_apm && dist >= R - 2.0f && dist <= R + 2.0f) {
+        if (g.do_apm && dist >= Rin - 2.0f && dist <= Rout + 2.0f) {
             const bool in_t = g.owner_t[rc.cell] == me, in1 = g.owner_t1[rc.cell] == me;
             if (in_t != in1) {
                 apm_mask |= 1u << j;
@@ -231,9 +238,9 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
             }
         }
         // node flags (FP64 mode: the moment-store flag follows the geometry of t+1)
-        if (g.do_flags && dist >= R - 2.0f && dist <= R + 5.5f)
+        if (g.do_flags && dist >= Rin - 2.0f && dist <= Rout + 5.5f)
             g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
-        if (dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
+        if (dist >= Rin - 0.5f && dist <= Rout + 2.0f && owner_L[rc.cell] == 0) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     const int first = blockIdx.x - cm.y;
-    const float R = (float)B.R;
+    const float Rin = body_rin(B), Rout = body_rout(B);
     unsigned mask[GEOM_CELLS];
     int nl = 0;
 #pragma unroll
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
         RegionCell rc = region_cell(p, B, lo, cm.y, j);
         if (!rc.valid) continue;
         const float dist = frame_dist(p, B, F, rc);
-        if (dist >= R - 0.5f && dist <= R + 2.0f && owner_L[rc.cell] == 0) {
+        if (dist >= Rin - 0.5f && dist <= Rout + 2.0f && owner_L[rc.cell] == 0) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
                 const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
@@ -315,8 +322,9 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_c(Params p, GeomArgs g) {
                 const long long jj = B.link_off + at;
                 g.Lcell[jj] = (uint32_t)rc.cell;
                 g.Ldir[jj] = (uint8_t)i;
-                g.Ldelta[jj] = p.exact ? link_delta(B, d, L::cx(i), L::cy(i), L::cz(i))
-                                       : (double)link_delta_f(B.halfway, B.shape, (float)B.R, df, L::cx(i), L::cy(i), L::cz(i));
+                g.Ldelta[jj] = p.exact ? link_delta(B, d, L::cx(i), L::cy(i), L::cz(i), F.co, F.si)
+                                       : (double)link_delta_f(B.halfway, B.shape, (float)B.R, (float)B.R2, F.cof,
+                                                              F.sif, df, L::cx(i), L::cy(i), L::cz(i));
             }
             at++;
         }
@@ -383,6 +391,13 @@ __global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies,
         wrap_pose(p, P, P + 3);
         pose(bodies[b], t + 1, P + 6);
         wrap_pose(p, P + 6, P + 9);
+        if (bodies[b].shape == 2) {
+            sincos_cw(orient(bodies[b], t), P[19], P[18]);
+            sincos_cw(orient(bodies[b], t + 1), P[25], P[24]);
+        } else {
+            P[18] = P[24] = 1.0;
+            P[19] = P[25] = 0.0;
+        }
         for (int a = 0; a < 3; ++a) {
             P[12 + a] = floor(P[3 + a]);
             P[15 + a] = P[3 + a] - P[12 + a];
@@ -404,12 +419,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom1(Params p, GeomArgs g) {
         int lo[3];
         region_lo(p, B, P, REGION_MARGIN, lo);
         const uint16_t me = (uint16_t)(b + 1);
-        const float R = (float)B.R;
+        const float Rin = body_rin(B), Rout = body_rout(B);
         for (int j = 0; j < GEOM_CELLS; ++j) {
             RegionCell rc = region_cell(p, B, lo, cm.y, j);
             if (!rc.valid) continue;
             const float dist = frame_dist(p, B, F, rc);
-            if (dist < R - 2.0f || dist > R + 2.0f) continue;
+            if (dist < Rin - 2.0f || dist > Rout + 2.0f) continue;
             const bool in_t = g.owner_t[rc.cell] == me;
             const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
             if (in1) g.owner_t1[rc.cell] = me;
@@ -439,12 +454,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
         __syncthreads();
         int lo[3];
         region_lo(p, B, P, REGION_MARGIN, lo);
-        const float R = (float)B.R;
+        const float Rin = body_rin(B), Rout = body_rout(B);
         for (int j = 0; j < GEOM_CELLS; ++j) {
             RegionCell rc = region_cell(p, B, lo, cm.y, j);
             if (!rc.valid) continue;
             const float dist = frame_dist(p, B, F, rc);
-            if (dist < R - 2.0f || dist > R + 3.0f) continue;
+            if (dist < Rin - 2.0f || dist > Rout + 3.0f) continue;
             uint8_t nf;
             if (g.owner_t1[rc.cell]) {
                 nf = FL_SOLID;
@@ -460,7 +475,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
                 }
                 nf = one ? FL_BND : 0;
                 // boundary node of t+1 next to a moving body: listed by the lowest one
-                if (minmov == b + 1 && dist <= R + 1.5f) {
+                if (minmov == b + 1 && dist <= Rout + 1.5f) {
                     const unsigned long long at = atomicAdd(g.bn_mov_cnt, 1ull);
                     if ((long long)at < g.bn_mov_cap) g.bn_mov[at] = (uint32_t)rc.cell;
                 }
@@ -490,12 +505,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_bnd_lists(Params p, GeomArgs g
     __syncthreads();
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
-    const float R = (float)B.R;
+    const float Rin = body_rin(B), Rout = body_rout(B);
     for (int j = 0; j < GEOM_CELLS; ++j) {
         RegionCell rc = region_cell(p, B, lo, cm.y, j);
         if (!rc.valid) continue;
         const float dist = frame_dist(p, B, F, rc);
-        if (dist < R - 0.5f || dist > R + 1.5f || g.owner_t[rc.cell] != 0) continue;
+        if (dist < Rin - 0.5f || dist > Rout + 1.5f || g.owner_t[rc.cell] != 0) continue;
         int minall = 1 << 20, minmov = 1 << 20;
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
@@ -615,8 +630,9 @@ static cudaError_t import_t(int prec, const Params &p, const double *in, void *p
 // were built from --, then forward Euler gives U(t+1) and W(t+1) from the
 // lattice-frame force and torque (Eqs. ForceInMovement, TorqueInMovement:
 // static plus impulsive terms), weight less buoyancy (rho_b - rho0) V g and
-// M = rho_b V, I = M R^2/2 (cylinder, about z) or 2/5 M R^2 (sphere).  The
-// body record keeps X0 = X(t+1), t0 = t+1, so pose(t+1), pose(t+2) follow.
+// M = rho_b V, I = M R^2/2 (cylinder, about z), M (R^2 + R2^2)/4 (ellipse,
+// V = pi R R2 nz) or 2/5 M R^2 (sphere).  The body record keeps X0 = X(t+1),
+// theta0 = theta(t+1), t0 = t+1, so pose(t+1), pose(t+2) follow.
 // A body within 2 cells of a non-periodic face, or faster than 0.25 at its
 // surface, sets counters[7].
 __global__ void k_free(Params p, BodyDev *bodies, const double *series, long long t, unsigned long long *counters) {
@@ -626,12 +642,19 @@ __global__ void k_free(Params p, BodyDev *bodies, const double *series, long lon
     if (!B.free) return;
     const double *Rw = series + ((t % p.series_cap) * p.nb + b) * SERIES_ROW;
     const double PI = 3.14159265358979323846;
-    const double V = B.shape == 1 ? 4.0 / 3.0 * PI * B.R * B.R * B.R : PI * B.R * B.R * (double)p.nz;
+    double V, I;
+    if (B.shape == 1) V = 4.0 / 3.0 * PI * B.R * B.R * B.R;
+    else if (B.shape == 2) V = PI * B.R * B.R2 * (double)p.nz;
+    else V = PI * B.R * B.R * (double)p.nz;
     const double M = B.density_ratio * p.rho0 * V;
-    const double I = B.shape == 1 ? 0.4 * M * B.R * B.R : 0.5 * M * B.R * B.R;
+    if (B.shape == 1) I = 0.4 * M * B.R * B.R;
+    else if (B.shape == 2) I = 0.25 * M * (B.R * B.R + B.R2 * B.R2);
+    else I = 0.5 * M * B.R * B.R;
     double X1[3];
     pose(B, t + 1, X1);
+    const double th1 = orient(B, t + 1);
     for (int a = 0; a < 3; ++a) B.X0[a] = X1[a];
+    B.theta0 = th1;
     B.t0 = t + 1;
     for (int a = 0; a < 3; ++a) {
         const double F = Rw[a] + Rw[6 + a];
@@ -644,7 +667,7 @@ __global__ void k_free(Params p, BodyDev *bodies, const double *series, long lon
     }
     bool bad = false;
     for (int a = 0; a < 3; ++a) {
-        if (p.per[a] || (a == 2 && B.shape == 0)) continue;
+        if (p.per[a] || (a == 2 && along_z(B.shape))) continue;
         const double n = (double)axis_len(p, a);
         if (X1[a] - B.R < 2.0 || X1[a] + B.R > n - 3.0) bad = true;
     }

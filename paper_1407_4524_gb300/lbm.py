@@ -23,7 +23,7 @@ ERRORS = {1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_UNS
           5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
 EDGE = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
-SHAPE = {"cylinder": 0, "sphere": 1}
+SHAPE = {"cylinder": 0, "sphere": 1, "ellipse": 2}
 FT_KIND = {"static": 0, "lattice": 1, "moving": 2, "impulsive": 3}
 SERIES_ROW = 18
 
@@ -47,7 +47,7 @@ class lbm_body(C.Structure):
     _fields_ = [
         ("shape", C.c_int), ("halfway", C.c_int), ("free_body", C.c_int), ("reserved", C.c_int),
         ("R", C.c_double), ("X0", C.c_double * 3), ("U", C.c_double * 3), ("W", C.c_double * 3),
-        ("t0", C.c_int64), ("density_ratio", C.c_double),
+        ("t0", C.c_int64), ("density_ratio", C.c_double), ("R2", C.c_double), ("theta0", C.c_double),
     ]
 
 
@@ -154,6 +154,8 @@ def body_struct(b: dict) -> lbm_body:
     s.t0 = int(b.get("t0", 0))
     s.free_body = int(bool(b.get("free", False)))
     s.density_ratio = float(b.get("density_ratio", 1.0))
+    s.R2 = float(b.get("R2", b["R"]))
+    s.theta0 = float(b.get("theta0", 0.0))
     return s
 
 

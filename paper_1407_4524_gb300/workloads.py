@@ -18,8 +18,10 @@ units per step):
   force      body-force density (gx, gy[, gz]) or absent
   u0         initial uniform velocity
   refill     "uB" (f^eq(rho_bar, u_B)) | "ubar" (f^eq(rho_bar, u_bar))
-  bodies     list of {"shape": "cylinder" | "sphere", "R", "X0", "U", "W",
-             "halfway", "t0"}
+  bodies     list of {"shape": "cylinder" | "sphere" | "ellipse", "R", "X0", "U",
+             "W", "halfway", "t0"; free bodies: "free", "density_ratio";
+             ellipses: "R2" (second semi-axis), "theta0"}
+  gravity    acceleration of the free bodies (lattice units)
   precision  "fp64" | "fp32" | "fp16"  (CUDA side only)
 """
 from __future__ import annotations
@@ -93,6 +95,26 @@ def sedimenting_disc_2d(precision: str = "fp64", density_ratio: float = 1.01, st
         name="sedimenting_disc_2d", lattice="D2Q9", n=(nx, ny), tau=tau,
         edges={"x": ("wall", "wall"), "y": ("wall", "wall")}, gravity=(0.0, -g_l),
         bodies=[dict(shape="cylinder", R=R, X0=(x0, y0), free=True, density_ratio=float(density_ratio))],
+        precision=precision, steps=steps,
+    )
+
+
+def sedimenting_ellipse_2d(precision: str = "fp64", density_ratio: float = 1.10, steps: int = 20000) -> dict:
+    """The paper's sedimenting ellipse in lattice units: D2Q9 135 x 1676, tau
+    0.6, walls on every face, a free ellipse with major axis a = 1 mm (the full
+    axis; semi-axes a/2 and a/4: aspect ratio 2), channel W = 4 a (blockage 4),
+    H = 50 a, released at the channel axis 48 mm above the bottom at
+    theta0 = pi/4, r_rho = 1.10; water and g as for the disc."""
+    nx, ny, tau = 135, 1676, 0.6
+    dx = 4e-3 / nx
+    nu_l = (tau - 0.5) / 3.0
+    dt = nu_l * dx * dx / 1e-6
+    g_l = 9.81 * dt * dt / dx
+    return dict(
+        name="sedimenting_ellipse_2d", lattice="D2Q9", n=(nx, ny), tau=tau,
+        edges={"x": ("wall", "wall"), "y": ("wall", "wall")}, gravity=(0.0, -g_l),
+        bodies=[dict(shape="ellipse", R=0.5e-3 / dx, R2=0.25e-3 / dx, theta0=math.pi / 4,
+                     X0=(0.5 * (nx - 1), 48e-3 / dx), free=True, density_ratio=float(density_ratio))],
         precision=precision, steps=steps,
     )
 

@@ -20,13 +20,17 @@ CASES = {
     "disc_channel": dict(  # walls on x: the disc drifts across the channel while it falls
         lattice="D2Q9", n=(46, 60), tau=0.65, gravity=(0.0, -2e-4), edges={"x": ("wall", "wall")},
         bodies=[dict(shape="cylinder", R=6.5, X0=(28.3, 30.2), U=(-0.01, 0.0), free=True, density_ratio=1.2)]),
+    "ellipse_channel": dict(  # a free ellipse released at 45 degrees: it falls, drifts and turns
+        lattice="D2Q9", n=(50, 70), tau=0.7, gravity=(0.0, -2e-4), edges={"x": ("wall", "wall")},
+        bodies=[dict(shape="ellipse", R=9.4, R2=4.7, theta0=0.785398, X0=(25.3, 35.2), free=True,
+                     density_ratio=1.5)]),
     "spheres_periodic": dict(
         lattice="D3Q19", n=(34, 32, 30), tau=0.8, gravity=(0.0, -5e-5, 2e-5),
         bodies=[dict(shape="sphere", R=5.1, X0=(9.6, 10.2, 14.1), U=(0.01, 0.0, -0.005), W=(0.0, 0.002, 0.0),
                      free=True, density_ratio=2.0),
                 dict(shape="sphere", R=4.2, X0=(24.3, 22.7, 13.6), free=True, density_ratio=0.8)]),
 }
-STEPS = {"disc_periodic": 150, "disc_channel": 150, "spheres_periodic": 60}
+STEPS = {"disc_periodic": 150, "disc_channel": 150, "ellipse_channel": 150, "spheres_periodic": 60}
 
 
 def _run(oracle_mod, spec, steps):

@@ -153,6 +153,32 @@ def test_sphere_swarm_full_size_sampled(oracle_mod):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sedimenting_ellipse_full_size(oracle_mod, prec):
+    """The paper's sedimenting ellipse (D2Q9 135x1676, free ellipse at 45
+    degrees, r_rho = 1.10) over 300 steps: FP64 bit-identical, FP32 within
+    tolerance."""
+    from paper_1407_4524_gb300 import lbm, workloads as W
+    spec = W.sedimenting_ellipse_2d(prec)
+    steps = 300
+    dom = lbm.Domain(spec, device=0)
+    dom.step(steps)
+    ref = oracle_mod.Oracle(spec)
+    ref.step(steps)
+    st, st_ref = dom.body_state(), ref.body_state()
+    assert st_ref[0, 4] < 0 and st_ref[0, 8] != 0.0  # falls and turns
+    if prec == "fp64":
+        assert np.array_equal(dom.series(), ref.series())
+        assert np.array_equal(st, st_ref)
+        err = 0.0
+    else:
+        err = ft_rel_error(dom.force_torque("lattice"), ref.force_torque("lattice"), spec)
+        assert err <= TOL_RED_FT
+        assert np.abs(st[:, :3] - st_ref[:, :3]).max() <= 1e-6
+    _report(f"sedimenting_ellipse_2d_{prec}_{steps}", {"lattice_ft_rel": err, "uy_final": float(st_ref[0, 4]),
+                                                        "w_final": float(st_ref[0, 8])})
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sedimenting_disc_full_size(oracle_mod, prec):
     """The paper's sedimenting disc (D2Q9 135x1073, walls, free disc,
     r_rho = 1.01) over 400 steps: FP64 bit-identical series and trajectory;

@@ -53,6 +53,13 @@ CASES_2D = {
     "long_rows_periodic": dict(  # rows of several staging segments, the last one partial
         lattice="D2Q9", n=(328, 24), tau=0.65, u0=(0.03, -0.01),
         bodies=[dict(shape="cylinder", R=4.5, X0=(300.3, 11.2), U=(0.03, 0.0))]),
+    "ellipse_channel": dict(  # static ellipse at 45 degrees: Delta in the rotated, scaled axes
+        lattice="D2Q9", n=(64, 34), tau=0.7, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+        inlet={"profile": "parabolic", "u": 0.05},
+        bodies=[dict(shape="ellipse", R=9.3, R2=4.4, theta0=0.785398, X0=(20.6, 16.8))]),
+    "ellipse_rotating": dict(  # rotation alone covers and uncovers nodes
+        lattice="D2Q9", n=(48, 46), tau=0.65, u0=(0.02, 0.0),
+        bodies=[dict(shape="ellipse", R=9.1, R2=3.7, theta0=0.3, X0=(23.2, 22.6), W=0.006, U=(0.01, 0.0))]),
     "moving_cylinders_periodic": dict(
         lattice="D2Q9", n=(97, 66), tau=0.6,
         bodies=[dict(shape="cylinder", R=8.2, X0=(6.3, 20.4), U=(0.06, -0.03)),  # crosses the seam
@@ -92,6 +99,9 @@ CASES_3D = {
     "walled_channel_sphere": dict(  # 16-byte rows, walls on y, inlet / outlet on x
         lattice="D3Q19", n=(48, 20, 18), tau=0.62, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
         inlet={"u": 0.03}, u0=(0.03, 0.0, 0.0), bodies=[dict(shape="sphere", R=4.6, X0=(14.2, 9.7, 8.9))]),
+    "ellipse_3d_rotating": dict(  # elliptic cylinder along z in D3Q19, rotating about z
+        lattice="D3Q19", n=(36, 34, 8), tau=0.7, u0=(0.02, 0.01, 0.0),
+        bodies=[dict(shape="ellipse", R=8.2, R2=4.6, theta0=1.1, X0=(17.4, 16.9, 0.0), W=(0.0, 0.0, 0.005))]),
     "walled_box_cylinder3d": dict(
         lattice="D3Q19", n=(30, 28, 9), tau=0.7, u0=(0.02, 0.01, 0.0),
         edges={"x": ("wall", "wall"), "y": ("wall", "wall"), "z": "periodic"},
