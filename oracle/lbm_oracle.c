@@ -29,10 +29,10 @@
  *
  * Floating point: everything is FP64, loops run in cell order
  * ((z*ny + y)*nx + x) and direction order, and every formula is written as a
- * single fixed expression (compile with -ffp-contract=off).  The readings of
- * the paper that this file takes (sign of the moving-wall term, equilibrium of
- * the quasi-incompressible model, time levels, refill rule, edge treatment)
- * are listed in the design doc.
+ * single fixed expression (compile with -ffp-contract=off).  Where the paper
+ * leaves a choice open (sign of the moving-wall term, equilibrium of the
+ * quasi-incompressible model, time levels, refill rules, edge treatment) the
+ * comment at the function states the reading taken.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
  * against closed forms, conservation laws, symmetry and exact special cases.
@@ -67,7 +67,7 @@ typedef struct {
     int edge[6];         /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi: OR_PERIODIC.. */
     int inlet_parabolic; /* 0: uniform u_in, 1: parabolic in y, maximum u_in */
     int has_force;       /* Guo body force (used only by the Poiseuille check) */
-    int refill;          /* 0: feq(rho_bar, u_B); 1: feq(rho_bar, u_bar) */
+    int refill;          /* 0: feq(rho_bar, u_B); 1: feq(rho_bar, u_bar); 2: extrapolation */
     double tau;
     double rho0;
     double u_in;
@@ -108,6 +108,7 @@ typedef struct {
     double *series; /* [nrec][nb][OR_ROW] */
     double edge_me[6];
     long long n_fallback;
+    long long n_extrap; /* uncovered nodes refilled by extrapolation */
 } or_dom;
 
 /* ---- lattice tables (standard D2Q9 / D3Q19; direction order fixed here) -- */
@@ -451,7 +452,7 @@ static void edge_velocity(const or_dom *o, int kind, int y, int i, double uB[3])
  * Curved-wall value fhat_i(x_A, t) of Eq. Fillipova_interpolation for the
  * link from solid node A = x - c_i to fluid node F = x (c_i points A -> F).
  * The moving-wall term is read as +2 w_i rho_w 3 c_i.u_B (c_i pointing into
- * the fluid; see DESIGN.md): this makes a co-moving uniform flow a fixed point.
+ * the fluid): this makes a co-moving uniform flow a fixed point.
  */
 static double wall_value(const or_dom *o, long x, int xx, int yy, int zz, int i, double delta,
                          const double uB[3], long long *fallback)
@@ -656,6 +657,68 @@ static int record_row(or_dom *o, const double *row)
     return OR_OK;
 }
 
+/*
+ * Extrapolation refill (refill rule 2, after the extrapolation of the cited
+ * Lallemand-Luo proposal, Sec. 3, discussion after Eq. ForceInMovement): the
+ * node A = (x, y, z) uncovered between t and t+1 takes, per direction i,
+ *     f_i(A, t+1) = 3 fhat_i(A + c*, t) - 3 fhat_i(A + 2c*, t) + fhat_i(A + 3c*, t),
+ * the quadratic extrapolation along the lattice direction c* closest to the
+ * outward surface normal n at A (largest n.c / |c|, the first such direction in
+ * direction order).  n is the gradient of the body's shape function at the
+ * pose of t+1: r (sphere), (r_x, r_y, 0) (cylinder), and for the ellipse the
+ * gradient (xi / R^2, eta / R2^2) of its body-axes form turned back into the
+ * lattice axes.  The three nodes must lie in the lattice (periodic axes wrap)
+ * and be fluid at t; otherwise the function returns 0 and the equilibrium rule
+ * applies.  Returns the direction index of c* and the three cells.
+ */
+static int extrap_nodes(const or_dom *o, const or_body *b, long long t, int x, int y, int z, long nodes[3])
+{
+    const double INV_SQRT2 = 0.70710678118654752440;
+    double X1[3], r1[3], n[3];
+    pose(b, t + 1, X1);
+    disp(o, X1, x, y, z, r1);
+    if (b->shape == OR_SHAPE_ELLIPSE) {
+        double so, co, xi, eta;
+        sincos_cw(orient(b, t + 1), &so, &co);
+        body_axes(co, so, r1, &xi, &eta);
+        double gx = xi / (b->R * b->R), gy = eta / (b->R2 * b->R2);
+        n[0] = co * gx - so * gy;
+        n[1] = so * gx + co * gy;
+        n[2] = 0.0;
+    } else {
+        n[0] = r1[0];
+        n[1] = r1[1];
+        n[2] = b->shape == OR_SHAPE_SPHERE ? r1[2] : 0.0;
+    }
+    if (b->invert)
+        for (int a = 0; a < 3; ++a) n[a] = -n[a];
+    int best = 0;
+    double top = 0.0;
+    for (int i = 1; i < o->Q; ++i) {
+        const int *c = o->c[i];
+        double s = ((double)c[0] * n[0] + (double)c[1] * n[1]) + (double)c[2] * n[2];
+        int len2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        double score = len2 == 1 ? s : s * INV_SQRT2;
+        if (best == 0 || score > top) {
+            best = i;
+            top = score;
+        }
+    }
+    for (int k = 1; k <= 3; ++k) {
+        int p[3];
+        for (int a = 0; a < 3; ++a) {
+            p[a] = (a == 0 ? x : a == 1 ? y : z) + k * o->c[best][a];
+            if (p[a] >= 0 && p[a] < o->n[a]) continue;
+            if (!periodic(o, a)) return 0;
+            p[a] = ((p[a] % o->n[a]) + o->n[a]) % o->n[a];
+        }
+        long q = cell(o, p[0], p[1], p[2]);
+        if (o->solid[q] >= 0) return 0;
+        nodes[k - 1] = q;
+    }
+    return best;
+}
+
 static int one_step(or_dom *o)
 {
     const long N = o->N;
@@ -811,7 +874,16 @@ static int one_step(or_dom *o)
                         double ufill[3];
                         for (int a = 0; a < 3; ++a)
                             ufill[a] = (o->d.refill == 1 && cnt) ? us[a] / (double)cnt : uB[a];
-                        for (int i = 0; i < Q; ++i) o->fnew[(long)i * N + A] = feq(o, i, rbar, ufill);
+                        long en[3];
+                        if (o->d.refill == 2 && extrap_nodes(o, b, t, x, y, z, en)) {
+                            for (int i = 0; i < Q; ++i) {
+                                const double *fh = o->fhat + (long)i * N;
+                                o->fnew[(long)i * N + A] = (3.0 * fh[en[0]] - 3.0 * fh[en[1]]) + fh[en[2]];
+                            }
+                            o->n_extrap++;
+                        } else {
+                            for (int i = 0; i < Q; ++i) o->fnew[(long)i * N + A] = feq(o, i, rbar, ufill);
+                        }
                     }
                     /* impulsive terms of Eqs. ForceInMovement / TorqueInMovement */
                     double m[3] = {0.0, 0.0, 0.0};
@@ -906,6 +978,7 @@ int or_step(or_dom *o, int n)
 
 long long or_time(const or_dom *o) { return o ? o->t : -1; }
 long long or_fallbacks(const or_dom *o) { return o ? o->n_fallback : -1; }
+long long or_extrapolated(const or_dom *o) { return o ? o->n_extrap : -1; }
 
 /* series rows [first, first+count) of every body: out[count][nb][18] with
  * Fs Ts (static form), Fi Ti (impulsive terms), Fm Tm (moving frame) */

@@ -76,6 +76,8 @@ def _load():
     lib.or_time.argtypes = [P]
     lib.or_fallbacks.restype = C.c_longlong
     lib.or_fallbacks.argtypes = [P]
+    lib.or_extrapolated.restype = C.c_longlong
+    lib.or_extrapolated.argtypes = [P]
     lib.or_get_series.argtypes = [P, C.c_longlong, C.c_longlong, P]
     for name in ("or_get_f", "or_get_fhat", "or_get_macro", "or_get_solid", "or_get_edge_me", "or_get_bodies"):
         getattr(lib, name).argtypes = [P, P]
@@ -146,7 +148,7 @@ class Oracle:
     Optional: ``rho0``, ``eq`` ("incomp"/"standard"), ``edges`` (per axis
     "periodic" | (lo, hi) kinds among "wall", "inlet", "outlet"), ``inlet``
     ({"profile": "uniform"/"parabolic", "u": ...}), ``force``, ``u0``,
-    ``refill`` ("uB"/"ubar"), ``gravity`` (acceleration of free bodies),
+    ``refill`` ("uB"/"ubar"/"extrap"), ``gravity`` (acceleration of free bodies),
     ``bodies`` (list of dicts: shape, R, X0, U, W, halfway, invert, t0, free,
     density_ratio; ellipses: shape "ellipse", R and R2 the semi-axes, theta0).
     """
@@ -171,7 +173,7 @@ class Oracle:
         u0 = tuple(spec.get("u0", (0.0, 0.0, 0.0)))
         for k in range(3):
             d.u0[k] = float(u0[k]) if k < len(u0) else 0.0
-        d.refill = {"uB": 0, "ubar": 1}[spec.get("refill", "uB")]
+        d.refill = {"uB": 0, "ubar": 1, "extrap": 2}[spec.get("refill", "uB")]
         gv = tuple(spec.get("gravity", (0.0, 0.0, 0.0)))
         for k in range(3):
             d.gravity[k] = float(gv[k]) if k < len(gv) else 0.0
@@ -209,6 +211,10 @@ class Oracle:
     @property
     def fallbacks(self) -> int:
         return int(self.lib.or_fallbacks(self.h))
+
+    def extrapolated(self) -> int:
+        """Uncovered nodes refilled by extrapolation so far (refill "extrap")."""
+        return int(self.lib.or_extrapolated(self.h))
 
     # -- state ----------------------------------------------------------------
     def _grid(self, arr, lead):

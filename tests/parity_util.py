@@ -1,7 +1,7 @@
 """Helpers shared by the GPU parity tests (comparison metrics only)."""
 import numpy as np
 
-# tolerances (BASELINE the benchmark spec): FP64 mode 1e-12 relative on force and
+# tolerances of the method's precision modes: FP64 mode 1e-12 relative on force and
 # torque; reduced precision 1e-5 absolute on populations (rho ~ 1) and 1e-4
 # relative on force and torque after N steps.
 TOL_FP64_FT = 1e-12
