@@ -82,10 +82,17 @@ extern "C" {
 #define LBM_INLET_PARABOLIC 1 /* u_x(y) = 4 u_in (y+1/2)(ny-1/2-y)/ny^2 */
 
 /* Refill of nodes uncovered by a moving body (Sec. 3, after Eq.
- * ForceInMovement): equilibrium at the mean density of the fluid neighbours
- * with the body velocity at the node (default) or the neighbour-mean velocity. */
+ * ForceInMovement, which lists three rules): equilibrium at the mean density
+ * of the fluid neighbours with the body velocity at the node (default) or the
+ * neighbour-mean velocity; or the quadratic extrapolation
+ * f_i(A) = 3 fhat_i(A+c*) - 3 fhat_i(A+2c*) + fhat_i(A+3c*) of the
+ * post-collision values at t along the lattice direction c* closest to the
+ * body's outward normal at A (largest n.c/|c|), falling back to the default
+ * rule where one of the three nodes is solid at t or outside a non-periodic
+ * face. */
 #define LBM_REFILL_RHOBAR_UB 0
 #define LBM_REFILL_RHOBAR_UBAR 1
+#define LBM_REFILL_EXTRAP 2
 
 #define LBM_SHAPE_CYLINDER 0 /* disc in the x-y plane (infinite along z in 3-D) */
 #define LBM_SHAPE_SPHERE 1
@@ -174,6 +181,8 @@ typedef struct lbm_stats {
     int64_t unstable;        /* non-zero: a NaN or |u| > 0.3 was seen at a boundary
                                 node, or a force was not finite (LBM_ERR_UNSTABLE);
                                 domains without bodies are not checked */
+    int64_t extrapolated;    /* A- nodes refilled by extrapolation (LBM_REFILL_EXTRAP),
+                                summed over steps */
 } lbm_stats;
 
 typedef struct lbm_domain lbm_domain;

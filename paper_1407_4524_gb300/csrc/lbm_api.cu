@@ -584,7 +584,8 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
         if (d.edge[e] == LBM_EDGE_OUTLET && e != 1) return fail(LBM_ERR_ARG, "the outlet must be the x-high face");
     }
     if (d.lattice == LBM_D2Q9 && d.edge[4] != LBM_EDGE_PERIODIC) return fail(LBM_ERR_ARG, "D2Q9: z must be periodic");
-    if (d.refill != LBM_REFILL_RHOBAR_UB && d.refill != LBM_REFILL_RHOBAR_UBAR) return fail(LBM_ERR_ARG, "unknown refill rule");
+    if (d.refill != LBM_REFILL_RHOBAR_UB && d.refill != LBM_REFILL_RHOBAR_UBAR && d.refill != LBM_REFILL_EXTRAP)
+        return fail(LBM_ERR_ARG, "unknown refill rule");
     if (d.inlet_profile != LBM_INLET_UNIFORM && d.inlet_profile != LBM_INLET_PARABOLIC)
         return fail(LBM_ERR_ARG, "unknown inlet profile");
     if ((d.alloc == nullptr) != (d.free == nullptr)) return fail(LBM_ERR_ARG, "alloc and free go together");
@@ -664,7 +665,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
         if ((rc = alloc_t(D, &D->owner[k], N, nullptr))) return bail(rc);
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
-    if ((rc = alloc_t(D, &D->counters, 8, nullptr))) return bail(rc);
+    if ((rc = alloc_t(D, &D->counters, N_COUNTERS, nullptr))) return bail(rc);
     {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
@@ -976,7 +977,7 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
     std::memset(out, 0, sizeof(*out));
     CK(cudaStreamSynchronize(D->s));
-    unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[N_COUNTERS] = {};
     CK(cudaMemcpy(c, D->counters, sizeof(c), cudaMemcpyDeviceToHost));
     out->step = D->t;
     out->cells = D->p.N;
@@ -986,6 +987,7 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     out->device_bytes = (int64_t)D->bytes;
     out->timeouts = (int64_t)c[6];
     out->unstable = (int64_t)c[5];
+    out->extrapolated = (int64_t)c[8];
     out->h2d_bytes = D->h2d;
     out->d2h_bytes = D->d2h;
     if (D->nb && D->prec != LBM_FP64 && D->t > 0) {
@@ -1134,7 +1136,7 @@ int domain_bytes(const lbm_domain_desc &d, const lbm_body *hb, int n, int64_t *b
     const long long cap = d.series_capacity > 0 ? d.series_capacity : 8192;
     long long b = 0;
     b += 2 * (N * T.Q * S + (d.precision == LBM_FP64 ? N * 4 * C : 256) + N * 2); // pop, mac, owner
-    b += N + 8 * 8;                                                               // flags, counters
+    b += N + 8 * N_COUNTERS;                                                      // flags, counters
     const long long nbx = std::max(n, 1);
     long long loff = 0, aoff = 0, chunks = 0, bns = 0;
     for (int k = 0; k < n; ++k) {

@@ -39,6 +39,7 @@ constexpr int BULK_THREADS = 128;
 constexpr int BULK_MIN_BLOCKS = 8; // reduced precision: <= 64 registers, half the warps resident
 constexpr int LINK_THREADS = 256;
 constexpr int IMP_THREADS = 128;
+constexpr int N_COUNTERS = 16; // entries of the device counter array (StepBufs::counters)
 
 struct StepBufs {
     const void *src; // fhat(t)   (k_links also writes wall values into it)
@@ -65,7 +66,8 @@ struct StepBufs {
     double *series;
     unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered,
                                   // [3] links of this step, [4] links of the last step,
-                                  // [5] unstable flag, [6] timeout flag
+                                  // [5] unstable flag, [6] timeout flag,
+                                  // [7] free body out of range, [8] extrapolation refills
     unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
 };
@@ -834,6 +836,64 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
 
 // covered (sign +1) and uncovered (sign -1) nodes of one moving body:
 // impulsive terms and refill (one CTA per moving body)
+// Extrapolation refill (LBM_REFILL_EXTRAP; the extrapolation proposal the
+// paper cites in Sec. 3, after Eq. ForceInMovement): the uncovered node A
+// takes f_i(A, t+1) = 3 fhat_i(A + c*, t) - 3 fhat_i(A + 2c*, t) + fhat_i(A + 3c*, t)
+// along the lattice direction c* closest to the outward normal n of the body
+// at t+1 through A (largest n.c / |c|, the first in direction order): n is the
+// gradient of the shape function (r for a sphere, (r_x, r_y, 0) for a
+// cylinder, the body-axes gradient (xi / R^2, eta / R2^2) turned back for an
+// ellipse).  The three cells must lie in the lattice (periodic axes wrap) and
+// be fluid at t; returns 0 when they do not (the equilibrium rule then
+// applies), else the index of c* with the three cells.
+template <class L>
+__device__ __forceinline__ int extrap_cells(const Params &p, const BodyDev &B, const double *X1, const uint16_t *owner_t,
+                                            int x, int y, int z, long long cells[3]) {
+    double r1[3], n[3];
+    disp(p, X1, x, y, z, r1);
+    if (B.shape == 2) {
+        const double co = X1[15], si = X1[16]; // orientation at t+1
+        double xi, eta;
+        body_axes(co, si, r1[0], r1[1], xi, eta);
+        const double gx = xi / (B.R * B.R), gy = eta / (B.R2 * B.R2);
+        n[0] = co * gx - si * gy;
+        n[1] = si * gx + co * gy;
+        n[2] = 0.0;
+    } else {
+        n[0] = r1[0];
+        n[1] = r1[1];
+        n[2] = B.shape == 1 ? r1[2] : 0.0;
+    }
+    int best = 0;
+    double top = 0.0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const double sdot = ((double)L::cx(i) * n[0] + (double)L::cy(i) * n[1]) + (double)L::cz(i) * n[2];
+        const int len2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+        const double score = len2 == 1 ? sdot : sdot * 0.70710678118654752440;
+        if (best == 0 || score > top) {
+            best = i;
+            top = score;
+        }
+    }
+    const int c[3] = {L::cx(best), L::cy(best), L::cz(best)};
+    const int nn[3] = {p.nx, p.ny, p.nz};
+    const int o[3] = {x, y, z};
+    for (int k = 1; k <= 3; ++k) {
+        int q[3];
+        for (int a = 0; a < 3; ++a) {
+            q[a] = o[a] + k * c[a];
+            if (q[a] >= 0 && q[a] < nn[a]) continue;
+            if (!p.per[a]) return 0;
+            q[a] = ((q[a] % nn[a]) + nn[a]) % nn[a];
+        }
+        const long long cq = cell_of(p, q[0], q[1], q[2]);
+        if (owner_t[cq] != 0) return 0;
+        cells[k - 1] = cq;
+    }
+    return best;
+}
+
 template <class L, class P>
 __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &sb, int b) {
     using S = typename P::S;
@@ -889,11 +949,20 @@ __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &
                     nn++;
                 }
                 C f[L::Q];
+                long long ec[3];
+                const bool ex = p.refill == 2 && extrap_cells<L>(p, B, X1, sb.owner_t, x, y, z, ec) != 0;
+                if (ex) {
+                    for (int i = 0; i < L::Q; ++i) {
+                        const S *fi = src + (long long)i * p.N;
+                        f[i] = ((C)3 * (C)ldP(fi + ec[0]) - (C)3 * (C)ldP(fi + ec[1])) + (C)ldP(fi + ec[2]);
+                    }
+                }
                 if constexpr (P::exact) {
                     double rbar = nn ? sum / (double)nn : p.rho0;
                     double uf[3];
                     for (int a = 0; a < 3; ++a) uf[a] = (p.refill == 1 && nn) ? us[a] / (double)nn : uB[a];
-                    for (int i = 0; i < L::Q; ++i) f[i] = feq_x<L>(p, i, rbar, uf);
+                    if (!ex)
+                        for (int i = 0; i < L::Q; ++i) f[i] = feq_x<L>(p, i, rbar, uf);
                     for (int i = 0; i < L::Q; ++i) {
                         m[0] += (double)L::cx(i) * f[i];
                         m[1] += (double)L::cy(i) * f[i];
@@ -911,7 +980,8 @@ __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &
                     float uf[3];
                     for (int a = 0; a < 3; ++a) uf[a] = (float)((p.refill == 1 && nn) ? us[a] / (double)nn : uB[a]);
                     const float usq15 = 1.5f * (uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
-                    for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, drb, uf, usq15);
+                    if (!ex)
+                        for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, drb, uf, usq15);
                     for (int i = 0; i < L::Q; ++i) {
                         m[0] += (double)L::cx(i) * (double)f[i];
                         m[1] += (double)L::cy(i) * (double)f[i];
@@ -924,6 +994,7 @@ __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &
                 }
                 for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + A, f[i]);
                 atomicAdd(&sb.counters[2], 1ull);
+                if (ex) atomicAdd(&sb.counters[8], 1ull);
             }
             double r[3], tq[3];
             disp(p, X, x, y, z, r);
@@ -1010,11 +1081,20 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
                 us[2] += uu[2];
                 nn++;
             }
-            const float drb = nn ? sum / (float)nn : 0.0f;
-            float uf[3];
-            for (int a = 0; a < 3; ++a) uf[a] = (p.refill == 1 && nn) ? us[a] / (float)nn : (float)uBd[a];
-            const float usq15 = 1.5f * (uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
-            for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, drb, uf, usq15);
+            long long ec[3];
+            if (p.refill == 2 && extrap_cells<L>(p, B, X1, sb.owner_t, x, y, z, ec) != 0) {
+                for (int i = 0; i < L::Q; ++i) {
+                    const S *fi = src + (long long)i * p.N;
+                    f[i] = (3.0f * ldP(fi + ec[0]) - 3.0f * ldP(fi + ec[1])) + ldP(fi + ec[2]);
+                }
+                atomicAdd(&sb.counters[8], 1ull);
+            } else {
+                const float drb = nn ? sum / (float)nn : 0.0f;
+                float uf[3];
+                for (int a = 0; a < 3; ++a) uf[a] = (p.refill == 1 && nn) ? us[a] / (float)nn : (float)uBd[a];
+                const float usq15 = 1.5f * (uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+                for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, drb, uf, usq15);
+            }
             atomicAdd(&sb.counters[2], 1ull);
         }
         for (int i = 0; i < L::Q; ++i) {

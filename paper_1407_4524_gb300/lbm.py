@@ -62,7 +62,7 @@ class lbm_batch_desc(C.Structure):
 class lbm_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("step", "cells", "fluid_cells", "links", "fallback_links",
                                           "covered", "uncovered", "device_bytes", "h2d_bytes", "d2h_bytes",
-                                          "timeouts", "unstable")]
+                                          "timeouts", "unstable", "extrapolated")]
 
 
 class LbmError(RuntimeError):
@@ -178,7 +178,7 @@ def domain_desc(spec: dict, device: int = 0, series_capacity: int = 0):
     inlet = spec.get("inlet", {})
     d.inlet_profile = 1 if inlet.get("profile", "uniform") == "parabolic" else 0
     d.u_in = float(inlet.get("u", 0.0))
-    d.refill = {"uB": 0, "ubar": 1}[spec.get("refill", "uB")]
+    d.refill = {"uB": 0, "ubar": 1, "extrap": 2}[spec.get("refill", "uB")]
     g = spec.get("force")
     d.has_force = int(g is not None)
     for j in range(3):

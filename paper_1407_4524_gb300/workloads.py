@@ -17,7 +17,8 @@ units per step):
   inlet      {"profile": "uniform" | "parabolic", "u": velocity (max if parabolic)}
   force      body-force density (gx, gy[, gz]) or absent
   u0         initial uniform velocity
-  refill     "uB" (f^eq(rho_bar, u_B)) | "ubar" (f^eq(rho_bar, u_bar))
+  refill     "uB" (f^eq(rho_bar, u_B)) | "ubar" (f^eq(rho_bar, u_bar)) | "extrap"
+             (quadratic extrapolation along the lattice direction nearest the normal)
   bodies     list of {"shape": "cylinder" | "sphere" | "ellipse", "R", "X0", "U",
              "W", "halfway", "t0"; free bodies: "free", "density_ratio";
              ellipses: "R2" (second semi-axis), "theta0"}

@@ -3,7 +3,7 @@
 Cases span several CUDA blocks and ragged tails (sizes not multiples of the
 block width), both lattices, every edge kind, static / translating /
 rotating bodies (including bodies that straddle a periodic seam), both
-equilibria, both refill rules and all three precision modes.  FP64 mode must
+equilibria, all three refill rules and all three precision modes.  FP64 mode must
 reproduce the oracle to the benchmark spec's tolerance (it is built to be
 bit-identical); FP32 / FP16 modes to the stated reduced-precision tolerance.
 """
@@ -71,6 +71,13 @@ CASES_2D = {
     "refill_ubar": dict(
         lattice="D2Q9", n=(45, 41), tau=0.9, refill="ubar", u0=(0.01, 0.02),
         bodies=[dict(shape="cylinder", R=6.6, X0=(22.2, 20.1), U=(0.07, 0.05))]),
+    "refill_extrap": dict(  # extrapolation refill; the wall and the seam force fallbacks
+        lattice="D2Q9", n=(52, 38), tau=0.8, refill="extrap", u0=(0.01, -0.02),
+        edges={"x": "periodic", "y": ("wall", "wall")},
+        bodies=[dict(shape="cylinder", R=6.1, X0=(45.3, 7.3), U=(0.08, 0.03), W=0.004)]),
+    "refill_extrap_ellipse": dict(  # normal from the rotated ellipse's gradient at t+1
+        lattice="D2Q9", n=(50, 44), tau=0.7, refill="extrap", u0=(0.02, 0.0),
+        bodies=[dict(shape="ellipse", R=8.7, R2=4.1, theta0=0.9, X0=(24.1, 21.7), W=0.008, U=(0.03, 0.02))]),
     "halfway_body": dict(
         lattice="D2Q9", n=(40, 33), tau=0.66, u0=(0.03, 0.01),
         bodies=[dict(shape="cylinder", R=5.5, X0=(19.0, 16.5), halfway=True)]),
@@ -96,6 +103,11 @@ CASES_3D = {
                 dict(shape="sphere", R=4.7, X0=(30.0, 24.5, 2.2), U=(0.05, -0.02, 0.04), W=(0.002, 0.0, -0.003)),
                 dict(shape="sphere", R=3.9, X0=(28.0, 7.0, 20.0), U=(-0.03, 0.04, 0.01))]),
     "single_cell_box": dict(lattice="D3Q19", n=(1, 1, 1), tau=0.8, u0=(0.01, 0.02, -0.03)),
+    "refill_extrap_spheres": dict(
+        lattice="D3Q19", n=(36, 30, 28), tau=0.7, refill="extrap", u0=(0.01, 0.0, 0.01),
+        edges={"x": "periodic", "y": ("wall", "wall"), "z": "periodic"},
+        bodies=[dict(shape="sphere", R=5.2, X0=(9.4, 15.2, 13.8), U=(0.06, 0.03, -0.04)),
+                dict(shape="sphere", R=4.1, X0=(27.0, 8.0, 3.0), U=(-0.04, 0.0, 0.05), W=(0.0, 0.004, 0.0))]),
     "walled_channel_sphere": dict(  # 16-byte rows, walls on y, inlet / outlet on x
         lattice="D3Q19", n=(48, 20, 18), tau=0.62, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
         inlet={"u": 0.03}, u0=(0.03, 0.0, 0.0), bodies=[dict(shape="sphere", R=4.6, X0=(14.2, 9.7, 8.9))]),
@@ -267,3 +279,19 @@ def test_staged_wait_expiry_is_reported(monkeypatch):
     assert dom.stats()["timeouts"] == 0
     assert np.isfinite(dom.force_torque("static")).all()
     dom.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("dim,name", [("2d", "refill_extrap"), ("2d", "refill_extrap_ellipse"),
+                                      ("3d", "refill_extrap_spheres")])
+def test_extrapolation_refill_choices_match(oracle_mod, dim, name, prec):
+    """The extrapolation refill takes the same decisions as the oracle in every
+    precision (normal, direction and fallback are evaluated in FP64 from the
+    pose): as many nodes extrapolated, as many uncovered."""
+    spec = dict((CASES_2D if dim == "2d" else CASES_3D)[name], precision=prec)
+    steps = 120 if dim == "2d" else 40
+    dom, ref = _run_both(oracle_mod, spec, steps)
+    st = dom.stats()
+    assert st["extrapolated"] == ref.extrapolated() > 0
+    if name == "refill_extrap":  # trailing side next to the wall: some fallbacks to the equilibrium rule
+        assert st["uncovered"] > st["extrapolated"]
