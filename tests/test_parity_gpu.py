@@ -71,10 +71,11 @@ CASES_2D = {
     "refill_ubar": dict(
         lattice="D2Q9", n=(45, 41), tau=0.9, refill="ubar", u0=(0.01, 0.02),
         bodies=[dict(shape="cylinder", R=6.6, X0=(22.2, 20.1), U=(0.07, 0.05))]),
-    "refill_extrap": dict(  # extrapolation refill; the wall and the seam force fallbacks
+    "refill_extrap": dict(  # extrapolation refill; the static neighbour forces some fallbacks
         lattice="D2Q9", n=(52, 38), tau=0.8, refill="extrap", u0=(0.01, -0.02),
         edges={"x": "periodic", "y": ("wall", "wall")},
-        bodies=[dict(shape="cylinder", R=6.1, X0=(45.3, 7.3), U=(0.08, 0.03), W=0.004)]),
+        bodies=[dict(shape="cylinder", R=6.0, X0=(14.0, 19.0)),
+                dict(shape="cylinder", R=6.0, X0=(28.3, 19.4), U=(0.03, 0.0), W=0.004)]),
     "refill_extrap_ellipse": dict(  # normal from the rotated ellipse's gradient at t+1
         lattice="D2Q9", n=(50, 44), tau=0.7, refill="extrap", u0=(0.02, 0.0),
         bodies=[dict(shape="ellipse", R=8.7, R2=4.1, theta0=0.9, X0=(24.1, 21.7), W=0.008, U=(0.03, 0.02))]),
@@ -106,7 +107,7 @@ CASES_3D = {
     "refill_extrap_spheres": dict(
         lattice="D3Q19", n=(36, 30, 28), tau=0.7, refill="extrap", u0=(0.01, 0.0, 0.01),
         edges={"x": "periodic", "y": ("wall", "wall"), "z": "periodic"},
-        bodies=[dict(shape="sphere", R=5.2, X0=(9.4, 15.2, 13.8), U=(0.06, 0.03, -0.04)),
+        bodies=[dict(shape="sphere", R=5.2, X0=(9.4, 15.2, 13.8), U=(0.06, 0.0, -0.04)),
                 dict(shape="sphere", R=4.1, X0=(27.0, 8.0, 3.0), U=(-0.04, 0.0, 0.05), W=(0.0, 0.004, 0.0))]),
     "walled_channel_sphere": dict(  # 16-byte rows, walls on y, inlet / outlet on x
         lattice="D3Q19", n=(48, 20, 18), tau=0.62, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
@@ -293,5 +294,5 @@ def test_extrapolation_refill_choices_match(oracle_mod, dim, name, prec):
     dom, ref = _run_both(oracle_mod, spec, steps)
     st = dom.stats()
     assert st["extrapolated"] == ref.extrapolated() > 0
-    if name == "refill_extrap":  # trailing side next to the wall: some fallbacks to the equilibrium rule
+    if name == "refill_extrap":  # trailing side next to the static body: some fallbacks to the equilibrium rule
         assert st["uncovered"] > st["extrapolated"]
