@@ -74,6 +74,8 @@ typedef struct {
     double g[3];
     double u0[3];
     double gravity[3]; /* acceleration of the free bodies (weight less buoyancy) */
+    int edge_rule;     /* 0: wall / inlet faces are half-way links; 1: Zou-He nodes on the faces */
+    int pad;
 } or_desc;
 
 typedef struct {
@@ -583,6 +585,12 @@ or_dom *or_create(const or_desc *d)
         if (d->edge[e] == OR_OUTLET && e != 1) return NULL;
     }
     if (!(d->tau > 0.5)) return NULL;
+    if (d->edge_rule != 0 && d->edge_rule != 1) return NULL;
+    if (d->edge_rule == 1) { /* Zou-He faces: an inner neighbour distinct from both faces */
+        const int nn[3] = {d->nx, d->ny, d->nz};
+        for (int a = 0; a < 3; ++a)
+            if (d->edge[2 * a] != OR_PERIODIC && nn[a] < 3) return NULL;
+    }
     or_dom *o = (or_dom *)calloc(1, sizeof(or_dom));
     if (!o) return NULL;
     o->d = *d;
@@ -719,6 +727,151 @@ static int extrap_nodes(const or_dom *o, const or_body *b, long long t, int x, i
     return best;
 }
 
+/*
+ * Zou-He velocity condition (edge rule 1; the paper's test section imposes
+ * its no-slip walls this way, after its cited reference).  The nodes of a
+ * wall or inlet face lie ON the boundary (walls at the node layers 0 and
+ * n - 1, not half-way) with a prescribed velocity u_w: 0 on walls; on the
+ * inlet u_in, or the on-node parabola 4 u_in y (H - y) / H^2, H = ny - 1.
+ * After streaming, the populations that would come from outside the face are
+ * closed from the known ones at the same node:
+ *   a node on one such face, outward normal n (axis a, sign s):
+ *     j = rho_u u_w - g/2  (the Guo-shifted momentum sum_i c_i f_i; rho_u is
+ *         rho0 in the quasi-incompressible model, rho otherwise),
+ *     rho = S0 + 2 S+ - j.n, i.e. rho (1 + u_w.n) = S0 + 2 S+ + g.n/2 in the
+ *         standard model (S0: the populations with c.n = 0, S+: c.n > 0),
+ *     f_i = f_ib + 6 w_i c_i.j - sum_t c_i,t N_t   for every c_i.n < 0,
+ *     N_t = T_t / 2 - j_t / 3 with T_t = sum over c.n = 0 of f c_t, for the
+ *         two (one in 2-D) tangential axes t;
+ *   so that sum_i f_i = rho and sum_i c_i f_i = j exactly (up to rounding);
+ *   a node on two or three such faces (an edge or corner): u_w = 0 (a wall
+ *     wins over the inlet) without the force shift (sum_i c_i f_i = 0 there),
+ *     rho = the density at t of the inner diagonal
+ *     neighbour (one step inward along each face normal) taken as the sum of
+ *     its fhat(t), every unknown population whose opposite is known bounces
+ *     back (f_i = f_ib), along the axis of a 3-D edge those bounced
+ *     populations carry a correction that cancels the momentum of the known
+ *     ones, and the unknown pairs whose opposite is unknown too share the
+ *     rest of rho equally.
+ */
+static int zh_face(const or_dom *o, int a, int side)
+{
+    int e = o->d.edge[2 * a + side];
+    return e == OR_WALL || e == OR_INLET;
+}
+
+static void zouhe_node(or_dom *o, int x, int y, int z)
+{
+    const long N = o->N;
+    const int Q = o->Q;
+    const int pos[3] = {x, y, z};
+    int nface = 0, axis = 0, sgn = 0, wall = 0, inward[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        if (pos[a] == 0 && zh_face(o, a, 0)) {
+            nface++;
+            axis = a;
+            sgn = -1;
+            inward[a] = 1;
+            wall |= o->d.edge[2 * a] == OR_WALL;
+        } else if (pos[a] == o->n[a] - 1 && zh_face(o, a, 1)) {
+            nface++;
+            axis = a;
+            sgn = 1;
+            inward[a] = -1;
+            wall |= o->d.edge[2 * a + 1] == OR_WALL;
+        }
+    }
+    if (nface == 0) return;
+    const long xc = cell(o, x, y, z);
+    if (o->solid[xc] >= 0) return;
+    double f[19];
+    int unknown[19];
+    for (int i = 0; i < Q; ++i) {
+        long s = -1;
+        int body;
+        int k = classify(o, x, y, z, i, &s, &body);
+        f[i] = o->fnew[(long)i * N + xc];
+        unknown[i] = k == K_WALL || k == K_INLET;
+    }
+    if (nface == 1) {
+        double uw[3] = {0.0, 0.0, 0.0}, g[3] = {0.0, 0.0, 0.0}, j[3], T[3] = {0.0, 0.0, 0.0};
+        if (!wall) {
+            if (!o->d.inlet_parabolic) {
+                uw[0] = o->d.u_in;
+            } else {
+                double H = (double)(o->n[1] - 1);
+                uw[0] = 4.0 * o->d.u_in * (double)y * (H - (double)y) / (H * H);
+            }
+        }
+        if (o->d.has_force)
+            for (int a = 0; a < 3; ++a) g[a] = o->d.g[a];
+        double S0 = 0.0, Sp = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            int cn = o->c[i][axis] * sgn;
+            if (cn == 0) {
+                S0 += f[i];
+                for (int a = 0; a < 3; ++a) T[a] += o->c[i][a] * f[i];
+            } else if (cn > 0) {
+                Sp += f[i];
+            }
+        }
+        if (o->d.eq == 0) { /* the density follows: rho = S0 + 2 S+ - j.n */
+            for (int a = 0; a < 3; ++a) j[a] = o->d.rho0 * uw[a] - 0.5 * g[a];
+        } else {
+            double rho = ((S0 + 2.0 * Sp) + (double)sgn * (0.5 * g[axis])) / (1.0 + (double)sgn * uw[axis]);
+            for (int a = 0; a < 3; ++a) j[a] = rho * uw[a] - 0.5 * g[a];
+        }
+        double Nt[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 3; ++a)
+            if (a != axis) Nt[a] = 0.5 * T[a] - j[a] / 3.0;
+        for (int i = 0; i < Q; ++i) {
+            if (!unknown[i]) continue;
+            const int *c = o->c[i];
+            double cj = ((double)c[0] * j[0] + (double)c[1] * j[1]) + (double)c[2] * j[2];
+            double v = f[o->opp[i]] + (6.0 * o->w[i]) * cj;
+            for (int a = 0; a < 3; ++a)
+                if (a != axis && c[a] != 0) v = v - (double)c[a] * Nt[a];
+            o->fnew[(long)i * N + xc] = v;
+        }
+        return;
+    }
+    const long xin = cell(o, x + inward[0], y + inward[1], z + inward[2]);
+    double rc = 0.0;
+    for (int i = 0; i < Q; ++i) rc += o->fhat[(long)i * N + xin];
+    int buried[19], nbur = 0;
+    for (int i = 0; i < Q; ++i) {
+        buried[i] = unknown[i] && unknown[o->opp[i]];
+        nbur += buried[i];
+    }
+    for (int i = 0; i < Q; ++i)
+        if (unknown[i] && !buried[i]) f[i] = f[o->opp[i]];
+    /* along an axis with no face at the node (the axis of a 3-D edge) the
+     * bounced pairs carry no momentum, the known pairs carry T; the m
+     * bounced populations moving along it take -c T / m, so the momentum
+     * along it is 0 */
+    for (int a = 0; a < 3; ++a) {
+        if (inward[a] != 0) continue;
+        double T = 0.0;
+        int m = 0;
+        for (int i = 0; i < Q; ++i) {
+            if (o->c[i][a] == 0) continue;
+            if (!unknown[i] && !unknown[o->opp[i]]) T += o->c[i][a] * f[i];
+            if (unknown[i] && !buried[i]) m++;
+        }
+        if (m == 0) continue;
+        double Nt = T / (double)m;
+        for (int i = 0; i < Q; ++i)
+            if (unknown[i] && !buried[i] && o->c[i][a] != 0) f[i] = f[i] - (double)o->c[i][a] * Nt;
+    }
+    double rest = rc;
+    for (int i = 0; i < Q; ++i)
+        if (!buried[i]) rest = rest - f[i];
+    for (int i = 0; i < Q; ++i)
+        if (buried[i]) f[i] = rest / (double)nbur;
+    for (int i = 0; i < Q; ++i)
+        if (unknown[i]) o->fnew[(long)i * N + xc] = f[i];
+}
+
 static int one_step(or_dom *o)
 {
     const long N = o->N;
@@ -762,6 +915,8 @@ static int one_step(or_dom *o)
                         for (int a = 0; a < 3; ++a) rB[a] = d[a] - delta * o->c[i][a];
                         body_velocity(b, rB, uB);
                         v = wall_value(o, xc, x, y, z, i, delta, uB, &fallback);
+                    } else if (o->d.edge_rule == 1) {
+                        v = 0.0; /* closed by zouhe_node below */
                     } else {
                         double uB[3];
                         edge_velocity(o, k, y, i, uB);
@@ -771,6 +926,10 @@ static int one_step(or_dom *o)
                 }
             }
     o->n_fallback += fallback;
+    if (o->d.edge_rule == 1)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) zouhe_node(o, x, y, z);
 
     /* 4: momentum exchange over the cut links, in cell and direction order.
      * By Eq. Equalities, fhat_i(x_A - c_i, t) is the wall value that streamed
@@ -789,6 +948,7 @@ static int one_step(or_dom *o)
                     int body;
                     int k = classify(o, x, y, z, i, &s, &body);
                     if (k == K_FLUID || k == K_OUTLET) continue;
+                    if (k != K_BODY && o->d.edge_rule == 1) continue; /* Zou-He faces have no links */
                     const int *c = o->c[i];
                     const int *cb = o->c[o->opp[i]];
                     double fa = o->fnew[(long)i * N + xc];

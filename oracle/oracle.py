@@ -29,6 +29,7 @@ class _Desc(C.Structure):
         ("has_force", C.c_int), ("refill", C.c_int),
         ("tau", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double),
         ("g", C.c_double * 3), ("u0", C.c_double * 3), ("gravity", C.c_double * 3),
+        ("edge_rule", C.c_int), ("pad", C.c_int),
     ]
 
 
@@ -149,6 +150,8 @@ class Oracle:
     "periodic" | (lo, hi) kinds among "wall", "inlet", "outlet"), ``inlet``
     ({"profile": "uniform"/"parabolic", "u": ...}), ``force``, ``u0``,
     ``refill`` ("uB"/"ubar"/"extrap"), ``gravity`` (acceleration of free bodies),
+    ``edge_rule`` ("link": wall / inlet faces as half-way links; "zouhe": Zou-He
+    nodes on the faces),
     ``bodies`` (list of dicts: shape, R, X0, U, W, halfway, invert, t0, free,
     density_ratio; ellipses: shape "ellipse", R and R2 the semi-axes, theta0).
     """
@@ -174,6 +177,7 @@ class Oracle:
         for k in range(3):
             d.u0[k] = float(u0[k]) if k < len(u0) else 0.0
         d.refill = {"uB": 0, "ubar": 1, "extrap": 2}[spec.get("refill", "uB")]
+        d.edge_rule = {"link": 0, "zouhe": 1}[spec.get("edge_rule", "link")]
         gv = tuple(spec.get("gravity", (0.0, 0.0, 0.0)))
         for k in range(3):
             d.gravity[k] = float(gv[k]) if k < len(gv) else 0.0
