@@ -68,15 +68,32 @@ extern "C" {
 #define LBM_EQ_INCOMP 0
 #define LBM_EQ_STANDARD 1
 
-/* Edge kinds for the six faces.  Walls and the inlet are links at
- * Delta = 1/2 handled by the same curved-wall rule (u_B = 0 for walls,
- * u_B = inlet profile at the wall point for the inlet); the outlet copies the
- * last interior column (zero gradient).  Inlet only on x-low, outlet only on
- * x-high; a wall takes precedence at corners. */
+/* Edge kinds for the six faces.  Under LBM_EDGE_RULE_LINK (default) walls
+ * and the inlet are links at Delta = 1/2 handled by the same curved-wall rule
+ * (u_B = 0 for walls, u_B = inlet profile at the wall point for the inlet;
+ * walls half-way, at -1/2 and n - 1/2); the outlet copies the last interior
+ * column (zero gradient).  Inlet only on x-low, outlet only on x-high; a wall
+ * takes precedence at corners. */
 #define LBM_EDGE_PERIODIC 0
 #define LBM_EDGE_WALL 1
 #define LBM_EDGE_INLET 2
 #define LBM_EDGE_OUTLET 3
+
+/* Edge rule (the test section of the paper imposes its no-slip walls with
+ * the Zou-He velocity condition of its cited reference).
+ * LBM_EDGE_RULE_ZOUHE: the nodes of wall and inlet faces lie ON the boundary
+ * (walls at the node layers 0 and n - 1) with velocity 0 (walls) or the
+ * inlet profile (u_in, or 4 u_in y (H - y) / H^2 with H = ny - 1); after
+ * streaming, the populations entering from outside are closed at each face
+ * node so that its momentum sum_i c_i f_i equals rho u_w - g/2 (rho0 u_w - g/2
+ * in the quasi-incompressible model; g the body force): bounce-back of the
+ * non-equilibrium part plus the tangential correction.  Edge and corner nodes
+ * (two or three such faces) take u = 0 without the force shift, bounce-back,
+ * a tangential correction along a 3-D edge, and share the density of their
+ * inner diagonal neighbour at t among the remaining unknown pairs.  Needs at
+ * least 3 nodes along each such axis; not available in serving batches. */
+#define LBM_EDGE_RULE_LINK 0
+#define LBM_EDGE_RULE_ZOUHE 1
 
 #define LBM_INLET_UNIFORM 0
 #define LBM_INLET_PARABOLIC 1 /* u_x(y) = 4 u_in (y+1/2)(ny-1/2-y)/ny^2 */
@@ -136,6 +153,8 @@ typedef struct lbm_domain_desc {
     void *alloc_ctx;         /* passed through to alloc / free */
     double gravity[3];       /* acceleration of the free bodies: each feels its
                                 weight less buoyancy, (rho_b - rho0) V gravity */
+    int edge_rule;           /* LBM_EDGE_RULE_* */
+    int reserved_edge;       /* must be 0 */
 } lbm_domain_desc;
 
 typedef struct lbm_body {

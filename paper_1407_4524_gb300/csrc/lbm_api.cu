@@ -588,6 +588,14 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
         return fail(LBM_ERR_ARG, "unknown refill rule");
     if (d.inlet_profile != LBM_INLET_UNIFORM && d.inlet_profile != LBM_INLET_PARABOLIC)
         return fail(LBM_ERR_ARG, "unknown inlet profile");
+    if ((d.edge_rule != LBM_EDGE_RULE_LINK && d.edge_rule != LBM_EDGE_RULE_ZOUHE) || d.reserved_edge)
+        return fail(LBM_ERR_ARG, "unknown edge rule");
+    if (d.edge_rule == LBM_EDGE_RULE_ZOUHE) {
+        const int nn[3] = {d.nx, d.ny, d.nz};
+        for (int a = 0; a < 3; ++a)
+            if (d.edge[2 * a] != LBM_EDGE_PERIODIC && nn[a] < 3)
+                return fail(LBM_ERR_ARG, "Zou-He faces need at least 3 nodes along their axis");
+    }
     if ((d.alloc == nullptr) != (d.free == nullptr)) return fail(LBM_ERR_ARG, "alloc and free go together");
 
     cudaError_t e = cudaSetDevice(d.device);
@@ -628,6 +636,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     p.inlet_parabolic = d.inlet_profile == LBM_INLET_PARABOLIC;
     p.has_force = d.has_force ? 1 : 0;
     p.refill = d.refill;
+    p.zouhe = d.edge_rule == LBM_EDGE_RULE_ZOUHE;
     p.tau = d.tau;
     p.omega = 1.0 / d.tau;
     p.rho0 = d.rho0;
@@ -1173,6 +1182,7 @@ int batch_check_desc(const lbm_domain_desc &d, const lbm_body *hb, int n, int64_
     for (int k = 0; k < n; ++k)
         if (is_moving(hb[k])) return fail(LBM_ERR_ARG, "served solves take static bodies only");
     if (d.has_force) return fail(LBM_ERR_ARG, "served solves take no body force");
+    if (d.edge_rule != LBM_EDGE_RULE_LINK) return fail(LBM_ERR_ARG, "served solves take the link edge rule");
     return LBM_OK;
 }
 

@@ -139,6 +139,7 @@ struct Params {
     int staged;  // reduced precision: stream-collide from rows staged in shared memory
     int stage_expire_test; // test hook: the staged kernel issues no copy, so its waits expire
     int nsm;     // multiprocessors of the device
+    int zouhe;   // wall / inlet faces are Zou-He nodes (else half-way links)
     long long series_cap;
     long long me_stride; // ME contribution arrays are [ME_PER_LINK][me_stride]
     double tau, omega, rho0, u_in;

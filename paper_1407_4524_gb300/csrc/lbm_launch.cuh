@@ -62,6 +62,13 @@ template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &
         k_bulk<L, P, FM_XFACES><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
     else
         k_bulk<L, P, FM_GENERAL><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
+    if (p.zouhe) { // the Zou-He face nodes, which the bulk kernel skipped
+        long long plane = 0;
+        const long long n[3] = {p.nx, p.ny, p.nz};
+        for (int a = 0; a < 3; ++a) plane = std::max(plane, n[(a + 1) % 3] * n[(a + 2) % 3]);
+        const dim3 grid((unsigned)((plane + BULK_THREADS - 1) / BULK_THREADS), 1, 6);
+        k_zouhe<L, P><<<grid, BULK_THREADS, 0, s>>>(p, src, dst, sb.flags, mt, mt1);
+    }
     return cudaGetLastError();
 }
 

@@ -245,7 +245,7 @@ template <class L, class S> inline size_t stage_smem(int seg) {
 // the copies)
 template <class L, class P> inline bool staged_ok(const Params &p) {
     using S = typename P::S;
-    return !P::exact && ((size_t)p.nx * sizeof(S)) % 16 == 0 && p.nx >= 32;
+    return !P::exact && !p.zouhe && ((size_t)p.nx * sizeof(S)) % 16 == 0 && p.nx >= 32;
 }
 
 } // namespace lbm

@@ -355,6 +355,131 @@ __device__ __forceinline__ void face_terms(const Params &p, const typename P::S 
     }
 }
 
+// true when node (x,y,z) lies on a wall or inlet face (of a Zou-He domain)
+__device__ __forceinline__ bool zh_node(const Params &p, int x, int y, int z) {
+    auto zf = [](int e) { return e == 1 || e == 2; };
+    return (x == 0 && zf(p.edge[0])) || (x == p.nx - 1 && zf(p.edge[1])) || (y == 0 && zf(p.edge[2])) ||
+           (y == p.ny - 1 && zf(p.edge[3])) || (z == 0 && zf(p.edge[4])) || (z == p.nz - 1 && zf(p.edge[5]));
+}
+
+// Zou-He velocity condition on the wall and inlet faces (LBM_EDGE_RULE_ZOUHE;
+// the paper's test section imposes its no-slip walls this way, after its
+// cited reference).  The face nodes lie ON the boundary with velocity u_w (0
+// on walls; u_in or the on-node parabola 4 u_in y (H - y) / H^2, H = ny - 1,
+// on the inlet); `unknown` holds the populations whose pull source lies
+// beyond such a face (the bounce bits of pull_core), which are closed here
+// from the known ones at the same node:
+//   one face, outward normal n along `axis` with sign `sgn`:
+//     j = rho_u u_w - g/2 (rho_u = rho0, or rho = (S0 + 2 S+ + g.n/2) /
+//     (1 + u_w.n) in the standard model), f_i = f_ib + 6 w_i c_i.j -
+//     sum_t c_i,t N_t with N_t = T_t / 2 - j_t / 3 and T_t the c_t-moment of
+//     the populations with c.n = 0 -- so that the node's momentum is j;
+//   two or three faces (edge, corner): u_w = 0 without the force shift,
+//     bounce-back of the unknown populations with a known opposite, along
+//     the axis of a 3-D edge a correction that cancels the known pairs'
+//     momentum, and the unknown pairs share the rest of the density of the
+//     inner diagonal neighbour at t (the sum of its fhat) equally.
+// FP64: the oracle's operation order.  Reduced precision: the same formulas
+// on the deviations f - w (the weights cancel in each of them).
+template <class L, class P>
+__device__ __forceinline__ void zouhe_fill(const Params &p, const typename P::S *__restrict__ src, int x, int y, int z,
+                                        unsigned unknown, typename P::C *f) {
+    using C = typename P::C;
+    const int pos[3] = {x, y, z}, nn[3] = {p.nx, p.ny, p.nz};
+    int nface = 0, axis = 0, sgn = 0, wall = 0, inward[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        const int elo = p.edge[2 * a], ehi = p.edge[2 * a + 1];
+        if (pos[a] == 0 && (elo == 1 || elo == 2)) {
+            nface++;
+            axis = a;
+            sgn = -1;
+            inward[a] = 1;
+            wall |= elo == 1;
+        } else if (pos[a] == nn[a] - 1 && (ehi == 1 || ehi == 2)) {
+            nface++;
+            axis = a;
+            sgn = 1;
+            inward[a] = -1;
+            wall |= ehi == 1;
+        }
+    }
+    auto cc = [](int i, int a) { return a == 0 ? L::cx(i) : (a == 1 ? L::cy(i) : L::cz(i)); };
+    if (nface == 1) {
+        C uw[3] = {C(0), C(0), C(0)}, g[3] = {C(0), C(0), C(0)}, j[3], T[3] = {C(0), C(0), C(0)};
+        if (!wall) {
+            if (!p.inlet_parabolic) {
+                uw[0] = (C)p.u_in;
+            } else {
+                const double H = (double)(p.ny - 1);
+                uw[0] = (C)(4.0 * p.u_in * (double)y * (H - (double)y) / (H * H));
+            }
+        }
+        if (p.has_force)
+            for (int a = 0; a < 3; ++a) g[a] = (C)p.g[a];
+        C S0 = C(0), Sp = C(0);
+        for (int i = 0; i < L::Q; ++i) {
+            const int cn = cc(i, axis) * sgn;
+            if (cn == 0) {
+                S0 += f[i];
+                for (int a = 0; a < 3; ++a) T[a] += (C)cc(i, a) * f[i];
+            } else if (cn > 0) {
+                Sp += f[i];
+            }
+        }
+        if (p.eq == 0) {
+            for (int a = 0; a < 3; ++a) j[a] = (C)p.rho0 * uw[a] - C(0.5) * g[a];
+        } else {
+            C rho;
+            if constexpr (P::exact) rho = ((S0 + 2.0 * Sp) + (double)sgn * (0.5 * g[axis])) / (1.0 + (double)sgn * uw[axis]);
+            else rho = ((1.0f + (S0 + 2.0f * Sp)) + (float)sgn * (0.5f * g[axis])) / (1.0f + (float)sgn * uw[axis]);
+            for (int a = 0; a < 3; ++a) j[a] = rho * uw[a] - C(0.5) * g[a];
+        }
+        C Nt[3] = {C(0), C(0), C(0)};
+        for (int a = 0; a < 3; ++a)
+            if (a != axis) Nt[a] = C(0.5) * T[a] - j[a] / C(3);
+        for (int i = 0; i < L::Q; ++i) {
+            if (!((unknown >> i) & 1u)) continue;
+            const C cj = ((C)L::cx(i) * j[0] + (C)L::cy(i) * j[1]) + (C)L::cz(i) * j[2];
+            C v = f[L::opp(i)] + (C(6) * L::template w<C>(i)) * cj;
+            for (int a = 0; a < 3; ++a)
+                if (a != axis && cc(i, a) != 0) v = v - (C)cc(i, a) * Nt[a];
+            f[i] = v;
+        }
+        return;
+    }
+    const long long xin = cell_of(p, x + inward[0], y + inward[1], z + inward[2]);
+    C rc = C(0); // density of the inner neighbour at t (its deviation in the reduced modes)
+    for (int i = 0; i < L::Q; ++i) rc += (C)ldS(src + (long long)i * p.N + xin);
+    unsigned buried = 0u;
+    int nbur = 0;
+    for (int i = 0; i < L::Q; ++i)
+        if (((unknown >> i) & 1u) && ((unknown >> L::opp(i)) & 1u)) {
+            buried |= 1u << i;
+            nbur++;
+        }
+    for (int i = 0; i < L::Q; ++i)
+        if (((unknown >> i) & 1u) && !((buried >> i) & 1u)) f[i] = f[L::opp(i)];
+    for (int a = 0; a < 3; ++a) {
+        if (inward[a] != 0) continue;
+        C T = C(0);
+        int m = 0;
+        for (int i = 0; i < L::Q; ++i) {
+            if (cc(i, a) == 0) continue;
+            if (!((unknown >> i) & 1u) && !((unknown >> L::opp(i)) & 1u)) T += (C)cc(i, a) * f[i];
+            if (((unknown >> i) & 1u) && !((buried >> i) & 1u)) m++;
+        }
+        if (m == 0) continue;
+        const C Nt = T / (C)m;
+        for (int i = 0; i < L::Q; ++i)
+            if (((unknown >> i) & 1u) && !((buried >> i) & 1u) && cc(i, a) != 0) f[i] = f[i] - (C)cc(i, a) * Nt;
+    }
+    C rest = rc;
+    for (int i = 0; i < L::Q; ++i)
+        if (!((buried >> i) & 1u)) rest = rest - f[i];
+    for (int i = 0; i < L::Q; ++i)
+        if ((buried >> i) & 1u) f[i] = rest / (C)nbur;
+}
+
 __device__ __forceinline__ bool on_edge(const Params &p, int x, int y, int z) {
     return (!p.per[0] && (x == 0 || x == p.nx - 1)) || (!p.per[1] && (y == 0 || y == p.ny - 1)) ||
            (!p.per[2] && (z == 0 || z == p.nz - 1));
@@ -549,6 +674,9 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
                                           const typename P::C *__restrict__ mac_t, typename P::C *__restrict__ mac_t1,
                                           int x, int y, int z) {
     using C = typename P::C;
+    if constexpr (FM != FM_PERIODIC) {
+        if (p.zouhe && zh_node(p, x, y, z)) return; // Zou-He face nodes: k_zouhe
+    }
     const long long cell = cell_of(p, x, y, z);
     const uint8_t fl = __ldg(flags + cell);
     if (fl & FL_SOLID) return;
@@ -587,6 +715,57 @@ __global__ void __launch_bounds__(BULK_THREADS, P::exact ? 4 : BULK_MIN_BLOCKS) 
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= p.nx) return;
     bulk_node<L, P, FM>(p, src, dst, flags, mac_t, mac_t1, x, y, z);
+}
+
+// Zou-He face nodes (the bulk kernel skips them): pull, closure of the
+// populations entering from outside (zouhe_fill), moments, BGK collision,
+// store.  One thread per node of a face plane, blockIdx.z = face (x-lo, x-hi,
+// y-lo, y-hi, z-lo, z-hi); a node on several Zou-He faces is taken by the
+// first of them.
+template <class L, class P>
+__global__ void __launch_bounds__(BULK_THREADS) k_zouhe(Params p, const typename P::S *__restrict__ src,
+                                                        typename P::S *__restrict__ dst,
+                                                        const uint8_t *__restrict__ flags,
+                                                        const typename P::C *__restrict__ mac_t,
+                                                        typename P::C *__restrict__ mac_t1) {
+    using C = typename P::C;
+    const int face = blockIdx.z, a = face >> 1, side = face & 1;
+    auto zf = [](int e) { return e == 1 || e == 2; };
+    if (!zf(p.edge[face])) return;
+    const int nn[3] = {p.nx, p.ny, p.nz};
+    const int au = a == 0 ? 1 : 0, av = a == 2 ? 1 : 2;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)nn[au] * nn[av]) return;
+    int q[3];
+    q[a] = side ? nn[a] - 1 : 0;
+    q[au] = (int)(k % nn[au]);
+    q[av] = (int)(k / nn[au]);
+    for (int f = 0; f < face; ++f)
+        if (zf(p.edge[f]) && q[f >> 1] == ((f & 1) ? nn[f >> 1] - 1 : 0)) return;
+    const int x = q[0], y = q[1], z = q[2];
+    const long long cell = cell_of(p, x, y, z);
+    const uint8_t fl = __ldg(flags + cell);
+    if (fl & FL_SOLID) return;
+    C f[L::Q];
+    unsigned inlet_only;
+    const unsigned unknown = pull_core<L, P, FM_GENERAL>(p, src, x, y, z, cell, f, inlet_only);
+    zouhe_fill<L, P>(p, src, x, y, z, unknown, f);
+    if constexpr (P::exact) {
+        double rho, u[3];
+        moments_x<L>(p, f, rho, u);
+        if (fl & FL_MAC) {
+            mac_t1[4 * cell] = rho;
+            mac_t1[4 * cell + 1] = u[0];
+            mac_t1[4 * cell + 2] = u[1];
+            mac_t1[4 * cell + 3] = u[2];
+        }
+        collide_x<L>(p, f, rho, u);
+    } else {
+        float drho, u[3];
+        moments_f<L>(p, f, drho, u);
+        collide_f<L>(p, f, drho, u);
+    }
+    for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
 }
 
 // Work of one cut link j of body b: the wall value fhat_i(x_A, t) of Eq.

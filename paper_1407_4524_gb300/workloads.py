@@ -19,6 +19,7 @@ units per step):
   u0         initial uniform velocity
   refill     "uB" (f^eq(rho_bar, u_B)) | "ubar" (f^eq(rho_bar, u_bar)) | "extrap"
              (quadratic extrapolation along the lattice direction nearest the normal)
+  edge_rule  "link" (walls / inlet as half-way links) | "zouhe" (Zou-He nodes on the faces)
   bodies     list of {"shape": "cylinder" | "sphere" | "ellipse", "R", "X0", "U",
              "W", "halfway", "t0"; free bodies: "free", "density_ratio";
              ellipses: "R2" (second semi-axis), "theta0"}
@@ -77,15 +78,24 @@ def sphere_channel_3d(precision: str = "fp32") -> dict:
     )
 
 
-def sedimenting_disc_2d(precision: str = "fp64", density_ratio: float = 1.01, steps: int = 20000) -> dict:
+def _wall_spacing(nx: int, width: float, edge_rule: str) -> float:
+    """Lattice spacing of a channel of `width` across nx nodes: Zou-He walls
+    sit on the outer node rows (nx - 1 spacings), half-way link walls half a
+    spacing outside them (nx spacings)."""
+    return width / (nx - 1) if edge_rule == "zouhe" else width / nx
+
+
+def sedimenting_disc_2d(precision: str = "fp64", density_ratio: float = 1.01, steps: int = 20000,
+                        edge_rule: str = "zouhe") -> dict:
     """The paper's sedimenting disc in lattice units: D2Q9 135 x 1073, tau 0.6,
-    walls on every face, a free disc of diameter d = W/4 falling under gravity.
+    no-slip walls on every face (Zou-He nodes, the paper's edge treatment, or
+    half-way links), a free disc of diameter d = W/4 falling under gravity.
     Physical data: W = 4 mm (135 nodes), H = 8 W, d = 1 mm, water (rho 1000,
     nu 1e-6 m^2/s), g = 9.81 m/s^2; nu_lattice = (tau - 1/2)/3 fixes the time
     step dt = nu_lattice dx^2 / nu, so g_lattice = g dt^2 / dx.  The centre
     starts 25 mm above the bottom and 0.76 mm off the channel axis."""
     nx, ny, tau = 135, 1073, 0.6
-    dx = 4e-3 / nx
+    dx = _wall_spacing(nx, 4e-3, edge_rule)
     nu_l = (tau - 0.5) / 3.0
     dt = nu_l * dx * dx / 1e-6
     g_l = 9.81 * dt * dt / dx
@@ -93,26 +103,28 @@ def sedimenting_disc_2d(precision: str = "fp64", density_ratio: float = 1.01, st
     x0 = 0.5 * (nx - 1) + 7.6e-4 / dx
     y0 = 25e-3 / dx
     return dict(
-        name="sedimenting_disc_2d", lattice="D2Q9", n=(nx, ny), tau=tau,
+        name="sedimenting_disc_2d", lattice="D2Q9", n=(nx, ny), tau=tau, edge_rule=edge_rule,
         edges={"x": ("wall", "wall"), "y": ("wall", "wall")}, gravity=(0.0, -g_l),
         bodies=[dict(shape="cylinder", R=R, X0=(x0, y0), free=True, density_ratio=float(density_ratio))],
         precision=precision, steps=steps,
     )
 
 
-def sedimenting_ellipse_2d(precision: str = "fp64", density_ratio: float = 1.10, steps: int = 20000) -> dict:
+def sedimenting_ellipse_2d(precision: str = "fp64", density_ratio: float = 1.10, steps: int = 20000,
+                           edge_rule: str = "zouhe") -> dict:
     """The paper's sedimenting ellipse in lattice units: D2Q9 135 x 1676, tau
-    0.6, walls on every face, a free ellipse with major axis a = 1 mm (the full
+    0.6, no-slip walls on every face (Zou-He nodes or half-way links), a free
+    ellipse with major axis a = 1 mm (the full
     axis; semi-axes a/2 and a/4: aspect ratio 2), channel W = 4 a (blockage 4),
     H = 50 a, released at the channel axis 48 mm above the bottom at
     theta0 = pi/4, r_rho = 1.10; water and g as for the disc."""
     nx, ny, tau = 135, 1676, 0.6
-    dx = 4e-3 / nx
+    dx = _wall_spacing(nx, 4e-3, edge_rule)
     nu_l = (tau - 0.5) / 3.0
     dt = nu_l * dx * dx / 1e-6
     g_l = 9.81 * dt * dt / dx
     return dict(
-        name="sedimenting_ellipse_2d", lattice="D2Q9", n=(nx, ny), tau=tau,
+        name="sedimenting_ellipse_2d", lattice="D2Q9", n=(nx, ny), tau=tau, edge_rule=edge_rule,
         edges={"x": ("wall", "wall"), "y": ("wall", "wall")}, gravity=(0.0, -g_l),
         bodies=[dict(shape="ellipse", R=0.5e-3 / dx, R2=0.25e-3 / dx, theta0=math.pi / 4,
                      X0=(0.5 * (nx - 1), 48e-3 / dx), free=True, density_ratio=float(density_ratio))],

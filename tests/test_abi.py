@@ -114,3 +114,51 @@ def test_batch_rejects_bad_arguments_without_gpu():
     fn = lib.lbm_get_populations_noalloc
     fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert fn(None, None) == 1
+
+
+def test_edge_rule_validated_without_gpu():
+    from paper_1407_4524_gb300 import lbm
+    lib = lbm.load()
+    h = ctypes.c_void_p()
+    spec = dict(lattice="D2Q9", n=(8, 8), tau=0.8, edges={"x": "periodic", "y": ("wall", "wall")})
+    d = _desc(lbm, dict(spec, edge_rule="zouhe"))
+    d.edge_rule = 5
+    assert lib.lbm_create_domain(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"edge rule" in lib.lbm_last_error()
+    d = _desc(lbm, dict(spec, n=(8, 2), edge_rule="zouhe"))
+    assert lib.lbm_create_domain(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"at least 3 nodes" in lib.lbm_last_error()
+    out = ctypes.c_int64()
+    d = _desc(lbm, dict(spec, precision="fp32", edge_rule="zouhe"))
+    rc = lib.lbm_batch_solve_bytes(ctypes.byref(d), None, 0, 10, ctypes.byref(out))
+    assert rc == 1 and b"link edge rule" in lib.lbm_last_error()
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's structures have the header's sizes and field offsets
+    (checked by compiling the header with the host C compiler)."""
+    import shutil
+    import subprocess
+    from pathlib import Path
+    from paper_1407_4524_gb300 import lbm
+    if not shutil.which("gcc"):
+        pytest.skip("no host C compiler")
+    inc = Path(__file__).resolve().parents[1] / "include"
+    structs = {"lbm_domain_desc": lbm.lbm_domain_desc, "lbm_body": lbm.lbm_body, "lbm_stats": lbm.lbm_stats,
+               "lbm_batch_desc": lbm.lbm_batch_desc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(inc), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.split("\n") if line)
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)

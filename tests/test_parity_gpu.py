@@ -79,6 +79,17 @@ CASES_2D = {
     "refill_extrap_ellipse": dict(  # normal from the rotated ellipse's gradient at t+1
         lattice="D2Q9", n=(50, 44), tau=0.7, refill="extrap", u0=(0.02, 0.0),
         bodies=[dict(shape="ellipse", R=8.7, R2=4.1, theta0=0.9, X0=(24.1, 21.7), W=0.008, U=(0.03, 0.02))]),
+    "zouhe_poiseuille": dict(  # Zou-He walls on the node rows 0 and ny - 1, body force
+        lattice="D2Q9", n=(5, 33), tau=0.8, force=(1e-5, 0.0), edge_rule="zouhe",
+        edges={"x": "periodic", "y": ("wall", "wall")}),
+    "zouhe_channel_cylinder": dict(  # Zou-He parabolic inlet and walls, zero-gradient outlet
+        lattice="D2Q9", n=(61, 29), tau=0.7, edge_rule="zouhe", u0=(0.02, 0.0),
+        edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")}, inlet={"profile": "parabolic", "u": 0.05},
+        bodies=[dict(shape="cylinder", R=6.3, X0=(15.4, 14.2))]),
+    "zouhe_box_rotating": dict(  # closed Zou-He box: every corner; a rotating ellipse
+        lattice="D2Q9", n=(41, 37), tau=0.75, edge_rule="zouhe", eq="standard",
+        edges={"x": ("wall", "wall"), "y": ("wall", "wall")},
+        bodies=[dict(shape="ellipse", R=9.0, R2=5.2, theta0=0.4, X0=(20.3, 18.2), W=0.01)]),
     "halfway_body": dict(
         lattice="D2Q9", n=(40, 33), tau=0.66, u0=(0.03, 0.01),
         bodies=[dict(shape="cylinder", R=5.5, X0=(19.0, 16.5), halfway=True)]),
@@ -115,6 +126,14 @@ CASES_3D = {
     "ellipse_3d_rotating": dict(  # elliptic cylinder along z in D3Q19, rotating about z
         lattice="D3Q19", n=(36, 34, 8), tau=0.7, u0=(0.02, 0.01, 0.0),
         bodies=[dict(shape="ellipse", R=8.2, R2=4.6, theta0=1.1, X0=(17.4, 16.9, 0.0), W=(0.0, 0.0, 0.005))]),
+    "zouhe_duct_sphere": dict(  # Zou-He inlet, walls on y and z (3-D edges), outlet
+        lattice="D3Q19", n=(40, 21, 19), tau=0.65, edge_rule="zouhe", u0=(0.03, 0.0, 0.0),
+        edges={"x": ("inlet", "outlet"), "y": ("wall", "wall"), "z": ("wall", "wall")}, inlet={"u": 0.03},
+        bodies=[dict(shape="sphere", R=4.8, X0=(13.2, 10.4, 9.3))]),
+    "zouhe_closed_box": dict(  # every 3-D edge and corner; a rotating sphere
+        lattice="D3Q19", n=(23, 21, 20), tau=0.7, edge_rule="zouhe",
+        edges={"x": ("wall", "wall"), "y": ("wall", "wall"), "z": ("wall", "wall")},
+        bodies=[dict(shape="sphere", R=5.1, X0=(11.3, 10.2, 9.8), W=(0.004, -0.006, 0.008))]),
     "walled_box_cylinder3d": dict(
         lattice="D3Q19", n=(30, 28, 9), tau=0.7, u0=(0.02, 0.01, 0.0),
         edges={"x": ("wall", "wall"), "y": ("wall", "wall"), "z": "periodic"},
