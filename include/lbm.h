@@ -282,6 +282,25 @@ int lbm_get_populations(lbm_domain *dom, double *out);
 #define LBM_NOALLOC_MAX_VALUES 4194304
 int lbm_get_populations_noalloc(lbm_domain *dom, double *out);
 
+/* Sets the populations of the current step t: `f` is host FP64 f_i(x, t)
+ * (pre-collision), layout [Q][nz][ny][nx], as lbm_get_populations returns
+ * (SoA, x fastest).  The library computes the moments (Eqs.
+ * LBMmacroscopics_0/1) and the BGK collision (Eq. collision) of every node
+ * and stores fhat(x, t), from which the next lbm_step streams; in the reduced
+ * modes f - w is rounded to the storage precision.  The values at solid
+ * nodes are ignored by the step.  Bodies (lbm_set_bodies) re-initialise the
+ * populations, so set the bodies first.  Synchronous; the caller keeps `f`.
+ * Errors: LBM_ERR_ARG (NULL), LBM_ERR_OOM (staging buffer), LBM_ERR_CUDA. */
+int lbm_set_populations(lbm_domain *dom, const double *f);
+
+/* Moments of the current step t into host `out` [4][nz][ny][nx]: rho, u_x,
+ * u_y, u_z, with rho_u u = sum_i c_i f_i + g/2 (rho_u = rho0 in the
+ * quasi-incompressible model, else rho; g the body force), evaluated from the
+ * stored post-collision populations (the collision keeps rho and adds g to the
+ * momentum).  Zero at solid nodes.  Synchronous.
+ * Errors: LBM_ERR_ARG (NULL), LBM_ERR_OOM (staging buffer), LBM_ERR_CUDA. */
+int lbm_get_macros(lbm_domain *dom, double *out);
+
 /* Body state at the current step: out[n_bodies][9] = X(t), U(t), W(t).
  * Synchronises.  (Free bodies: their integrated motion.) */
 int lbm_get_body_state(lbm_domain *dom, double *out);

@@ -32,6 +32,25 @@ cudaError_t launch_links_p12(int Q, int prec, const Params &p, const StepBufs &s
 cudaError_t launch_bulk_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
 cudaError_t launch_finish_p12(int Q, int prec, const Params &p, const StepBufs &sb, cudaStream_t s);
 
+cudaError_t launch_load_p0(int Q, const Params &p, const double *stage, long long c0, long long n, void *dst,
+                           void *mac, const uint8_t *flags, cudaStream_t s);
+cudaError_t launch_macros_p0(int Q, const Params &p, const void *src, const uint16_t *owner, long long c0,
+                             long long n, double *out, cudaStream_t s);
+cudaError_t launch_load_p12(int Q, int prec, const Params &p, const double *stage, long long c0, long long n,
+                            void *dst, void *mac, const uint8_t *flags, cudaStream_t s);
+cudaError_t launch_macros_p12(int Q, int prec, const Params &p, const void *src, const uint16_t *owner, long long c0,
+                              long long n, double *out, cudaStream_t s);
+
+cudaError_t launch_load(int Q, int prec, const Params &p, const double *stage, long long c0, long long n, void *dst,
+                        void *mac, const uint8_t *flags, cudaStream_t s) {
+    return prec == 0 ? launch_load_p0(Q, p, stage, c0, n, dst, mac, flags, s)
+                     : launch_load_p12(Q, prec, p, stage, c0, n, dst, mac, flags, s);
+}
+cudaError_t launch_macros(int Q, int prec, const Params &p, const void *src, const uint16_t *owner, long long c0,
+                          long long n, double *out, cudaStream_t s) {
+    return prec == 0 ? launch_macros_p0(Q, p, src, owner, c0, n, out, s)
+                     : launch_macros_p12(Q, prec, p, src, owner, c0, n, out, s);
+}
 cudaError_t launch_init(int Q, int prec, const Params &p, void *dst, void *mac, const uint8_t *flags,
                         const double u0[3], cudaStream_t s) {
     return prec == 0 ? launch_init_p0(Q, p, dst, mac, flags, u0, s) : launch_init_p12(Q, prec, p, dst, mac, flags, u0, s);
@@ -950,6 +969,50 @@ int lbm_get_populations(lbm_domain *D, double *out) {
     if (e == cudaSuccess) e = cudaMemcpy(out, tmp, n * sizeof(double), cudaMemcpyDeviceToHost);
     D->release(tmp);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("populations: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+// cells per staging chunk of lbm_set_populations / lbm_get_macros
+constexpr long long IO_CHUNK = 1ll << 22;
+
+int lbm_set_populations(lbm_domain *D, const double *f) {
+    if (!D || !f) return fail(LBM_ERR_ARG, "invalid arguments");
+    const long long N = D->p.N, chunk = std::min(N, IO_CHUNK);
+    double *stage = (double *)D->alloc((size_t)chunk * D->Q * sizeof(double));
+    if (!stage) return fail(LBM_ERR_OOM, "temporary staging buffer");
+    cudaError_t e = cudaStreamSynchronize(D->s);
+    for (long long c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+        const long long n = std::min(chunk, N - c0);
+        for (int i = 0; i < D->Q && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(stage + (long long)i * n, f + (long long)i * N + c0, (size_t)n * sizeof(double),
+                                cudaMemcpyHostToDevice, D->s);
+        if (e == cudaSuccess)
+            e = launch_load(D->Q, D->prec, D->p, stage, c0, n, D->pop[D->t & 1], D->mac[D->t & 1], D->flags, D->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(D->s); // the stage is reused by the next chunk
+    }
+    D->release(stage);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("set populations: ") + cudaGetErrorString(e));
+    D->h2d += N * D->Q * (long long)sizeof(double);
+    return LBM_OK;
+}
+
+int lbm_get_macros(lbm_domain *D, double *out) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    const long long N = D->p.N, chunk = std::min(N, IO_CHUNK);
+    double *stage = (double *)D->alloc((size_t)chunk * 4 * sizeof(double));
+    if (!stage) return fail(LBM_ERR_OOM, "temporary staging buffer");
+    cudaError_t e = cudaSuccess;
+    for (long long c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+        const long long n = std::min(chunk, N - c0);
+        e = launch_macros(D->Q, D->prec, D->p, D->pop[D->t & 1], D->owner[D->t & 1], c0, n, stage, D->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(D->s);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = cudaMemcpy(out + (long long)k * N + c0, stage + (long long)k * n, (size_t)n * sizeof(double),
+                           cudaMemcpyDeviceToHost);
+    }
+    D->release(stage);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("macros: ") + cudaGetErrorString(e));
+    D->d2h += N * 4 * (long long)sizeof(double);
     return LBM_OK;
 }
 

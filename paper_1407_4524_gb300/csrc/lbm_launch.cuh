@@ -27,6 +27,22 @@ cudaError_t init_t(const Params &p, void *dst, void *mac, const uint8_t *flags, 
     return cudaGetLastError();
 }
 
+template <class L, class P>
+cudaError_t load_t(const Params &p, const double *stage, long long c0, long long n, void *dst, void *mac,
+                   const uint8_t *flags, cudaStream_t s) {
+    const unsigned grid = (unsigned)((n + BULK_THREADS - 1) / BULK_THREADS);
+    k_load<L, P><<<grid, BULK_THREADS, 0, s>>>(p, stage, c0, n, (typename P::S *)dst, (typename P::C *)mac, flags);
+    return cudaGetLastError();
+}
+
+template <class L, class P>
+cudaError_t macros_t(const Params &p, const void *src, const uint16_t *owner, long long c0, long long n, double *out,
+                     cudaStream_t s) {
+    const unsigned grid = (unsigned)((n + BULK_THREADS - 1) / BULK_THREADS);
+    k_macros<L, P><<<grid, BULK_THREADS, 0, s>>>(p, (const typename P::S *)src, owner, c0, n, out);
+    return cudaGetLastError();
+}
+
 template <class L, class P> cudaError_t links_t(const Params &p, const StepBufs &sb, int grid, cudaStream_t s) {
     if (p.nb == 0 || grid <= 0) return cudaSuccess;
     k_links<L, P><<<grid, LINK_THREADS, 0, s>>>(p, sb);

@@ -667,6 +667,67 @@ __global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
 }
 
+// f(x, t) given on the host (FP64, staged as [Q][n] for the cells c0 ..
+// c0 + n - 1): moments (kept at the FL_MAC nodes in FP64 mode), collision,
+// store of fhat(x, t) -- the state the next step starts from, as after k_init
+template <class L, class P>
+__global__ void __launch_bounds__(BULK_THREADS) k_load(Params p, const double *__restrict__ stage, long long c0,
+                                                       long long n, typename P::S *__restrict__ dst,
+                                                       typename P::C *__restrict__ mac,
+                                                       const uint8_t *__restrict__ flags) {
+    using C = typename P::C;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long cell = c0 + k;
+    C f[L::Q];
+    if constexpr (P::exact) {
+        for (int i = 0; i < L::Q; ++i) f[i] = stage[(long long)i * n + k];
+        double rho, u[3];
+        moments_x<L>(p, f, rho, u);
+        if (flags[cell] & FL_MAC) {
+            mac[4 * cell] = rho;
+            mac[4 * cell + 1] = u[0];
+            mac[4 * cell + 2] = u[1];
+            mac[4 * cell + 3] = u[2];
+        }
+        collide_x<L>(p, f, rho, u);
+    } else {
+        for (int i = 0; i < L::Q; ++i) f[i] = (float)(stage[(long long)i * n + k] - L::template w<double>(i));
+        float drho, u[3];
+        moments_f<L>(p, f, drho, u);
+        collide_f<L>(p, f, drho, u);
+    }
+    for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
+}
+
+// rho(x, t), u(x, t) of the cells c0 .. c0 + n - 1 from the stored fhat(x, t):
+// the collision keeps rho and adds the body force g to sum_i c_i f_i, so
+// rho_u u = sum_i c_i fhat_i - g/2 (rho_u = rho0, or rho in the standard
+// model); out[4][n], zero at solid nodes
+template <class L, class P>
+__global__ void __launch_bounds__(BULK_THREADS) k_macros(Params p, const typename P::S *__restrict__ src,
+                                                         const uint16_t *__restrict__ owner, long long c0,
+                                                         long long n, double *__restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long cell = c0 + k;
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    if (owner[cell] == 0) { // fluid at t
+        for (int i = 0; i < L::Q; ++i) {
+            double v = (double)ldS(src + (long long)i * p.N + cell);
+            if constexpr (!P::exact) v += L::template w<double>(i);
+            r += v;
+            j[0] += (double)L::cx(i) * v;
+            j[1] += (double)L::cy(i) * v;
+            j[2] += (double)L::cz(i) * v;
+        }
+        const double den = p.eq == 0 ? p.rho0 : r;
+        for (int a = 0; a < 3; ++a) j[a] = (j[a] - 0.5 * p.g[a]) / den;
+    }
+    out[k] = r;
+    for (int a = 0; a < 3; ++a) out[(long long)(a + 1) * n + k] = j[a];
+}
+
 // pull-stream + moments + BGK collision of one node (x, y, z)
 template <class L, class P, int FM = FM_GENERAL>
 __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *__restrict__ src,

@@ -96,6 +96,8 @@ def load(build_if_missing: bool = True):
     lib.lbm_get_force_torque.argtypes = [P, C.c_int64, C.c_int64, C.c_int, P]
     lib.lbm_get_series.argtypes = [P, C.c_int64, C.c_int64, P]
     lib.lbm_get_populations.argtypes = [P, P]
+    lib.lbm_set_populations.argtypes = [P, P]
+    lib.lbm_get_macros.argtypes = [P, P]
     lib.lbm_get_solid.argtypes = [P, P]
     lib.lbm_get_body_state.argtypes = [P, P]
     lib.lbm_get_stats.argtypes = [P, C.POINTER(lbm_stats)]
@@ -315,6 +317,19 @@ class Domain:
         _check(self.lib.lbm_get_populations(self.h, out.ctypes.data))
         nx, ny, nz = self.shape
         return out.reshape(self.q, nz, ny, nx)
+
+    def set_populations(self, f: np.ndarray):
+        """set f(t) (pre-collision, FP64, shape [Q, nz, ny, nx] or [Q, N]); the
+        library collides it into the state the next step starts from"""
+        a = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.q, self.N))
+        _check(self.lib.lbm_set_populations(self.h, a.ctypes.data))
+
+    def macros(self) -> np.ndarray:
+        """rho, u_x, u_y, u_z at t, shape [4, nz, ny, nx] (zero at solid nodes)"""
+        out = np.empty(4 * self.N)
+        _check(self.lib.lbm_get_macros(self.h, out.ctypes.data))
+        nx, ny, nz = self.shape
+        return out.reshape(4, nz, ny, nx)
 
     def body_state(self) -> np.ndarray:
         """[n_bodies, 9]: X(t), U(t), W(t)"""
