@@ -67,11 +67,19 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
     const S *src = (const S *)sb.src;
     S *dst = (S *)sb.dst;
     const long long N = p.N;
-    if (a.owner_t[cell] != 0) return; // warp-uniform
     int x, y, z;
     coords_of(p, cell, x, y, z);
-    const long long sc = i == 0 ? cell : nbr<L>(p, x, y, z, i, 1);
+    const long long sc = i == 0 ? cell : nbr<L>(p, x, y, z, i, 1);      // pull source x - c_i
+    const long long G = act && i > 0 ? nbr<L>(p, x, y, z, ib, 1) : -1; // x + c_i
+    // every load that depends on the node alone is issued here, together:
+    // the owners at t (node, pull sources, x + c_i) and t+1, fhat(x, t) and
+    // the pulled fhat_i(x - c_i, t) (not used where x - c_i is solid)
+    const uint16_t own = a.owner_t[cell], own1 = a.owner_t1[cell];
     const uint16_t o = (act && i > 0 && sc >= 0) ? a.owner_t[sc] : (uint16_t)0;
+    const uint16_t oG = G >= 0 ? a.owner_t[G] : (uint16_t)1;
+    const float fo = act ? ldP(src + (long long)i * N + cell) : 0.0f;
+    const float fp = (act && sc >= 0) ? ldS(src + (long long)i * N + sc) : 0.0f;
+    if (own != 0) return; // warp-uniform
     if (from_static) { // a moving body next to it: that body's list has it
         const bool mv = o != 0 && a.bodies[o - 1].moving;
         if (__any_sync(0xffffffffu, mv)) return;
@@ -79,7 +87,6 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
     const unsigned cutmask = __ballot_sync(0xffffffffu, o != 0);
     if (!cutmask) return;
     // moments of the collided populations fhat(x, t) (= those of f(x, t))
-    const float fo = act ? ldP(src + (long long)i * N + cell) : 0.0f;
     const float drF = warp_sum(fo);
     float uF[3];
     {
@@ -129,8 +136,7 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
         float ubf[3], chi;
         if (dl < 0.5f) {
             // u_bf = u_G = u(x_F + c_i, t), chi = (2 Delta - 1)/(tau - 2)
-            const long long G = nbr<L>(p, x, y, z, ib, 1); // x - c_ib = x + c_i
-            if (G >= 0 && a.owner_t[G] == 0) {
+            if (G >= 0 && oG == 0) { // x + c_i fluid at t
                 float drG;
                 moments_hat<L>(p, src, G, drG, ubf);
                 chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
@@ -173,12 +179,11 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
         v[10] = d[2] * m0 - d[0] * m2;
         v[11] = d[0] * m1 - d[1] * m0;
     } else if (act) {
-        fi = sc >= 0 ? ldS(src + (long long)i * N + sc)
-                     : pull_edge<L, P>(p, src, (const float *)nullptr, x, y, z, cell, i);
+        fi = sc >= 0 ? fp : pull_edge<L, P>(p, src, (const float *)nullptr, x, y, z, cell, i);
     }
     // collision (or the streamed values of a node covered at t+1)
     float out = fi;
-    if (a.owner_t1[cell] == 0) {
+    if (own1 == 0) {
         const float dr = warp_sum(fi);
         float j0 = warp_sum(cxi * fi), j1 = warp_sum(cyi * fi), j2 = warp_sum(czi * fi);
         if (p.has_force) {

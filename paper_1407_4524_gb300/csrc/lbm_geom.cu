@@ -464,18 +464,30 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
             if (g.owner_t1[rc.cell]) {
                 nf = FL_SOLID;
             } else {
-                unsigned one = 0;
-                int minmov = 1 << 20;
+                unsigned one = 0, lowest = 0xffffu;
+                bool mine = false;
 #pragma unroll
                 for (int i = 1; i < L::Q; ++i) {
                     const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
                     const unsigned o = a >= 0 ? g.owner_t1[a] : 0u;
                     one |= o;
-                    if (o && g.bodies[o - 1].moving) minmov = min(minmov, (int)o);
+                    mine |= o == (unsigned)(b + 1);
+                    if (o && o < lowest) lowest = o;
                 }
                 nf = one ? FL_BND : 0;
-                // boundary node of t+1 next to a moving body: listed by the lowest one
-                if (minmov == b + 1 && dist <= Rout + 1.5f) {
+                // boundary node of t+1 next to a moving body: listed by the
+                // lowest-numbered moving one (this body is moving; a
+                // lower-numbered neighbour body is looked up only if present)
+                bool list = mine && dist <= Rout + 1.5f;
+                if (list && lowest < (unsigned)(b + 1)) {
+#pragma unroll
+                    for (int i = 1; i < L::Q; ++i) {
+                        const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                        const unsigned o = a >= 0 ? g.owner_t1[a] : 0u;
+                        if (o && o < (unsigned)(b + 1) && g.bodies[o - 1].moving) list = false;
+                    }
+                }
+                if (list) {
                     const unsigned long long at = atomicAdd(g.bn_mov_cnt, 1ull);
                     if ((long long)at < g.bn_mov_cap) g.bn_mov[at] = (uint32_t)rc.cell;
                 }
