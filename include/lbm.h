@@ -236,7 +236,10 @@ int lbm_set_bodies(lbm_domain *dom, const lbm_body *host_bodies, int n);
 /* Replace the motion of existing bodies between steps (free-body coupling):
  * new X0, U, W, t0 for each body; shape and R must stay the same.  The pose
  * at the current step must equal the pose the domain already holds within
- * 1e-9 cells (the solid set at t does not jump); LBM_ERR_ARG otherwise. */
+ * 1e-9 cells (the solid set at t does not jump); LBM_ERR_ARG otherwise.  The
+ * records go to the device through pinned staging in stream order after the
+ * steps already enqueued: the call does not wait for them (unless a body
+ * starts or stops moving, which rebuilds the body maps and synchronises). */
 int lbm_update_bodies(lbm_domain *dom, const lbm_body *host_bodies, int n);
 
 /* Advance n steps, asynchronously on the domain's stream.  Step t -> t+1
@@ -246,8 +249,12 @@ int lbm_step(lbm_domain *dom, int n);
 
 /* Copy series rows [first, first+count) of every body into host memory:
  * out[count][n_bodies][6] = (Fx, Fy, Fz, Tx, Ty, Tz) in form `kind`
- * (LBM_FT_*).  Synchronises.  Rows older than the ring capacity are gone
- * (LBM_ERR_ARG). */
+ * (LBM_FT_*).  Waits only for the steps that wrote those rows (the end of
+ * the lbm_step call that reached step first+count), so steps enqueued after
+ * them keep running: reading the row of step t after enqueuing step t+1
+ * overlaps the copy with the GPU's work.  Rows older than the ring capacity
+ * are gone (LBM_ERR_ARG).  LBM_ERR_UNSTABLE / LBM_ERR_TIMEOUT / LBM_ERR_STATE
+ * report a flag the device set in any step so far. */
 int lbm_get_force_torque(lbm_domain *dom, int64_t first, int64_t count, int kind, double *out);
 
 /* Raw series rows: out[count][n_bodies][LBM_SERIES_ROW]. */

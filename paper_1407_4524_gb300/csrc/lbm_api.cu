@@ -150,6 +150,20 @@ struct lbm_domain {
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
+    // reads of the force series wait for the step that wrote the rows (an
+    // event recorded at the end of each lbm_step call, with the step count
+    // reached) on their own non-blocking stream, not for the whole stream:
+    // the caller may enqueue step t+1 before reading the row of step t
+    static constexpr int N_STEP_EV = 8;
+    cudaStream_t sio = nullptr;
+    cudaEvent_t step_ev[N_STEP_EV] = {};
+    int64_t step_ev_t[N_STEP_EV] = {};
+    int step_ev_next = 0;
+    // body records staged in pinned memory for lbm_update_bodies (two, each
+    // reused once its copy has completed)
+    BodyDev *hbd_pin[2] = {nullptr, nullptr};
+    cudaEvent_t up_ev[2] = {nullptr, nullptr};
+    int up_k = 0;
 
     void *alloc(size_t n) {
         if (n == 0) n = 256;
@@ -187,6 +201,12 @@ template <class T> int alloc_t(lbm_domain *D, T **slot, size_t count, std::vecto
 void free_body_buffers(lbm_domain *D) {
     for (void *ptr : D->body_allocs) D->release(ptr);
     D->body_allocs.clear();
+    for (int k = 0; k < 2; ++k) { // pinned body staging: sized for the body count it was made for
+        if (!D->hbd_pin[k]) continue;
+        cudaEventSynchronize(D->up_ev[k]);
+        cudaFreeHost(D->hbd_pin[k]);
+        D->hbd_pin[k] = nullptr;
+    }
     D->dbodies = nullptr;
     D->dmoving = nullptr;
     D->chunk_all = D->chunk_mov = nullptr;
@@ -405,8 +425,16 @@ int init_populations(lbm_domain *D) {
     return LBM_OK;
 }
 
+// body records -> device through a pinned staging buffer, in stream order
+// after the steps already enqueued (no host synchronisation)
 int upload_body_array(lbm_domain *D) {
-    CK(cudaMemcpyAsync(D->dbodies, D->hbd.data(), sizeof(BodyDev) * D->nb, cudaMemcpyHostToDevice, D->s));
+    const int k = D->up_k;
+    D->up_k ^= 1;
+    if (!D->hbd_pin[k]) CK(cudaMallocHost((void **)&D->hbd_pin[k], sizeof(BodyDev) * (size_t)std::max(D->nb, 1)));
+    CK(cudaEventSynchronize(D->up_ev[k])); // the copy that last read this buffer is done
+    std::memcpy(D->hbd_pin[k], D->hbd.data(), sizeof(BodyDev) * D->nb);
+    CK(cudaMemcpyAsync(D->dbodies, D->hbd_pin[k], sizeof(BodyDev) * D->nb, cudaMemcpyHostToDevice, D->s));
+    CK(cudaEventRecord(D->up_ev[k], D->s));
     D->h2d += (long long)(sizeof(BodyDev) * D->nb);
     return LBM_OK;
 }
@@ -711,8 +739,16 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     if ((e = cudaStreamCreateWithPriority(&D->s2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&D->ev_prep, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&D->ev_links, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&D->ev_side, cudaEventDisableTiming)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&D->ev_side, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&D->sio, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&D->up_ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&D->up_ev[1], cudaEventDisableTiming)) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e)));
+    for (int k = 0; k < lbm_domain::N_STEP_EV; ++k) {
+        if ((e = cudaEventCreateWithFlags(&D->step_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(fail(LBM_ERR_CUDA, std::string("event creation: ") + cudaGetErrorString(e)));
+        D->step_ev_t[k] = -1;
+    }
     if ((e = launch_flags_full(D->Q, p, D->owner[0], D->flags, D->s)) != cudaSuccess)
         return bail(fail(LBM_ERR_CUDA, std::string("flags: ") + cudaGetErrorString(e)));
     if ((rc = init_populations(D))) return bail(rc);
@@ -741,6 +777,16 @@ int lbm_destroy_domain(lbm_domain *D) {
     if (D->ev_prep) cudaEventDestroy(D->ev_prep);
     if (D->ev_links) cudaEventDestroy(D->ev_links);
     if (D->ev_side) cudaEventDestroy(D->ev_side);
+    if (D->sio) {
+        cudaStreamSynchronize(D->sio);
+        cudaStreamDestroy(D->sio);
+    }
+    for (int k = 0; k < lbm_domain::N_STEP_EV; ++k)
+        if (D->step_ev[k]) cudaEventDestroy(D->step_ev[k]);
+    for (int k = 0; k < 2; ++k) {
+        if (D->up_ev[k]) cudaEventDestroy(D->up_ev[k]);
+        if (D->hbd_pin[k]) cudaFreeHost(D->hbd_pin[k]);
+    }
     delete D;
     return LBM_OK;
 }
@@ -868,7 +914,8 @@ int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
                 return fail(LBM_ERR_ARG, "bodies may not translate along a non-periodic axis");
         }
     }
-    CK(cudaStreamSynchronize(D->s));
+    // no host synchronisation: the new records reach the device in stream
+    // order after the steps already enqueued (upload_body_array)
     const int cur = (int)(D->t & 1), nxt = cur ^ 1;
     bool maps_changed = false;
     for (int b = 0; b < n; ++b) {
@@ -908,18 +955,44 @@ int lbm_step(lbm_domain *D, int n) {
         int rc = do_step(D);
         if (rc) return rc;
     }
+    if (n > 0) { // the steps up to D->t are done when this event is
+        const int k = D->step_ev_next;
+        CK(cudaEventRecord(D->step_ev[k], D->s));
+        D->step_ev_t[k] = D->t;
+        D->step_ev_next = (k + 1) % lbm_domain::N_STEP_EV;
+    }
     return LBM_OK;
 }
+
+namespace {
+// Makes D->sio wait until the steps before `t_end` are complete: on the
+// earliest recorded step event that covers them, else on all of D->s.
+int wait_steps(lbm_domain *D, int64_t t_end) {
+    int best = -1;
+    for (int k = 0; k < lbm_domain::N_STEP_EV; ++k)
+        if (D->step_ev_t[k] >= t_end && (best < 0 || D->step_ev_t[k] < D->step_ev_t[best])) best = k;
+    if (best >= 0) {
+        CK(cudaStreamWaitEvent(D->sio, D->step_ev[best], 0));
+    } else {
+        CK(cudaStreamSynchronize(D->s));
+    }
+    return LBM_OK;
+}
+} // namespace
 
 int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
     if (!D || !out || first < 0 || count < 0) return fail(LBM_ERR_ARG, "invalid arguments");
     if (first + count > D->t) return fail(LBM_ERR_ARG, "rows beyond the current step");
     if (first < D->t - D->series_cap) return fail(LBM_ERR_ARG, "rows older than the series ring");
     if (D->nb == 0 || count == 0) return LBM_OK;
-    CK(cudaStreamSynchronize(D->s));
+    int wrc = wait_steps(D, first + count);
+    if (wrc) return wrc;
     {
+        // sticky flags: a flag a later step (still running) sets may show up
+        // here already
         unsigned long long flags[3] = {0, 0, 0}; // unstable, timeout, free body out of range
-        CK(cudaMemcpy(flags, D->counters + 5, sizeof(flags), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(flags, D->counters + 5, sizeof(flags), cudaMemcpyDeviceToHost, D->sio));
+        CK(cudaStreamSynchronize(D->sio));
         if (flags[1]) return fail(LBM_ERR_TIMEOUT, "a stream-collide block gave up waiting for its staged rows");
         if (flags[0])
             return fail(LBM_ERR_UNSTABLE, "the solve went unstable (NaN or |u| > 0.3 at a boundary node, or a "
@@ -933,10 +1006,12 @@ int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
     while (done < count) {
         int64_t r = (first + done) % D->series_cap;
         int64_t m = std::min<int64_t>(count - done, D->series_cap - r);
-        CK(cudaMemcpy(out + done * row, D->series + r * row, m * row * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(out + done * row, D->series + r * row, m * row * sizeof(double), cudaMemcpyDeviceToHost,
+                           D->sio));
         D->d2h += (long long)(m * row * sizeof(double));
         done += m;
     }
+    CK(cudaStreamSynchronize(D->sio));
     return LBM_OK;
 }
 
