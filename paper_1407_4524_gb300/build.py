@@ -1,9 +1,12 @@
 """Build liblbm.so (the CUDA library behind include/lbm.h) for sm_103a.
 
 Each translation unit is compiled by its own nvcc process (in parallel), then
-linked into ``paper_1407_4524_gb300/_build/liblbm.so``.  Every unit uses
-``--fmad=false``: the FP64 mode reproduces fixed operation orders, and the
-FP32 path requests its fused multiply-adds explicitly.
+linked into ``paper_1407_4524_gb300/_build/liblbm.so``.  The FP64 mode, the
+geometry and the host side are built with ``--fmad=false`` (the FP64 mode
+reproduces fixed operation orders, and the geometry decides solid / fluid in
+the oracle's arithmetic); the reduced-precision units (lbm_fp32.cu,
+lbm_batch.cu) let the compiler contract, and the FP64 decisions made there
+(the direction of the extrapolation refill) use explicitly rounded operations.
 """
 from __future__ import annotations
 
@@ -19,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
 SOURCES = ["lbm_api.cu", "lbm_geom.cu", "lbm_fp64.cu", "lbm_fp32.cu", "lbm_batch.cu"]
+CONTRACT = ("lbm_fp32.cu", "lbm_batch.cu")  # reduced-precision units: FP contraction allowed
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -54,7 +58,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        c = list(common)
+        if src in CONTRACT:
+            c[c.index("--fmad=false")] = "--fmad=true"
+        cmd = [nvcc] + c + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -1215,6 +1215,11 @@ struct lbm_batch {
     cudaStream_t s = nullptr, s2 = nullptr;
     bool own_s = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // extra capture streams: the bulk kernels of different groups run on
+    // parallel branches of the tick graph (their solves are disjoint)
+    static constexpr int NBRANCH = 3;
+    cudaStream_t sb[NBRANCH] = {};
+    cudaEvent_t ev_branch[NBRANCH] = {};
     int tpl = 32;
     int side_blocks = 0;
     int64_t used = 0;
@@ -1396,15 +1401,29 @@ int batch_rebuild(lbm_batch *B) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
+    // one tick: fork; the boundary kernels of every group on the high-priority
+    // branch, the bulk kernel of each group on a branch of its own (groups
+    // beyond the branches share them); join; end-of-tick kernel
+    int ngrp = 0;
+    for (int k = 0; k < NG; ++k) ngrp += B->g[k].nslots ? 1 : 0;
+    const int nbr = std::min(ngrp, lbm_batch::NBRANCH + 1); // branch 0 is B->s itself
     for (int t = 0; t < B->tpl && e == cudaSuccess; ++t) {
         if ((e = cudaEventRecord(B->ev_fork, B->s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(B->s2, B->ev_fork, 0)) != cudaSuccess) break;
+        for (int b = 1; b < nbr && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(B->sb[b - 1], B->ev_fork, 0);
+        int gi = 0;
         for (int k = 0; k < NG && e == cudaSuccess; ++k) {
             const auto &G = B->g[k];
             if (G.nslots == 0) continue;
             if (G.grid > 0)
                 e = launch_bbnd(G.Q, G.prec, B->dsolves, G.slots, G.node_pre, G.nslots, G.grid, B->s2);
-            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.kind, G.fm, B->dsolves, G.work, G.nwork, B->s);
+            const int b = gi++ % nbr;
+            cudaStream_t bs = b == 0 ? B->s : B->sb[b - 1];
+            if (e == cudaSuccess) e = launch_bbulk(G.Q, G.kind, G.fm, B->dsolves, G.work, G.nwork, bs);
+        }
+        for (int b = 1; b < nbr && e == cudaSuccess; ++b) {
+            if ((e = cudaEventRecord(B->ev_branch[b - 1], B->sb[b - 1])) != cudaSuccess) break;
+            e = cudaStreamWaitEvent(B->s, B->ev_branch[b - 1], 0);
         }
         if (e != cudaSuccess) break;
         if ((e = cudaEventRecord(B->ev_join, B->s2)) != cudaSuccess) break;
@@ -1456,6 +1475,10 @@ int lbm_batch_create(const lbm_batch_desc *desc, lbm_batch **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&B->s2, cudaStreamNonBlocking, prio_hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming);
+    for (int k = 0; k < lbm_batch::NBRANCH && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&B->sb[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_branch[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         lbm_batch_destroy(B);
         return fail(LBM_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
@@ -1484,6 +1507,10 @@ int lbm_batch_destroy(lbm_batch *B) {
     B->release(B->dsolves);
     if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     if (B->ev_join) cudaEventDestroy(B->ev_join);
+    for (int k = 0; k < lbm_batch::NBRANCH; ++k) {
+        if (B->ev_branch[k]) cudaEventDestroy(B->ev_branch[k]);
+        if (B->sb[k]) cudaStreamDestroy(B->sb[k]);
+    }
     if (B->s2) cudaStreamDestroy(B->s2);
     if (B->own_s && B->s) cudaStreamDestroy(B->s);
     delete B;

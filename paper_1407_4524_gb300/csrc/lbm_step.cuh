@@ -1089,15 +1089,17 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
 template <class L>
 __device__ __forceinline__ int extrap_cells(const Params &p, const BodyDev &B, const double *X1, const uint16_t *owner_t,
                                             int x, int y, int z, long long cells[3]) {
+    // every product and sum explicitly rounded (no contraction, whatever the
+    // unit's build flags): the choice of c* is the oracle's
     double r1[3], n[3];
     disp(p, X1, x, y, z, r1);
     if (B.shape == 2) {
         const double co = X1[15], si = X1[16]; // orientation at t+1
-        double xi, eta;
-        body_axes(co, si, r1[0], r1[1], xi, eta);
-        const double gx = xi / (B.R * B.R), gy = eta / (B.R2 * B.R2);
-        n[0] = co * gx - si * gy;
-        n[1] = si * gx + co * gy;
+        const double xi = __dadd_rn(__dmul_rn(co, r1[0]), __dmul_rn(si, r1[1]));
+        const double eta = __dsub_rn(__dmul_rn(co, r1[1]), __dmul_rn(si, r1[0]));
+        const double gx = __ddiv_rn(xi, __dmul_rn(B.R, B.R)), gy = __ddiv_rn(eta, __dmul_rn(B.R2, B.R2));
+        n[0] = __dsub_rn(__dmul_rn(co, gx), __dmul_rn(si, gy));
+        n[1] = __dadd_rn(__dmul_rn(si, gx), __dmul_rn(co, gy));
         n[2] = 0.0;
     } else {
         n[0] = r1[0];
@@ -1108,9 +1110,10 @@ __device__ __forceinline__ int extrap_cells(const Params &p, const BodyDev &B, c
     double top = 0.0;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        const double sdot = ((double)L::cx(i) * n[0] + (double)L::cy(i) * n[1]) + (double)L::cz(i) * n[2];
+        const double sdot = __dadd_rn(__dadd_rn(__dmul_rn((double)L::cx(i), n[0]), __dmul_rn((double)L::cy(i), n[1])),
+                                      __dmul_rn((double)L::cz(i), n[2]));
         const int len2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
-        const double score = len2 == 1 ? sdot : sdot * 0.70710678118654752440;
+        const double score = len2 == 1 ? sdot : __dmul_rn(sdot, 0.70710678118654752440);
         if (best == 0 || score > top) {
             best = i;
             top = score;
