@@ -393,13 +393,19 @@ BULK_SOURCES = ("lbm_dev.cuh", "lbm_step.cuh", "lbm_launch.cuh", "lbm_stage.cuh"
 
 
 def _kernel_rev() -> str:
-    """hash of the stream-collide kernel's sources the traffic figure was taken on"""
+    """hash of the stream-collide kernel's sources the traffic figure was taken
+    on (code only: comments and blank lines do not change it)"""
     import hashlib
+    import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1407_4524_gb300", "csrc")
     for f in BULK_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:12]
 
 

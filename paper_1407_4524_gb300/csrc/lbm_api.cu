@@ -4,11 +4,18 @@
 // buffers (rho,u at the nodes flagged FL_MAC), the node flags, two owner
 // arrays (solid owner at t and t+1), two cut-link buffers (t and t+1), the
 // per-link momentum-exchange contributions, the covered/uncovered lists and
-// the force/torque ring.  lbm_step enqueues, per step:
+// the force/torque ring.  lbm_step enqueues, per step, in FP64 mode:
 //   moving bodies only: k_prep (poses, link prefixes),
 //                       k_geom_a, k_geom_b, k_geom_c  (geometry of t+1)
-//   k_links (wall values + ME per link), k_bulk (stream-collide),
-//   k_finish (per-body series row; A+/A- impulsive terms and refill).
+//   k_links (wall values + ME per link), k_bulk (stream-collide; then
+//   k_zouhe for the Zou-He face nodes), k_finish (per-body series row;
+//   A+/A- impulsive terms and refill), k_free (free bodies);
+// in the reduced-precision modes (do_step_overlapped): k_fprep on the main
+// stream, then the surface kernels (k_fgeom1/2, k_bnd, k_finish, k_free) on
+// a high-priority side stream beside k_bulk (+ k_zouhe) on the main stream.
+// Each lbm_step call ends with a step event that the series reads wait on.
+// The serving batch (lbm_batch_*) keeps solves of this kind in slots and
+// replays a CUDA graph of batched ticks (lbm_batch.cu).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -27,6 +27,11 @@
 // neighbour), which the boundary-node kernel (lbm_bnd.cuh) steps on a second
 // stream; k_finish converts the exact fixed-point per-body sums.  Storage is
 // f - w, arithmetic FP32.
+//
+// Every mode: under the Zou-He edge rule k_bulk also skips the nodes of the
+// wall and inlet faces, which k_zouhe steps (pull, closure of the entering
+// populations, collision).  k_init / k_load set the state (an equilibrium or
+// populations given on the host); k_macros reads rho, u back.
 #pragma once
 
 #include <type_traits>
