@@ -166,6 +166,19 @@ struct lbm_domain {
     cudaEvent_t step_ev[N_STEP_EV] = {};
     int64_t step_ev_t[N_STEP_EV] = {};
     int step_ev_next = 0;
+    // CUDA-graph replay: lbm_step runs GRAPH_STEPS consecutive steps (from an
+    // even step, so that the buffer parities match) as one captured graph; the
+    // step kernels read their step index from the device counter, so the same
+    // graph serves every replay.  Kernel timing inside it uses its own events.
+    static constexpr int GRAPH_STEPS = 16;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t scap = nullptr; // capture stream (the domain's stream may be the legacy default stream)
+    bool graph_dirty = true;   // capture again before the next replay
+    bool graph_failed = false; // capture not possible: plain launches only
+    bool capturing = false;
+    int cap_k = 0;             // step index within the graph being captured
+    cudaEvent_t gev[2 * GRAPH_STEPS] = {};
+    bool g_timed = false;      // a timed replay ran since the timings were last read
     // body records staged in pinned memory for lbm_update_bodies (two, each
     // reused once its copy has completed)
     BodyDev *hbd_pin[2] = {nullptr, nullptr};
@@ -464,6 +477,7 @@ int upload_bodies(lbm_domain *D) {
     for (int b = 0; b < D->nb; ++b) D->n_free += D->hbd[b].free ? 1 : 0;
     D->nchunk_all = (int)all.size();
     D->nchunk_mov = (int)mv.size();
+    D->graph_dirty = true; // launch shapes follow the body maps
     CK(cudaMemcpyAsync(D->dbodies, D->hbd.data(), sizeof(BodyDev) * D->nb, cudaMemcpyHostToDevice, D->s));
     D->h2d += (long long)(sizeof(BodyDev) * D->nb);
     if (!mov.empty()) CK(cudaMemcpyAsync(D->dmoving, mov.data(), sizeof(int) * mov.size(), cudaMemcpyHostToDevice, D->s));
@@ -487,13 +501,34 @@ int build_bnd_lists(lbm_domain *D) {
     return LBM_OK;
 }
 
+// events around the bulk kernel of this step (kernel timing): the graph's own
+// pair while a graph is captured, else the next pair of the ring
+int timing_events(lbm_domain *D, cudaEvent_t &a, cudaEvent_t &b) {
+    if (D->capturing) {
+        a = D->gev[2 * D->cap_k];
+        b = D->gev[2 * D->cap_k + 1];
+        return LBM_OK;
+    }
+    if (D->ev_used + 2 > D->ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            D->ev.push_back(e);
+        }
+    }
+    a = D->ev[D->ev_used];
+    b = D->ev[D->ev_used + 1];
+    D->ev_used += 2;
+    return LBM_OK;
+}
+
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     if (prec != LBM_FP64 && D->nb) return do_step_overlapped(D);
     if (D->nb && (D->n_moving || D->prep_dirty)) {
         // the A+/A- lists of the previous step update the solid flags of t
         CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
-                       D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
+                       D->counters + 9, D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
         D->prep_dirty = false;
     }
     if (D->n_moving) {
@@ -504,24 +539,19 @@ int do_step(lbm_domain *D) {
     }
     StepBufs sb = step_bufs(D);
     if (D->nb) CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
+    cudaEvent_t ta = nullptr, tb = nullptr;
     if (D->timing) {
-        if (D->ev_used + 2 > D->ev.size()) {
-            for (int k = 0; k < 64; ++k) {
-                cudaEvent_t e;
-                CK(cudaEventCreate(&e));
-                D->ev.push_back(e);
-            }
-        }
-        CK(cudaEventRecord(D->ev[D->ev_used], D->s));
+        int trc = timing_events(D, ta, tb);
+        if (trc) return trc;
+        CK(cudaEventRecord(ta, D->s));
     }
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
-    if (D->timing) {
-        CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
-        D->ev_used += 2;
-    }
+    if (D->timing) CK(cudaEventRecord(tb, D->s));
     if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
-    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->t, D->counters, D->s));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->s));
+    CK(launch_tick(D->counters, D->s));
     D->t += 1;
+    if (D->capturing) D->cap_k += 1;
     return LBM_OK;
 }
 
@@ -538,7 +568,8 @@ int do_step_overlapped(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     const int cur = (int)(D->t & 1), nxt = cur ^ 1;
     if (D->n_moving || D->prep_dirty || D->lists_dirty) {
-        CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->flags, D->chg_cnt, D->chg_cell, D->chg_val, D->chg_cap,
+        CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->counters + 9, D->flags, D->chg_cnt, D->chg_cell,
+                        D->chg_val, D->chg_cap,
                         D->apm_cnt, D->bn_cnt + 1 + nxt, D->s));
         D->prep_dirty = false;
     }
@@ -572,25 +603,20 @@ int do_step_overlapped(lbm_domain *D) {
     ba.poses = D->poses;
     CK(launch_bnd(Q, prec, D->p, ba, sb, D->side_serial ? D->bnd_grid_full : D->bnd_grid, ss));
     CK(launch_finish(Q, prec, D->p, sb, ss));
-    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->t, D->counters, ss));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, ss));
     if (!D->side_serial) CK(cudaEventRecord(D->ev_side, D->s2));
+    cudaEvent_t ta = nullptr, tb = nullptr;
     if (D->timing) {
-        if (D->ev_used + 2 > D->ev.size()) {
-            for (int k = 0; k < 64; ++k) {
-                cudaEvent_t e;
-                CK(cudaEventCreate(&e));
-                D->ev.push_back(e);
-            }
-        }
-        CK(cudaEventRecord(D->ev[D->ev_used], D->s));
+        int trc = timing_events(D, ta, tb);
+        if (trc) return trc;
+        CK(cudaEventRecord(ta, D->s));
     }
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
-    if (D->timing) {
-        CK(cudaEventRecord(D->ev[D->ev_used + 1], D->s));
-        D->ev_used += 2;
-    }
+    if (D->timing) CK(cudaEventRecord(tb, D->s));
     if (!D->side_serial) CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
+    CK(launch_tick(D->counters, D->s));
     D->t += 1;
+    if (D->capturing) D->cap_k += 1;
     return LBM_OK;
 }
 
@@ -790,6 +816,10 @@ int lbm_destroy_domain(lbm_domain *D) {
     }
     for (int k = 0; k < lbm_domain::N_STEP_EV; ++k)
         if (D->step_ev[k]) cudaEventDestroy(D->step_ev[k]);
+    if (D->gexec) cudaGraphExecDestroy(D->gexec);
+    for (int k = 0; k < 2 * lbm_domain::GRAPH_STEPS; ++k)
+        if (D->gev[k]) cudaEventDestroy(D->gev[k]);
+    if (D->scap) cudaStreamDestroy(D->scap);
     for (int k = 0; k < 2; ++k) {
         if (D->up_ev[k]) cudaEventDestroy(D->up_ev[k]);
         if (D->hbd_pin[k]) cudaFreeHost(D->hbd_pin[k]);
@@ -806,6 +836,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if (rc) return rc;
     CK(cudaStreamSynchronize(D->s));
     free_body_buffers(D);
+    D->graph_dirty = true;
     D->nb = n;
     D->p.nb = n;
     D->hb.assign(hb, hb + n);
@@ -882,7 +913,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     // solid owners at t = 0, flags, links (both buffers), initial state
     const size_t N = (size_t)D->p.N;
     CK(cudaMemsetAsync(D->owner[0], 0, N * sizeof(uint16_t), D->s));
-    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr,
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr, nullptr,
                    nullptr, nullptr, D->s));
     GeomArgs g = geom_args(D, false);
     CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
@@ -898,7 +929,7 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
         CK(cudaMemcpyAsync(D->link_cnt[1], D->link_cnt[0], nbx * sizeof(long long), cudaMemcpyDeviceToDevice,
                            D->s));
     }
-    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr,
+    CK(launch_prep(D->p, D->dbodies, D->link_cnt[0], D->link_pre, D->tile_pre, D->poses, 0, nullptr, nullptr, nullptr,
                    nullptr, nullptr, D->s));
     D->prep_dirty = false;
     if ((rc = init_populations(D))) return rc;
@@ -955,12 +986,73 @@ int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     return upload_body_array(D);
 }
 
+namespace {
+// Capture GRAPH_STEPS steps from the current (even) step into D->gexec.  The
+// captured steps do not run: D->t is restored.
+int capture_graph(lbm_domain *D) {
+    if (D->gexec) {
+        cudaGraphExecDestroy(D->gexec);
+        D->gexec = nullptr;
+    }
+    for (int k = 0; k < 2 * lbm_domain::GRAPH_STEPS; ++k)
+        if (!D->gev[k]) CK(cudaEventCreate(&D->gev[k]));
+    if (!D->scap && cudaStreamCreateWithFlags(&D->scap, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        D->graph_failed = true;
+        return LBM_OK;
+    }
+    const int64_t t0 = D->t;
+    cudaStream_t user = D->s;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(D->scap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        D->graph_failed = true;
+        return LBM_OK;
+    }
+    D->s = D->scap; // the steps are recorded, not run; the graph is launched into the domain's stream
+    D->capturing = true;
+    D->cap_k = 0;
+    int rc = LBM_OK;
+    for (int k = 0; k < lbm_domain::GRAPH_STEPS && rc == LBM_OK; ++k) rc = do_step(D);
+    cudaError_t e = cudaStreamEndCapture(D->scap, &graph);
+    D->s = user;
+    D->capturing = false;
+    D->t = t0;
+    // the side-stream kernels keep their high priority inside the graph
+    if (rc == LBM_OK && e == cudaSuccess)
+        e = cudaGraphInstantiateWithFlags(&D->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != LBM_OK || e != cudaSuccess) {
+        (void)cudaGetLastError();
+        D->gexec = nullptr;
+        D->graph_failed = true; // plain launches from now on
+        return rc != LBM_OK ? rc : fail(LBM_ERR_CUDA, std::string("step graph: ") + cudaGetErrorString(e));
+    }
+    D->graph_dirty = false;
+    return LBM_OK;
+}
+} // namespace
+
 int lbm_step(lbm_domain *D, int n) {
     if (!D || n < 0) return fail(LBM_ERR_ARG, "invalid arguments");
     CK(cudaSetDevice(D->d.device));
-    for (int k = 0; k < n; ++k) {
+    const int G = lbm_domain::GRAPH_STEPS;
+    for (int k = 0; k < n;) {
+        const bool graph = !D->graph_failed && !D->prep_dirty && !D->lists_dirty && (D->t & 1) == 0 && n - k >= G;
+        if (graph && (D->graph_dirty || !D->gexec)) {
+            int rc = capture_graph(D);
+            if (rc && !D->graph_failed) return rc;
+        }
+        if (graph && D->gexec) {
+            CK(cudaGraphLaunch(D->gexec, D->s));
+            D->t += G;
+            k += G;
+            if (D->timing) D->g_timed = true;
+            continue;
+        }
         int rc = do_step(D);
         if (rc) return rc;
+        ++k;
     }
     if (n > 0) { // the steps up to D->t are done when this event is
         const int k = D->step_ev_next;
@@ -1170,8 +1262,10 @@ int lbm_set_stream(lbm_domain *D, void *stream) {
 int lbm_set_kernel_timing(lbm_domain *D, int enable) {
     if (!D) return fail(LBM_ERR_ARG, "null domain");
     CK(cudaStreamSynchronize(D->s));
+    if (D->timing != (enable != 0)) D->graph_dirty = true; // the graph holds the timing events or not
     D->timing = enable != 0;
     D->ev_used = 0;
+    D->g_timed = false;
     return LBM_OK;
 }
 
@@ -1184,9 +1278,19 @@ int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
         CK(cudaEventElapsedTime(&ms, D->ev[k], D->ev[k + 1]));
         tot += ms;
     }
-    *launches = (int64_t)(D->ev_used / 2);
+    int64_t n = (int64_t)(D->ev_used / 2);
+    if (D->g_timed) { // the bulk kernels of the last graph replay
+        for (int k = 0; k < lbm_domain::GRAPH_STEPS; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, D->gev[2 * k], D->gev[2 * k + 1]));
+            tot += ms;
+        }
+        n += lbm_domain::GRAPH_STEPS;
+    }
+    *launches = n;
     *total_ms = tot;
     D->ev_used = 0;
+    D->g_timed = false;
     return LBM_OK;
 }
 
@@ -1197,6 +1301,8 @@ int lbm_launches_per_step(const lbm_domain *D, int *out) {
     else
         *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
     if (D->n_free) *out += 1; // free-body update
+    if (D->p.zouhe) *out += 1; // Zou-He face nodes
+    *out += 1;                 // step counter
     return LBM_OK;
 }
 
@@ -1565,7 +1671,7 @@ int lbm_batch_admit(lbm_batch *B, const lbm_domain_desc *desc, const lbm_body *h
     long long nodes = 0;
     if (n > 0) {
         // poses of t = 0 and the boundary-node list (all static)
-        cudaError_t e = launch_fprep(D->p, D->dbodies, D->poses, 0, D->flags, D->chg_cnt, D->chg_cell, D->chg_val,
+        cudaError_t e = launch_fprep(D->p, D->dbodies, D->poses, 0, nullptr, D->flags, D->chg_cnt, D->chg_cell, D->chg_val,
                                      D->chg_cap, D->apm_cnt, D->bn_cnt + 2, D->s);
         if (e == cudaSuccess && (rc = build_bnd_lists(D))) {
             lbm_destroy_domain(D);

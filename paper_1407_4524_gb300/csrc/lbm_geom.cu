@@ -124,9 +124,11 @@ __device__ void prefix_over_bodies(const Params &p, const long long *link_cnt, l
 // the solid flags of the nodes that the previous step covered (A+) or
 // uncovered (A-), so that the flags describe the solid set of step t
 __global__ void __launch_bounds__(1024) k_prep(Params p, const BodyDev *bodies, const long long *link_cnt,
-                                               long long *link_pre, long long *tile_pre, double *poses, long long t,
-                                               uint8_t *flags, const long long *apm_cnt, const uint32_t *apm_cell,
+                                               long long *link_pre, long long *tile_pre, double *poses, long long t_arg,
+                                               const unsigned long long *tdev, uint8_t *flags,
+                                               const long long *apm_cnt, const uint32_t *apm_cell,
                                                const int8_t *apm_sign) {
+    const long long t = tdev ? (long long)*tdev : t_arg; // the device step counter, when given
     if (flags) {
         for (int b = 0; b < p.nb; ++b) {
             const BodyDev &B = bodies[b];
@@ -370,10 +372,12 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
 // Reduced-precision modes.  Momentum-exchange sums are order independent
 // there (exact fixed point), so lists are appended with atomics.
 
-__global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies, double *poses, long long t,
-                                                uint8_t *flags, unsigned long long *chg_cnt, const uint32_t *chg_cell,
+__global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies, double *poses, long long t_arg,
+                                                const unsigned long long *tdev, uint8_t *flags,
+                                                unsigned long long *chg_cnt, const uint32_t *chg_cell,
                                                 const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
                                                 unsigned long long *bn_mov_next_cnt) {
+    const long long t = tdev ? (long long)*tdev : t_arg; // the device step counter, when given
     const long long n = (long long)min((unsigned long long)chg_cap, *chg_cnt);
     for (long long e = threadIdx.x; e < n; e += 1024) {
         const long long c = chg_cell[e];
@@ -547,19 +551,30 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_bnd_lists(Params p, GeomArgs g
 } // namespace
 
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
-                        long long *tile_pre, double *poses, long long t, uint8_t *flags, const long long *apm_cnt,
-                        const uint32_t *apm_cell, const int8_t *apm_sign, cudaStream_t s) {
-    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, tile_pre, poses, t, flags, apm_cnt, apm_cell,
+                        long long *tile_pre, double *poses, long long t, const unsigned long long *tdev,
+                        uint8_t *flags, const long long *apm_cnt, const uint32_t *apm_cell, const int8_t *apm_sign,
+                        cudaStream_t s) {
+    k_prep<<<1, 1024, 0, s>>>(p, bodies, link_cnt, link_pre, tile_pre, poses, t, tdev, flags, apm_cnt, apm_cell,
                               apm_sign);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t, uint8_t *flags,
-                         unsigned long long *chg_cnt, const uint32_t *chg_cell, const uint8_t *chg_val,
-                         long long chg_cap, long long *apm_cnt, unsigned long long *bn_mov_next_cnt,
-                         cudaStream_t s) {
-    k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt,
+cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t,
+                         const unsigned long long *tdev, uint8_t *flags, unsigned long long *chg_cnt,
+                         const uint32_t *chg_cell, const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
+                         unsigned long long *bn_mov_next_cnt, cudaStream_t s) {
+    k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, tdev, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt,
                                bn_mov_next_cnt);
+    return cudaGetLastError();
+}
+
+// end of a step: the device step counter (counters[9]) advances, so that the
+// kernels of the next step -- launched one by one or replayed from a graph --
+// read their step index on the device
+__global__ void k_tick(unsigned long long *counters) { counters[9] += 1ull; }
+
+cudaError_t launch_tick(unsigned long long *counters, cudaStream_t s) {
+    k_tick<<<1, 1, 0, s>>>(counters);
     return cudaGetLastError();
 }
 
@@ -647,7 +662,8 @@ static cudaError_t import_t(int prec, const Params &p, const double *in, void *p
 // theta0 = theta(t+1), t0 = t+1, so pose(t+1), pose(t+2) follow.
 // A body within 2 cells of a non-periodic face, or faster than 0.25 at its
 // surface, sets counters[7].
-__global__ void k_free(Params p, BodyDev *bodies, const double *series, long long t, unsigned long long *counters) {
+__global__ void k_free(Params p, BodyDev *bodies, const double *series, unsigned long long *counters) {
+    const long long t = (long long)counters[9]; // the device step counter
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= p.nb) return;
     BodyDev &B = bodies[b];
@@ -689,10 +705,10 @@ __global__ void k_free(Params p, BodyDev *bodies, const double *series, long lon
     if (bad) atomicOr(&counters[7], 1ull);
 }
 
-cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, long long t,
-                        unsigned long long *counters, cudaStream_t s) {
+cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, unsigned long long *counters,
+                        cudaStream_t s) {
     if (p.nb == 0) return cudaSuccess;
-    k_free<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, series, t, counters);
+    k_free<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, series, counters);
     return cudaGetLastError();
 }
 

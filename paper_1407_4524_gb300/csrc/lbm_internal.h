@@ -86,14 +86,15 @@ cudaError_t launch_finish(int Q, int prec, const Params &p, const StepBufs &sb, 
 
 // per step: wrapped poses at t and t+1 and the prefix of the link counts
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
-                        long long *tile_pre, double *poses, long long t, uint8_t *flags, const long long *apm_cnt,
-                        const uint32_t *apm_cell, const int8_t *apm_sign, cudaStream_t s);
+                        long long *tile_pre, double *poses, long long t, const unsigned long long *tdev,
+                        uint8_t *flags, const long long *apm_cnt, const uint32_t *apm_cell, const int8_t *apm_sign,
+                        cudaStream_t s);
 // reduced-precision modes: poses, and the flag changes of the previous step;
 // clears the change list and the covered/uncovered counters
-cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t, uint8_t *flags,
-                         unsigned long long *chg_cnt, const uint32_t *chg_cell, const uint8_t *chg_val,
-                         long long chg_cap, long long *apm_cnt, unsigned long long *bn_mov_next_cnt,
-                         cudaStream_t s);
+cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t,
+                         const unsigned long long *tdev, uint8_t *flags, unsigned long long *chg_cnt,
+                         const uint32_t *chg_cell, const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
+                         unsigned long long *bn_mov_next_cnt, cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,
@@ -125,8 +126,9 @@ cudaError_t launch_bfinish(SolveDev *solves, const int *slots, int nslots, cudaS
 cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStream_t s);
 
 // free bodies: Newton-Euler update after the force/torque row of step t
-cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, long long t,
-                        unsigned long long *counters, cudaStream_t s);
+cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, unsigned long long *counters,
+                        cudaStream_t s);
+cudaError_t launch_tick(unsigned long long *counters, cudaStream_t s);
 
 // population export: fhat as FP64 f (adds w back for the shifted modes)
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);

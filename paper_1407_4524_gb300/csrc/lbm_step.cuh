@@ -72,7 +72,8 @@ struct StepBufs {
     unsigned long long *counters; // [0] fallback links, [1] covered, [2] uncovered,
                                   // [3] links of this step, [4] links of the last step,
                                   // [5] unstable flag, [6] timeout flag,
-                                  // [7] free body out of range, [8] extrapolation refills
+                                  // [7] free body out of range, [8] extrapolation refills,
+                                  // [9] step counter t (advanced by k_tick)
     unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
 };
@@ -1399,6 +1400,7 @@ template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &
 // blocks [nb, nb + moving) handle the covered/uncovered nodes of one moving
 // body (they write disjoint parts of the series row)
 template <class L, class P> __global__ void __launch_bounds__(IMP_THREADS) k_finish(Params p, StepBufs sb) {
+    sb.t = (long long)sb.counters[9]; // the device step counter
     if (!P::exact && blockIdx.x == 0 && threadIdx.x == 0) {
         sb.counters[4] = sb.counters[3];
         sb.counters[3] = 0ull;

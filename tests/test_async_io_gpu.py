@@ -36,3 +36,50 @@ def test_pipelined_reads_and_updates_match_synchronous(dim, name, prec):
     assert np.array_equal(got, want)
     assert np.array_equal(dom.force_torque("lattice"), want)
     dom.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("dim,name", [("2d", "moving_cylinders_periodic"), ("2d", "zouhe_box_rotating"),
+                                      ("3d", "moving_spheres_periodic"), ("3d", "channel_sphere")])
+def test_graph_replay_matches_step_by_step(dim, name, prec):
+    """lbm_step(n) replays captured 16-step graphs (the kernels read their step
+    index on the device); one-step calls launch kernel by kernel: the results
+    are bit-identical, with and without kernel timing."""
+    from paper_1407_4524_gb300 import lbm
+    spec = dict((CASES_2D if dim == "2d" else CASES_3D)[name], precision=prec)
+    steps = 37  # a graph replay, a plain step to even parity, another replay, plain remainder
+    ref = lbm.Domain(spec, device=0)
+    for _ in range(steps):
+        ref.step(1)
+    want_ft = ref.force_torque("lattice") if ref.bodies else None
+    want_f = ref.populations()
+    ref.close()
+    for timing in (False, True):
+        dom = lbm.Domain(spec, device=0)
+        dom.set_kernel_timing(timing)
+        dom.step(1)
+        dom.step(steps - 1)
+        if timing:
+            n, ms = dom.kernel_time()
+            assert n > 0 and ms > 0.0
+        if want_ft is not None:
+            assert np.array_equal(dom.force_torque("lattice"), want_ft)
+        assert np.array_equal(dom.populations(), want_f)
+        assert dom.t == steps
+        dom.close()
+
+
+def test_free_body_graph_replay_matches():
+    from paper_1407_4524_gb300 import lbm
+    from test_free_gpu import CASES as FREE
+    name = sorted(FREE)[0]
+    spec = dict(FREE[name], precision="fp32")
+    ref = lbm.Domain(spec, device=0)
+    for _ in range(40):
+        ref.step(1)
+    want = ref.body_state()
+    ref.close()
+    dom = lbm.Domain(spec, device=0)
+    dom.step(40)
+    assert np.array_equal(dom.body_state(), want)
+    dom.close()
