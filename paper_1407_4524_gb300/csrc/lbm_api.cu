@@ -501,6 +501,12 @@ int build_bnd_lists(lbm_domain *D) {
     return LBM_OK;
 }
 
+// a timing event: while a graph is captured it must be an external event
+// record (a plain record inside a capture only orders the graph's branches)
+cudaError_t record_timing(lbm_domain *D, cudaEvent_t e) {
+    return D->capturing ? cudaEventRecordWithFlags(e, D->s, cudaEventRecordExternal) : cudaEventRecord(e, D->s);
+}
+
 // events around the bulk kernel of this step (kernel timing): the graph's own
 // pair while a graph is captured, else the next pair of the ring
 int timing_events(lbm_domain *D, cudaEvent_t &a, cudaEvent_t &b) {
@@ -543,10 +549,10 @@ int do_step(lbm_domain *D) {
     if (D->timing) {
         int trc = timing_events(D, ta, tb);
         if (trc) return trc;
-        CK(cudaEventRecord(ta, D->s));
+        CK(record_timing(D, ta));
     }
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
-    if (D->timing) CK(cudaEventRecord(tb, D->s));
+    if (D->timing) CK(record_timing(D, tb));
     if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
     if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->s));
     CK(launch_tick(D->counters, D->s));
@@ -609,10 +615,10 @@ int do_step_overlapped(lbm_domain *D) {
     if (D->timing) {
         int trc = timing_events(D, ta, tb);
         if (trc) return trc;
-        CK(cudaEventRecord(ta, D->s));
+        CK(record_timing(D, ta));
     }
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
-    if (D->timing) CK(cudaEventRecord(tb, D->s));
+    if (D->timing) CK(record_timing(D, tb));
     if (!D->side_serial) CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
     CK(launch_tick(D->counters, D->s));
     D->t += 1;
