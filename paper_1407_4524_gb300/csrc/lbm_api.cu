@@ -400,6 +400,7 @@ StepBufs step_bufs(lbm_domain *D) {
     sb.series = D->series;
     sb.counters = D->counters;
     sb.t = D->t;
+    sb.par = (int)(D->t & 1);
     return sb;
 }
 
@@ -534,7 +535,7 @@ int do_step(lbm_domain *D) {
     if (D->nb && (D->n_moving || D->prep_dirty)) {
         // the A+/A- lists of the previous step update the solid flags of t
         CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
-                       D->counters + 9, D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
+                       D->counters + 9 + (D->t & 1), D->flags, D->apm_cnt, D->apm_cell, D->apm_sign, D->s));
         D->prep_dirty = false;
     }
     if (D->n_moving) {
@@ -554,8 +555,7 @@ int do_step(lbm_domain *D) {
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
     if (D->timing) CK(record_timing(D, tb));
     if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
-    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->s));
-    CK(launch_tick(D->counters, D->s));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->counters + 9 + (D->t & 1), D->s));
     D->t += 1;
     if (D->capturing) D->cap_k += 1;
     return LBM_OK;
@@ -574,7 +574,7 @@ int do_step_overlapped(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     const int cur = (int)(D->t & 1), nxt = cur ^ 1;
     if (D->n_moving || D->prep_dirty || D->lists_dirty) {
-        CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->counters + 9, D->flags, D->chg_cnt, D->chg_cell,
+        CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->counters + 9 + (D->t & 1), D->flags, D->chg_cnt, D->chg_cell,
                         D->chg_val, D->chg_cap,
                         D->apm_cnt, D->bn_cnt + 1 + nxt, D->s));
         D->prep_dirty = false;
@@ -609,7 +609,7 @@ int do_step_overlapped(lbm_domain *D) {
     ba.poses = D->poses;
     CK(launch_bnd(Q, prec, D->p, ba, sb, D->side_serial ? D->bnd_grid_full : D->bnd_grid, ss));
     CK(launch_finish(Q, prec, D->p, sb, ss));
-    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, ss));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->counters + 9 + (D->t & 1), ss));
     if (!D->side_serial) CK(cudaEventRecord(D->ev_side, D->s2));
     cudaEvent_t ta = nullptr, tb = nullptr;
     if (D->timing) {
@@ -620,7 +620,6 @@ int do_step_overlapped(lbm_domain *D) {
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
     if (D->timing) CK(record_timing(D, tb));
     if (!D->side_serial) CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
-    CK(launch_tick(D->counters, D->s));
     D->t += 1;
     if (D->capturing) D->cap_k += 1;
     return LBM_OK;
@@ -1308,7 +1307,6 @@ int lbm_launches_per_step(const lbm_domain *D, int *out) {
         *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
     if (D->n_free) *out += 1; // free-body update
     if (D->p.zouhe) *out += 1; // Zou-He face nodes
-    *out += 1;                 // step counter
     return LBM_OK;
 }
 

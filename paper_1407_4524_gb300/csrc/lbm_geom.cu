@@ -568,15 +568,6 @@ cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, 
     return cudaGetLastError();
 }
 
-// end of a step: the device step counter (counters[9]) advances, so that the
-// kernels of the next step -- launched one by one or replayed from a graph --
-// read their step index on the device
-__global__ void k_tick(unsigned long long *counters) { counters[9] += 1ull; }
-
-cudaError_t launch_tick(unsigned long long *counters, cudaStream_t s) {
-    k_tick<<<1, 1, 0, s>>>(counters);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
     if (g.nchunks == 0) return cudaSuccess;
@@ -662,8 +653,9 @@ static cudaError_t import_t(int prec, const Params &p, const double *in, void *p
 // theta0 = theta(t+1), t0 = t+1, so pose(t+1), pose(t+2) follow.
 // A body within 2 cells of a non-periodic face, or faster than 0.25 at its
 // surface, sets counters[7].
-__global__ void k_free(Params p, BodyDev *bodies, const double *series, unsigned long long *counters) {
-    const long long t = (long long)counters[9]; // the device step counter
+__global__ void k_free(Params p, BodyDev *bodies, const double *series, unsigned long long *counters,
+                       const unsigned long long *tdev) {
+    const long long t = (long long)*tdev; // the device step index
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= p.nb) return;
     BodyDev &B = bodies[b];
@@ -706,9 +698,9 @@ __global__ void k_free(Params p, BodyDev *bodies, const double *series, unsigned
 }
 
 cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, unsigned long long *counters,
-                        cudaStream_t s) {
+                        const unsigned long long *tdev, cudaStream_t s) {
     if (p.nb == 0) return cudaSuccess;
-    k_free<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, series, counters);
+    k_free<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, series, counters, tdev);
     return cudaGetLastError();
 }
 

@@ -127,8 +127,7 @@ cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStre
 
 // free bodies: Newton-Euler update after the force/torque row of step t
 cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, unsigned long long *counters,
-                        cudaStream_t s);
-cudaError_t launch_tick(unsigned long long *counters, cudaStream_t s);
+                        const unsigned long long *tdev, cudaStream_t s);
 
 // population export: fhat as FP64 f (adds w back for the shifted modes)
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);

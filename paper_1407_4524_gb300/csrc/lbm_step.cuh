@@ -73,9 +73,11 @@ struct StepBufs {
                                   // [3] links of this step, [4] links of the last step,
                                   // [5] unstable flag, [6] timeout flag,
                                   // [7] free body out of range, [8] extrapolation refills,
-                                  // [9] step counter t (advanced by k_tick)
+                                  // [9], [10] step index t of even / odd steps (k_finish
+                                  // of step t writes t + 1 into the other one)
     unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
+    int par; // parity of the step: its index is counters[9 + par] on the device
 };
 
 // =================================================================== exact ==
@@ -1400,7 +1402,11 @@ template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &
 // blocks [nb, nb + moving) handle the covered/uncovered nodes of one moving
 // body (they write disjoint parts of the series row)
 template <class L, class P> __global__ void __launch_bounds__(IMP_THREADS) k_finish(Params p, StepBufs sb) {
-    sb.t = (long long)sb.counters[9]; // the device step counter
+    // the step index from the device (kernels replayed from a graph read it
+    // there); the next step's index goes into the other parity's word, which
+    // no kernel of this step reads
+    sb.t = (long long)sb.counters[9 + sb.par];
+    if (blockIdx.x == 0 && threadIdx.x == 0) sb.counters[9 + (sb.par ^ 1)] = (unsigned long long)(sb.t + 1);
     if (!P::exact && blockIdx.x == 0 && threadIdx.x == 0) {
         sb.counters[4] = sb.counters[3];
         sb.counters[3] = 0ull;
