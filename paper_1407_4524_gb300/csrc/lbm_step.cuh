@@ -1377,33 +1377,17 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
 }
 
 // per-body sum of the link contributions into the series row of step t
-constexpr int RED_CHUNK = 256; // links staged in shared memory per round of the FP64 sums
-
 template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &p, const StepBufs &sb, int b) {
     const BodyDev &B = sb.bodies[b];
     double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
-    double acc = 0.0;
-    if constexpr (EXACT) {
-        // sequential in link order (= cell, direction order of the oracle),
-        // from chunks of the link contributions that the whole block stages
-        // in shared memory (coalesced loads; the order of the adds is kept)
-        __shared__ double stage[ME_PER_LINK][RED_CHUNK];
-        const long long cnt = sb.link_cnt[b];
-        for (long long j0 = 0; j0 < cnt; j0 += RED_CHUNK) {
-            const int m = (int)min((long long)RED_CHUNK, cnt - j0);
-            __syncthreads();
-            for (int e = threadIdx.x; e < ME_PER_LINK * m; e += blockDim.x) {
-                const int k = e / m, j = e - k * m;
-                stage[k][j] = sb.me[k * p.me_stride + B.link_off + j0 + j];
-            }
-            __syncthreads();
-            if (threadIdx.x < ME_PER_LINK)
-                for (int j = 0; j < m; ++j) acc += stage[threadIdx.x][j];
-        }
-    }
     if (threadIdx.x < ME_PER_LINK) {
         const int k = threadIdx.x;
-        if constexpr (!EXACT) { // exact fixed-point sums accumulated by k_links; cleared for the next step
+        double acc = 0.0;
+        if constexpr (EXACT) { // sequential in link order (= cell, direction order of the oracle)
+            const long long cnt = sb.link_cnt[b];
+            const double *mk = sb.me + k * p.me_stride + B.link_off;
+            for (long long j = 0; j < cnt; ++j) acc += mk[j];
+        } else { // exact fixed-point sums accumulated by k_links; cleared for the next step
             unsigned long long *a = sb.acc + (long long)b * SERIES_ROW + (k < 6 ? k : k + 6);
             acc = from_fx(*a);
             *a = 0ull;
