@@ -366,7 +366,8 @@ def run_serving(args, dev):
     """The serving stream: Poisson arrivals (20 req/s, seed 4524) of D2Q9 and
     D3Q19 channel solves of uneven sizes, FP32 arithmetic with FP16 f - w
     storage, run in real time twice on the same GPU: continuous batching
-    (lbm_batch_*) and one solve at a time (lbm_step per solve, FIFO).
+    (lbm_batch_*) and one solve at a time (lbm_step per solve), with first-come
+    first-served queues and again with smallest-work-first queues.
     Latency = completion (series back on the host) - arrival."""
     from paper_1407_4524_gb300 import serving
     from paper_1407_4524_gb300 import workloads as W
@@ -382,6 +383,10 @@ def run_serving(args, dev):
         by_slots[slots] = res
     batched = by_slots[args.serving_slots]
     seq, _ = serving.serve_sequential(trace, device=dev)
+    # the same trace with smallest-work-first queues, for both loops
+    sjf_b, _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=args.serving_slots, ticks_per_launch=32,
+                                     device=dev, policy="sjf")
+    sjf_s, _ = serving.serve_sequential(trace, device=dev, policy="sjf")
     return {
         "trace": f"{len(trace)} requests, Poisson 20/s (seed 4524), D2Q9 {{128x64..1024x512}} / "
                  f"D3Q19 {{64^3..192x96x96}}, 2000-20000 steps, fp16 storage",
@@ -390,6 +395,7 @@ def run_serving(args, dev):
         "batched": rnd(batched),
         "batched_by_slots": {str(k): rnd(v) for k, v in by_slots.items()},
         "one_at_a_time": rnd(seq),
+        "sjf": {"batched": rnd(sjf_b), "one_at_a_time": rnd(sjf_s)},
         "mlups_ratio": round(batched["mlups"] / seq["mlups"], 3) if seq["mlups"] else None,
         "p50_s": round(batched["p50_s"], 4), "p99_s": round(batched["p99_s"], 4),
     }
