@@ -735,10 +735,6 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     p.rho0f = (float)d.rho0;
     p.inv_rho0f = 1.0f / p.rho0f;
     p.keepf = 1.0f - p.omegaf;
-    {
-        const LatTab tb = d.lattice == LBM_D2Q9 ? make_tab<Lat<9>>() : make_tab<Lat<19>>();
-        for (int i = 0; i < 19; ++i) p.wom[i] = i < d.lattice ? p.omegaf * (float)tb.w[i] : 0.0f;
-    }
     p.u_inf = (float)d.u_in;
     p.nb = 0;
     D->series_cap = d.series_capacity > 0 ? d.series_capacity : 8192;

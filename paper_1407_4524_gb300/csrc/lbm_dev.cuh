@@ -148,7 +148,6 @@ struct Params {
     float omegaf, rho0f, u_inf;
     float inv_rho0f;  // 1 / rho0f (correctly rounded, as the device division)
     float keepf;      // 1 - omegaf
-    float wom[19];    // omegaf * w_i
     float gf[3];
 };
 

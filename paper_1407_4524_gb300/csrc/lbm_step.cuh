@@ -197,18 +197,21 @@ __device__ __forceinline__ float dfeq_f(const Params &p, int i, float drho, cons
     return L::template w<float>(i) * fmaf(rr, poly, drho);
 }
 
-// BGK relaxation fhat = (1 - omega) f + omega f^eq in the deviation form,
-// with omega w_i taken from the parameters
+// BGK relaxation fhat = (1 - omega) f + omega f^eq in the deviation form:
+// omega (f^eq_i - w_i) = (w_i omega rho_u) poly_i + w_i omega drho, with the
+// two products formed once per weight class (rest, axis, diagonal)
 template <class L>
 __device__ __forceinline__ void collide_f(const Params &p, float f[], float drho, const float u[3]) {
     const float om = p.omegaf;
     const float usq15 = 1.5f * fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
     const float rr = p.eq == 0 ? p.rho0f : 1.0f + drho;
+    const float omr = om * rr, omd = om * drho;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const float cu = cdot_f<L>(i, u);
         const float poly = fmaf(cu, fmaf(4.5f, cu, 3.0f), -usq15); // 3cu + 4.5cu^2 - 1.5u^2
-        float v = fmaf(p.keepf, f[i], p.wom[i] * fmaf(rr, poly, drho));
+        const float w = L::template w<float>(i);
+        float v = fmaf(p.keepf, f[i], fmaf(w * omr, poly, w * omd));
         if (p.has_force) {
             float cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
             float cg = cx * p.gf[0] + cy * p.gf[1] + cz * p.gf[2];
@@ -566,38 +569,49 @@ __device__ __forceinline__ unsigned pull_core(const Params &p, const typename P:
         plain = !p.nonper || !__any_sync(__activemask(), yzface);
     }
     if (plain) {
-        int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-        bool lo_b = false, hi_b = false, lo_in = false, hi_in = false;
-        if constexpr (FM != FM_PERIODIC) {
-            if (!p.per[0]) { // x faces: wall / inlet links bounce, an outlet repeats the last column
-                const int e_lo = p.edge[0], e_hi = p.edge[1];
-                lo_b = x == 0 && (e_lo == 1 || e_lo == 2);
-                hi_b = x == p.nx - 1 && (e_hi == 1 || e_hi == 2);
-                lo_in = lo_b && e_lo == 2;
-                hi_in = hi_b && e_hi == 2;
-                if (x == p.nx - 1) xp = p.nx - 1;
-            }
-        }
         const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
         const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
         // 32-bit in-plane indices (fewer than 2^32 cells) and one wide
         // multiply-add per plane pointer
         const unsigned nx = (unsigned)p.nx, ny = (unsigned)p.ny, N32 = (unsigned)p.N;
-        unsigned bounce = 0u;
+        // warps without a node on a non-periodic x face (all but the first and
+        // last warp of a row) take the straight loads, with no per-direction
+        // selects
+        bool xface = false;
+        if constexpr (FM != FM_PERIODIC) xface = !p.per[0] && __any_sync(__activemask(), x == 0 || x == p.nx - 1);
+        if (!xface) {
+            const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
-            const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
-            const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
-            const unsigned k = ((unsigned)sz * ny + (unsigned)sy) * nx + (unsigned)sx;
-            if constexpr (FM != FM_PERIODIC) {
+            for (int i = 0; i < L::Q; ++i) {
+                const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
+                const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
+                const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
+                const unsigned k = ((unsigned)sz * ny + (unsigned)sy) * nx + (unsigned)sx;
+                v[i] = ld_as<V>(src + (size_t)N32 * (unsigned)i + k);
+            }
+            return 0u;
+        }
+        unsigned bounce = 0u;
+        if constexpr (FM != FM_PERIODIC) {
+            // x faces: wall / inlet links bounce, an outlet repeats the last column
+            int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+            const int e_lo = p.edge[0], e_hi = p.edge[1];
+            const bool lo_b = x == 0 && (e_lo == 1 || e_lo == 2);
+            const bool hi_b = x == p.nx - 1 && (e_hi == 1 || e_hi == 2);
+            const bool lo_in = lo_b && e_lo == 2;
+            const bool hi_in = hi_b && e_hi == 2;
+            if (x == p.nx - 1) xp = p.nx - 1;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const int sx = L::cx(i) == 1 ? xm : (L::cx(i) == -1 ? xp : x);
+                const int sy = L::cy(i) == 1 ? ym : (L::cy(i) == -1 ? yp : y);
+                const int sz = L::cz(i) == 1 ? zm : (L::cz(i) == -1 ? zp : z);
+                const unsigned k = ((unsigned)sz * ny + (unsigned)sy) * nx + (unsigned)sx;
                 const bool b = (L::cx(i) == 1 && lo_b) || (L::cx(i) == -1 && hi_b);
                 const typename P::S *plane = src + (size_t)N32 * (unsigned)(b ? L::opp(i) : i);
                 v[i] = ld_as<V>(plane + (b ? (unsigned)cell : k));
                 bounce |= (b ? 1u : 0u) << i;
                 inlet_only |= ((L::cx(i) == 1 && lo_in) || (L::cx(i) == -1 && hi_in) ? 1u : 0u) << i;
-            } else {
-                v[i] = ld_as<V>(src + (size_t)N32 * (unsigned)i + k);
             }
         }
         return bounce;
