@@ -21,7 +21,7 @@ namespace {
 // on one row (so only the blocks at the row ends take the face path) and
 // need no 64-bit division per node.
 template <class L, class P, int FM>
-__global__ void __launch_bounds__(BBULK_THREADS) k_bbulk(const SolveDev *__restrict__ solves,
+__global__ void __launch_bounds__(BBULK_THREADS, FM == FM_GENERAL ? 16 : 20) k_bbulk(const SolveDev *__restrict__ solves,
                                                          const int4 *__restrict__ work) {
     // the solve's record in shared memory: its parameters are read many times
     __shared__ SolveDev sv;

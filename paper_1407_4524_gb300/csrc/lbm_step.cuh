@@ -41,7 +41,6 @@
 namespace lbm {
 
 constexpr int BULK_THREADS = 128;
-constexpr int BULK_MIN_BLOCKS = 8; // reduced precision: <= 64 registers, half the warps resident
 constexpr int LINK_THREADS = 256;
 constexpr int IMP_THREADS = 128;
 constexpr int N_COUNTERS = 16; // entries of the device counter array (StepBufs::counters)
@@ -554,6 +553,12 @@ template <class V, class S> __device__ __forceinline__ V ld_as(const S *ptr) {
 // sections), FM_GENERAL (any edges).
 constexpr int FM_PERIODIC = 0, FM_XFACES = 1, FM_GENERAL = 2;
 
+// resident blocks of 128 the reduced-precision stream-collide kernels are
+// built for: 10 (<= 48 registers, 62.5 % of the warps) where the face code is
+// light (periodic domains, x faces only), 8 (<= 64 registers) for the general
+// face code; more blocks spill (measured: 12 blocks lose 5 %)
+template <int FM> constexpr int bulk_min_blocks() { return FM == FM_GENERAL ? 8 : 10; }
+
 inline int face_mode(const Params &p) {
     if (!p.nonper) return FM_PERIODIC;
     return (p.per[1] && p.per[2]) ? FM_XFACES : FM_GENERAL;
@@ -790,7 +795,7 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
 
 // pull-stream + moments + BGK collision over every fluid node
 template <class L, class P, int FM>
-__global__ void __launch_bounds__(BULK_THREADS, P::exact ? 4 : BULK_MIN_BLOCKS) k_bulk(Params p, const typename P::S *__restrict__ src,
+__global__ void __launch_bounds__(BULK_THREADS, P::exact ? 4 : bulk_min_blocks<FM>()) k_bulk(Params p, const typename P::S *__restrict__ src,
                                                        typename P::S *__restrict__ dst,
                                                        const uint8_t *__restrict__ flags,
                                                        const typename P::C *__restrict__ mac_t,
