@@ -31,28 +31,6 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Warp totals of 16 values per lane (exact: 64-bit integer adds) by a
-// transposed butterfly: at each halving step a lane keeps half of its values
-// and receives its partner's sums of that half, 16 shuffles in all instead of
-// 5 per value.  On return lane l holds the total of component
-// red16_component(l) (lanes l and l ^ 1 hold the same one).
-__device__ __forceinline__ unsigned long long red16(unsigned long long (&x)[16], int lane) {
-#pragma unroll
-    for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < half; ++j) {
-            const unsigned long long send = up ? x[j] : x[j + half];
-            const unsigned long long keep = up ? x[j + half] : x[j];
-            x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return x[0] + __shfl_xor_sync(0xffffffffu, x[0], 1);
-}
-__device__ __forceinline__ int red16_component(int lane) {
-    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-}
-
 // the step of boundary node `cell` (one warp; lane = lattice direction)
 template <class L, class P>
 __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, const StepBufs &sb, long long cell,
@@ -212,13 +190,24 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
     const int b0 = __shfl_sync(0xffffffffu, bi, __ffs(cutmask) - 1);
     const bool one_body = __all_sync(0xffffffffu, o == 0 || bi == b0);
     if (one_body) {
+        // lane c (< 12) gathers component c of every cut link's lane and
+        // sums it in fixed point: as many rounds as cut links
         unsigned long long *acc = sb.acc + (long long)b0 * SERIES_ROW;
-        unsigned long long xs[16];
+        const int myc = lane < ME_PER_LINK ? lane : 0;
+        unsigned long long tot = 0ull;
+        unsigned m = cutmask;
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            float mine = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) xs[c] = c < ME_PER_LINK ? to_fx(v[c]) : 0ull;
-        const unsigned long long s = red16(xs, lane);
-        const int c = red16_component(lane);
-        if ((lane & 1) == 0 && c < ME_PER_LINK && s) atomicAdd(acc + (c < 6 ? c : c + 6), s);
+            for (int c = 0; c < ME_PER_LINK; ++c) {
+                const float vc = __shfl_sync(0xffffffffu, v[c], j);
+                if (c == myc) mine = vc;
+            }
+            tot += to_fx(mine);
+        }
+        if (lane < ME_PER_LINK && tot) atomicAdd(acc + (lane < 6 ? lane : lane + 6), tot);
     } else if (o) {
         unsigned long long *acc = sb.acc + (long long)bi * SERIES_ROW;
         for (int c = 0; c < ME_PER_LINK; ++c) atomicAdd(acc + (c < 6 ? c : c + 6), to_fx(v[c]));
