@@ -308,6 +308,22 @@ int lbm_set_populations(lbm_domain *dom, const double *f);
  * Errors: LBM_ERR_ARG (NULL), LBM_ERR_OOM (staging buffer), LBM_ERR_CUDA. */
 int lbm_get_macros(lbm_domain *dom, double *out);
 
+/* State snapshots (checkpoint / resume; no counterpart in the paper).
+ * lbm_state_bytes: size of a snapshot of this domain (-1 for NULL).
+ * lbm_save_state: copies the whole state at the current step -- every device
+ * buffer (populations, moments, solid owners and flags, cut-link and
+ * boundary-node lists, body records, the force/torque ring, counters), the
+ * step index and the host's body records -- into `out` (caller-owned, at
+ * least lbm_state_bytes).  Synchronises.
+ * lbm_load_state: restores such a snapshot into a domain created with the
+ * same descriptor and given the same number of bodies by lbm_set_bodies, so
+ * that its buffers have the snapshot's sizes (LBM_ERR_ARG otherwise); the
+ * steps that follow reproduce those of the saved domain bit for bit.
+ * Synchronises. */
+int64_t lbm_state_bytes(const lbm_domain *dom);
+int lbm_save_state(lbm_domain *dom, void *out, int64_t cap);
+int lbm_load_state(lbm_domain *dom, const void *in, int64_t size);
+
 /* Body state at the current step: out[n_bodies][9] = X(t), U(t), W(t).
  * Synchronises.  (Free bodies: their integrated motion.) */
 int lbm_get_body_state(lbm_domain *dom, double *out);

@@ -113,6 +113,9 @@ struct lbm_domain {
     std::vector<lbm_body> hb;
     std::vector<BodyDev> hbd;
     std::vector<void *> body_allocs;
+    // every persistent device buffer with its size, in allocation order: the
+    // device part of a state snapshot (lbm_save_state / lbm_load_state)
+    std::vector<std::pair<void *, size_t>> state_bufs;
     BodyDev *dbodies = nullptr;
     int *dmoving = nullptr;
     int2 *chunk_all = nullptr, *chunk_mov = nullptr;
@@ -208,6 +211,7 @@ int alloc_into(lbm_domain *D, void **slot, size_t n, std::vector<void *> *track)
     if (cudaMemsetAsync(ptr, 0, n, D->s) != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaMemsetAsync failed");
     *slot = ptr;
     if (track) track->push_back(ptr);
+    D->state_bufs.emplace_back(ptr, n);
     return LBM_OK;
 }
 
@@ -219,7 +223,14 @@ template <class T> int alloc_t(lbm_domain *D, T **slot, size_t count, std::vecto
 }
 
 void free_body_buffers(lbm_domain *D) {
-    for (void *ptr : D->body_allocs) D->release(ptr);
+    for (void *ptr : D->body_allocs) {
+        for (size_t k = 0; k < D->state_bufs.size(); ++k)
+            if (D->state_bufs[k].first == ptr) {
+                D->state_bufs.erase(D->state_bufs.begin() + (long)k);
+                break;
+            }
+        D->release(ptr);
+    }
     D->body_allocs.clear();
     for (int k = 0; k < 2; ++k) { // pinned body staging: sized for the body count it was made for
         if (!D->hbd_pin[k]) continue;
@@ -1217,6 +1228,115 @@ int lbm_get_solid(lbm_domain *D, int32_t *out) {
     CK(cudaStreamSynchronize(D->s));
     CK(cudaMemcpy(o.data(), D->owner[D->t & 1], N * sizeof(uint16_t), cudaMemcpyDeviceToHost));
     for (size_t k = 0; k < N; ++k) out[k] = (int32_t)o[k] - 1;
+    return LBM_OK;
+}
+
+// ---- state snapshots --------------------------------------------------------
+//
+// Layout: SnapHeader, the bodies as the host holds them (lbm_body, BodyDev),
+// the sizes of the device buffers, then their contents in allocation order.
+namespace {
+struct SnapHeader {
+    char magic[8];
+    int32_t lattice, precision, nx, ny, nz, nb;
+    int64_t t;
+    int32_t prep_dirty, lists_dirty;
+    int64_t nbuf;
+};
+constexpr char SNAP_MAGIC[8] = {'L', 'B', 'M', 'S', 'N', 'A', 'P', '1'};
+} // namespace
+
+int64_t lbm_state_bytes(const lbm_domain *D) {
+    if (!D) return -1;
+    int64_t b = (int64_t)sizeof(SnapHeader) + (int64_t)D->nb * (int64_t)(sizeof(lbm_body) + sizeof(BodyDev));
+    b += (int64_t)D->state_bufs.size() * (int64_t)sizeof(int64_t);
+    for (const auto &e : D->state_bufs) b += (int64_t)e.second;
+    return b;
+}
+
+int lbm_save_state(lbm_domain *D, void *out, int64_t cap) {
+    if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    const int64_t need = lbm_state_bytes(D);
+    if (cap < need) return fail(LBM_ERR_ARG, "snapshot buffer smaller than lbm_state_bytes");
+    CK(cudaStreamSynchronize(D->s));
+    char *p = (char *)out;
+    SnapHeader h{};
+    std::memcpy(h.magic, SNAP_MAGIC, 8);
+    h.lattice = D->Q;
+    h.precision = D->prec;
+    h.nx = D->p.nx;
+    h.ny = D->p.ny;
+    h.nz = D->p.nz;
+    h.nb = D->nb;
+    h.t = D->t;
+    h.prep_dirty = D->prep_dirty ? 1 : 0;
+    h.lists_dirty = D->lists_dirty ? 1 : 0;
+    h.nbuf = (int64_t)D->state_bufs.size();
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    if (D->nb) {
+        std::memcpy(p, D->hb.data(), sizeof(lbm_body) * D->nb);
+        p += sizeof(lbm_body) * D->nb;
+        std::memcpy(p, D->hbd.data(), sizeof(BodyDev) * D->nb);
+        p += sizeof(BodyDev) * D->nb;
+    }
+    for (const auto &e : D->state_bufs) {
+        const int64_t n = (int64_t)e.second;
+        std::memcpy(p, &n, sizeof(n));
+        p += sizeof(n);
+    }
+    for (const auto &e : D->state_bufs) {
+        CK(cudaMemcpy(p, e.first, e.second, cudaMemcpyDeviceToHost));
+        p += e.second;
+        D->d2h += (long long)e.second;
+    }
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_domain *D, const void *in, int64_t size) {
+    if (!D || !in || size < (int64_t)sizeof(SnapHeader)) return fail(LBM_ERR_ARG, "invalid arguments");
+    const char *p = (const char *)in;
+    SnapHeader h;
+    std::memcpy(&h, p, sizeof(h));
+    p += sizeof(h);
+    if (std::memcmp(h.magic, SNAP_MAGIC, 8) != 0) return fail(LBM_ERR_ARG, "not a domain snapshot");
+    if (h.lattice != D->Q || h.precision != D->prec || h.nx != D->p.nx || h.ny != D->p.ny || h.nz != D->p.nz ||
+        h.nb != D->nb || h.nbuf != (int64_t)D->state_bufs.size() || size != lbm_state_bytes(D))
+        return fail(LBM_ERR_ARG, "the snapshot belongs to a domain of another shape or body set");
+    std::vector<lbm_body> hb((size_t)D->nb);
+    std::vector<BodyDev> hbd((size_t)D->nb);
+    if (D->nb) {
+        std::memcpy(hb.data(), p, sizeof(lbm_body) * D->nb);
+        p += sizeof(lbm_body) * D->nb;
+        std::memcpy(hbd.data(), p, sizeof(BodyDev) * D->nb);
+        p += sizeof(BodyDev) * D->nb;
+    }
+    for (size_t k = 0; k < D->state_bufs.size(); ++k) {
+        int64_t n;
+        std::memcpy(&n, p, sizeof(n));
+        p += sizeof(n);
+        if (n != (int64_t)D->state_bufs[k].second)
+            return fail(LBM_ERR_ARG, "the snapshot's buffers do not match this domain's");
+    }
+    CK(cudaStreamSynchronize(D->s));
+    if (D->nb) { // the host's body records and the body maps they imply, then the device state over them
+        D->hb = hb;
+        D->hbd = hbd;
+        int rc = upload_bodies(D);
+        if (rc) return rc;
+    }
+    for (const auto &e : D->state_bufs) {
+        CK(cudaMemcpy(e.first, p, e.second, cudaMemcpyHostToDevice));
+        p += e.second;
+        D->h2d += (long long)e.second;
+    }
+    D->t = h.t;
+    D->prep_dirty = h.prep_dirty != 0;
+    D->lists_dirty = h.lists_dirty != 0;
+    D->graph_dirty = true;
+    D->ev_used = 0;
+    D->g_timed = false;
+    for (int k = 0; k < lbm_domain::N_STEP_EV; ++k) D->step_ev_t[k] = -1;
     return LBM_OK;
 }
 

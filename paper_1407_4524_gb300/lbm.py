@@ -98,6 +98,10 @@ def load(build_if_missing: bool = True):
     lib.lbm_get_populations.argtypes = [P, P]
     lib.lbm_set_populations.argtypes = [P, P]
     lib.lbm_get_macros.argtypes = [P, P]
+    lib.lbm_state_bytes.restype = C.c_int64
+    lib.lbm_state_bytes.argtypes = [P]
+    lib.lbm_save_state.argtypes = [P, P, C.c_int64]
+    lib.lbm_load_state.argtypes = [P, P, C.c_int64]
     lib.lbm_get_solid.argtypes = [P, P]
     lib.lbm_get_body_state.argtypes = [P, P]
     lib.lbm_get_stats.argtypes = [P, C.POINTER(lbm_stats)]
@@ -330,6 +334,18 @@ class Domain:
         _check(self.lib.lbm_get_macros(self.h, out.ctypes.data))
         nx, ny, nz = self.shape
         return out.reshape(4, nz, ny, nx)
+
+    def save_state(self) -> bytes:
+        """snapshot of the whole state at the current step (checkpoint)"""
+        n = int(self.lib.lbm_state_bytes(self.h))
+        buf = np.empty(n, dtype=np.uint8)
+        _check(self.lib.lbm_save_state(self.h, buf.ctypes.data, n))
+        return buf.tobytes()
+
+    def load_state(self, blob: bytes):
+        """restore a snapshot taken from a domain of the same problem (resume)"""
+        buf = np.frombuffer(blob, dtype=np.uint8)
+        _check(self.lib.lbm_load_state(self.h, buf.ctypes.data, len(buf)))
 
     def body_state(self) -> np.ndarray:
         """[n_bodies, 9]: X(t), U(t), W(t)"""

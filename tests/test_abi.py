@@ -162,3 +162,11 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
+
+
+def test_state_bytes_of_null_domain():
+    from paper_1407_4524_gb300 import lbm
+    lib = lbm.load()
+    assert lib.lbm_state_bytes(None) == -1
+    assert lib.lbm_save_state(None, None, 0) == 1
+    assert lib.lbm_load_state(None, None, 0) == 1
