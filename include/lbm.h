@@ -319,7 +319,10 @@ int lbm_get_macros(lbm_domain *dom, double *out);
  * same descriptor and given the same number of bodies by lbm_set_bodies, so
  * that its buffers have the snapshot's sizes (LBM_ERR_ARG otherwise); the
  * steps that follow reproduce those of the saved domain bit for bit.
- * Synchronises. */
+ * A snapshot is raw host-endian memory of this library version: it is not a
+ * portable file format.  Every check runs before anything is changed, so
+ * LBM_ERR_ARG leaves the domain as it was; after LBM_ERR_CUDA its state is
+ * undefined (load the snapshot again or destroy the domain).  Synchronises. */
 int64_t lbm_state_bytes(const lbm_domain *dom);
 int lbm_save_state(lbm_domain *dom, void *out, int64_t cap);
 int lbm_load_state(lbm_domain *dom, const void *in, int64_t size);
