@@ -35,9 +35,11 @@
  * comment at the function states the reading taken.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
- * against closed forms, conservation laws, symmetry and exact special cases.
- * Absolute drag/lift/torque VALUES of the benchmark geometries are "parity
- * unpinned": the paper prints no numbers for them.
+ * against closed forms, conservation laws, symmetry and exact special cases;
+ * the absolute drag of a static cylinder and sphere by the Stokes drag of
+ * periodic arrays (Hasimoto; Sangani & Acrivos).  Absolute drag/lift/torque
+ * VALUES of the paper's own benchmark geometries are "parity unpinned": the
+ * paper prints no numbers for them.
  */
 #include <math.h>
 #include <stdint.h>
