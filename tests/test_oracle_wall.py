@@ -365,3 +365,24 @@ def test_taylor_couette_converges(oracle_mod):
     assert e1 < 0.03
     assert e2 < e1 / 2.5
     assert o1.fallbacks >= 0
+
+
+@pytest.mark.parametrize("tau,tol", [(0.8, 5e-3), (1.0, 2e-2)])
+def test_taylor_couette_torque(oracle_mod, tau, tol):
+    """Absolute torque: at steady state the fluid's torque on the rotating
+    inner cylinder is -4 pi mu B per unit length (B the 1/r coefficient of the
+    azimuthal velocity), and the fixed outer cylinder takes the opposite one.
+    The solid set does not change under rotation, so the three torque forms
+    apply; the moving-frame form differs only by the wall velocity terms.
+    Measured: 0.17 % off at tau = 0.8, 1.5 % at tau = 1.0 (the interpolated
+    wall's effective position drifts with the viscosity).  Taking the lever
+    arm at the wall point instead of the fluid node would be off by ~8 %."""
+    R1, R2 = 6.0, 12.0
+    _, o = _couette(oracle_mod, R1, R2, tau=tau)
+    w = 0.01 / R1
+    mu = (tau - 0.5) / 3
+    T = -4 * np.pi * mu * w * R1**2 * R2**2 / (R2**2 - R1**2)
+    for kind in ("static", "lattice", "moving"):
+        ft = o.force_torque(kind)[-1]
+        assert abs(ft[0, 5] / T - 1) < tol, (kind, ft[0, 5] / T)
+        assert abs(ft[1, 5] / -T - 1) < tol, (kind, ft[1, 5] / -T)
