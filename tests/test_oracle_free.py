@@ -7,7 +7,10 @@ ForceInMovement / TorqueInMovement) with weight less buoyancy.
 * in a closed periodic box without gravity the fluid momentum plus the body's
   M U is conserved to round-off (this pins the sign of the force applied to the
   body, the force form -- static plus impulsive -- and that the pose advanced
-  with the velocity the A+/A- sets were built from).
+  with the velocity the A+/A- sets were built from);
+* a free cylinder, ellipse or sphere spinning at the centre of a closed box:
+  the angular momentum of fluid plus body plus walls is conserved to
+  round-off (pins the moments of inertia and the sign of the applied torque).
 """
 import numpy as np
 import pytest
@@ -80,3 +83,66 @@ def test_momentum_of_fluid_plus_body_is_conserved(oracle_mod, lat):
     # the body has slowed down against the fluid, and the momentum it lost is in the fluid
     assert np.linalg.norm(o.body_state()[0, 3:6]) < np.linalg.norm(U_first)
     assert err <= 1e-12 * M * np.abs(U_first).max()
+
+
+@pytest.mark.parametrize("shape", ["cylinder", "ellipse", "sphere"])
+def test_angular_momentum_of_fluid_plus_spinning_body_is_conserved(oracle_mod, shape):
+    """A free body spun up at the centre of a closed box, fluid at rest: box
+    and body are symmetric under inversion through the centre, so the force
+    stays zero and the body stays put, and the fluid's angular momentum plus
+    the body's I W plus the torque given to the walls is conserved to
+    round-off.  This pins the moment of inertia (M R^2 / 2, M (a^2 + b^2) / 4,
+    2/5 M R^2 with M = rho_b V) and the sign of the torque applied to the body;
+    the ellipse adds the impulsive terms of the nodes its rotation covers and
+    uncovers (Eq. TorqueInMovement)."""
+    r = 1.4
+    if shape == "sphere":
+        lat, R, R2 = "D3Q19", 4.3, None
+        X0 = (8.5, 7.5, 7.0)  # centre of the 18 x 16 x 15 box
+        W0 = np.array([0.003, -0.002, 0.004])
+        b = dict(shape=shape, R=R, X0=X0, W=tuple(W0), free=True, density_ratio=r)
+        M = r * 4.0 / 3.0 * np.pi * R ** 3
+        I = 0.4 * M * R * R
+    else:
+        lat = "D2Q9"
+        X0 = (16.5, 14.5)  # centre of the 34 x 30 box
+        W0 = np.array([0.0, 0.0, 0.006])
+        if shape == "cylinder":
+            R, R2 = 5.7, None
+            b = dict(shape=shape, R=R, X0=X0, W=W0[2], free=True, density_ratio=r)
+            M = r * np.pi * R * R
+            I = 0.5 * M * R * R
+        else:
+            R, R2 = 8.2, 4.6
+            r, W0 = 3.0, np.array([0.0, 0.0, 0.012])  # heavier and faster: it keeps turning over nodes
+            b = dict(shape=shape, R=R, R2=R2, theta0=0.35, X0=X0, W=W0[2], free=True, density_ratio=r)
+            M = r * np.pi * R * R2
+            I = 0.25 * M * (R * R + R2 * R2)
+    o = oracle_mod.Oracle(_closed_box(lat, [b], (0.0,) * (2 if lat == "D2Q9" else 3)))
+    c, _, _ = _tables(oracle_mod, o)
+
+    def body_L(s, inertia):
+        X, U, W = s[0:3], s[3:6], s[6:9]
+        return inertia * W + np.cross(X, M * U)
+
+    _, L_fl, _ = _fluid_momentum(o, c)
+    total0 = L_fl + body_L(o.body_state()[0], I)
+    total0_wrong = L_fl + body_L(o.body_state()[0], 2.0 * I)
+    walls = np.zeros(3)
+    err, err_wrong, n_imp = 0.0, 0.0, 0
+    for _ in range(40):
+        o.step(1)
+        walls += o.edge_me()[3:]
+        _, L_fl, _ = _fluid_momentum(o, c)
+        s = o.body_state()[0]
+        err = max(err, np.abs(L_fl + body_L(s, I) + walls - total0).max())
+        err_wrong = max(err_wrong, np.abs(L_fl + body_L(s, 2.0 * I) + walls - total0_wrong).max())
+        n_imp += int(np.abs(o.series()[-1, 0, 9:12]).max() > 0)
+        assert np.abs(s[3:6]).max() < 1e-14  # no force: the body does not translate
+    s = o.body_state()[0]
+    spun_down = np.abs(s[6:9] - W0).max()
+    assert spun_down > 1e-3 * np.abs(W0).max()  # the fluid took up a visible part of the spin
+    assert err <= 1e-11 * I * np.abs(W0).max()
+    assert err_wrong > 1e3 * err  # a wrong moment of inertia breaks the balance
+    if shape == "ellipse":
+        assert n_imp > 3
