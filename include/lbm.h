@@ -230,7 +230,10 @@ int lbm_destroy_domain(lbm_domain *dom);
  * overlap, must keep a surface gap >= 2 cells from each other and >= 3 cells
  * from non-periodic faces, and must be smaller than half the domain on
  * periodic axes (LBM_ERR_ARG otherwise).  Bodies with U or W != 0 move by the
- * prescribed motion and have their links and A+/A- sets rebuilt every step. */
+ * prescribed motion and have their links and A+/A- sets rebuilt every step.
+ * LBM_ERR_ARG / LBM_ERR_STATE leave the domain unchanged; LBM_ERR_OOM (or
+ * LBM_ERR_CUDA) part-way through puts it back into its created state: no
+ * bodies, every node fluid, f(x,0) re-initialised, its buffers released. */
 int lbm_set_bodies(lbm_domain *dom, const lbm_body *host_bodies, int n);
 
 /* Replace the motion of existing bodies between steps (free-body coupling):

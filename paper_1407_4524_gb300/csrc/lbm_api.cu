@@ -840,12 +840,48 @@ int lbm_destroy_domain(lbm_domain *D) {
     return LBM_OK;
 }
 
+namespace {
+
+// the state lbm_create_domain leaves: no bodies, every node fluid, the
+// initial populations (after a failure part-way through placing bodies)
+void reset_to_no_bodies(lbm_domain *D) {
+    cudaStreamSynchronize(D->s);
+    free_body_buffers(D);
+    D->p.nb = 0;
+    D->p.me_stride = 0; // as created
+    D->hb.clear();
+    D->hbd.clear();
+    D->graph_dirty = true;
+    const size_t N = (size_t)D->p.N;
+    for (int k = 0; k < 2; ++k) cudaMemsetAsync(D->owner[k], 0, N * sizeof(uint16_t), D->s);
+    launch_flags_full(D->Q, D->p, D->owner[0], D->flags, D->s);
+    init_populations(D);
+    cudaStreamSynchronize(D->s);
+}
+
+int place_bodies(lbm_domain *D, const lbm_body *hb, int n);
+
+} // namespace
+
 int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if (!D || n < 0 || (n > 0 && !hb)) return fail(LBM_ERR_ARG, "invalid arguments");
     if (D->t != 0) return fail(LBM_ERR_STATE, "bodies can only be placed at t = 0");
     if (n > 65534) return fail(LBM_ERR_ARG, "at most 65534 bodies");
     int rc = validate_bodies(D, hb, n);
     if (rc) return rc;
+    rc = place_bodies(D, hb, n);
+    if (rc) { // out of memory (or a CUDA error) part-way: the domain goes back to no bodies
+        const std::string msg = g_err;
+        reset_to_no_bodies(D);
+        g_err = msg;
+    }
+    return rc;
+}
+
+namespace {
+
+int place_bodies(lbm_domain *D, const lbm_body *hb, int n) {
+    int rc = LBM_OK;
     CK(cudaStreamSynchronize(D->s));
     free_body_buffers(D);
     D->graph_dirty = true;
@@ -948,6 +984,8 @@ int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     CK(cudaStreamSynchronize(D->s));
     return LBM_OK;
 }
+
+} // namespace
 
 int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if (!D || !hb || n != D->nb) return fail(LBM_ERR_ARG, "update needs the same number of bodies");
