@@ -170,7 +170,8 @@ static double axis_disp(const or_dom *o, int axis, double x, double X)
     return v;
 }
 
-/* prescribed pose: X(t) = X0 + (t - t0) U */
+/* prescribed pose: X(t) = X0 + (t - t0) U (the body Omega(t) of the problem
+ * statement, Sec. 3, moving with a given velocity) */
 static void pose(const or_body *b, long long t, double X[3])
 {
     double dt = (double)(t - b->t0);
@@ -251,7 +252,10 @@ static void cross(const double a[3], const double b[3], double out[3])
     out[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-/* rigid-body velocity at offset r from the centre: U + W x r */
+/* rigid-body velocity at offset r from the centre: U + W x r (the wall
+ * velocity u_B of Eq. Fillipova_interpolation at the wall point, and the
+ * frame velocity v of Eqs. ForceInMovementMovingFrame /
+ * TorqueInMovementMovingFrame) */
 static void body_velocity(const or_body *b, const double r[3], double v[3])
 {
     double wr[3];
@@ -266,7 +270,9 @@ static void body_axes(double co, double si, const double v[3], double *xi, doubl
     *eta = co * v[1] - si * v[0];
 }
 
-/* r: offset from the centre; co, si: cos and sin of the body's orientation */
+/* membership of Omega(t): |r| <= R (sphere), the x-y distance (cylinder), the
+ * body-axes form (ellipse, the test section's sedimenting ellipse); r: offset
+ * from the centre; co, si: cos and sin of the body's orientation */
 static int inside(const or_body *b, const double r[3], double co, double si)
 {
     int in;
@@ -500,7 +506,9 @@ static double wall_value(const or_dom *o, long x, int xx, int yy, int zz, int i,
 
 /* ---- geometry ----------------------------------------------------------------- */
 
-/* solid owner of every node for the body poses at step t (bounding boxes) */
+/* solid owner of every node for the body poses at step t (bounding boxes):
+ * the solid set whose change from t to t+1 gives the covered and uncovered
+ * nodes A+ / A- of Sec. 3 */
 static void rasterise(or_dom *o, long long t, int *owner)
 {
     for (long x = 0; x < o->N; ++x) owner[x] = -1;
@@ -568,6 +576,8 @@ void or_destroy(or_dom *o)
     free(o);
 }
 
+/* initial state: f = f^eq(rho = 1, u0) at every node (Eq. collision's
+ * equilibrium in the quasi-incompressible form of Eqs. LBMmacroscopics) */
 static void init_state(or_dom *o)
 {
     for (long x = 0; x < o->N; ++x)
