@@ -39,7 +39,7 @@ def _s_cubic(c):
             - 3.0734 * c ** (10.0 / 3.0))
 
 
-def _steady_drag_ratio(oracle_mod, lattice, L, R, tau, halfway=False, g=1e-7):
+def _steady_drag_ratio(oracle_mod, lattice, L, R, tau, halfway=False, g=1e-7, eq="incomp"):
     """Run to steady state (momentum balance F_ME = g V_fluid, U settled) and
     return F_ME / ((1 - c) F_closed_form(U))."""
     mu = (tau - 0.5) / 3.0
@@ -51,7 +51,7 @@ def _steady_drag_ratio(oracle_mod, lattice, L, R, tau, halfway=False, g=1e-7):
         n = (L, L, L)
         body = dict(shape="sphere", R=R, X0=(L / 2 + 0.31, L / 2 + 0.17, L / 2 - 0.23), halfway=halfway)
         force = (g, 0.0, 0.0)
-    o = oracle_mod.Oracle(dict(lattice=lattice, n=n, tau=tau, force=force, bodies=[body]))
+    o = oracle_mod.Oracle(dict(lattice=lattice, n=n, tau=tau, force=force, bodies=[body], eq=eq))
     fluid = o.solid() < 0
     n_fluid = int(fluid.sum())
     U_prev = 0.0
@@ -92,3 +92,10 @@ def test_sphere_array_drag(oracle_mod):
 def test_staircase_wall_misses_the_closed_form(oracle_mod, lattice, L, R):
     r = _steady_drag_ratio(oracle_mod, lattice, L, R, 0.8, halfway=True)
     assert abs(r - 1.0) > 2 * TOL, r
+
+
+def test_cylinder_array_drag_standard_equilibrium(oracle_mod):
+    """The standard equilibrium (and the printed standard form of the
+    curved-wall g) gives the same Stokes drag at this Mach number."""
+    r = _steady_drag_ratio(oracle_mod, "D2Q9", 48, 8.3, 0.8, eq="standard")
+    assert abs(r - 1.0) < TOL, r
