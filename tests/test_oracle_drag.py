@@ -99,3 +99,30 @@ def test_cylinder_array_drag_standard_equilibrium(oracle_mod):
     curved-wall g) gives the same Stokes drag at this Mach number."""
     r = _steady_drag_ratio(oracle_mod, "D2Q9", 48, 8.3, 0.8, eq="standard")
     assert abs(r - 1.0) < TOL, r
+
+
+@pytest.mark.parametrize("Ub,refill", [(-0.002, "uB"), (-0.005, "uB"), (-0.005, "extrap")])
+def test_translating_cylinder_array_drag(oracle_mod, Ub, refill):
+    """The same array with every cylinder translating at U_b against the
+    driven flow: by Galilean invariance of Stokes flow the time-averaged
+    force follows the closed form with the superficial velocity relative to
+    the body.  This holds the moving-body forms to an absolute value: the
+    lattice-frame force with its impulsive terms over the covered and
+    uncovered nodes (Eq. ForceInMovement) and the moving-frame force (Eq.
+    ForceInMovementMovingFrame), for the u_B-equilibrium and the
+    extrapolation refill."""
+    L, R, tau, g = 48, 8.3, 0.8, 1e-6
+    X0 = (L / 2 + 0.31, L / 2 + 0.17)
+    o = oracle_mod.Oracle(dict(lattice="D2Q9", n=(L, L), tau=tau, force=(g, 0.0), refill=refill,
+                               bodies=[dict(shape="cylinder", R=R, X0=X0, U=(Ub, 0.0))]))
+    o.step(12000)
+    s = o.series()[-4800:, 0]  # the body crosses 10-24 nodes in the window
+    F_lattice = (s[:, 0] + s[:, 6]).mean()
+    F_moving = s[:, 12].mean()
+    fluid = o.solid() < 0
+    U_rel = (o.macro()[1][fluid] - Ub).sum() / float(L * L)
+    c = math.pi * R * R / L ** 2
+    F = (1.0 - c) * 4.0 * math.pi * (tau - 0.5) / 3.0 * U_rel / _k_square(c)
+    assert abs(F_lattice / F - 1.0) < TOL, F_lattice / F
+    assert abs(F_moving / F - 1.0) < TOL, F_moving / F
+    assert abs(F_lattice / (g * int(fluid.sum())) - 1.0) < 1e-2  # time-averaged balance
