@@ -44,3 +44,61 @@ def test_sphere_swarm_gap_rule():
             assert np.linalg.norm(d) - bs[i]["R"] - bs[j]["R"] >= 2.0
     assert all(np.linalg.norm(b["U"]) == 0.0 for b in bs[0::2])
     assert all(np.linalg.norm(b["U"]) <= 0.02 for b in bs[1::2])
+
+
+def _golden_setup():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sedimentation_setup.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            vals = [float(v) if v[0].isdigit() else v for v in line[1:]]
+            out[line[0]] = vals if len(vals) > 1 else vals[0]
+    return out
+
+
+def test_sedimentation_workloads_follow_the_printed_setup():
+    """The sedimentation workloads in lattice units restate the paper's
+    printed set-up: lattice size, tau, the on-node walls of the Zou-He edges
+    spanning the channel (and the printed sizes agree: (ny - 1) dx = H),
+    body sizes, start positions, orientation, density ratios, and gravity
+    through dt = nu_lattice dx^2 / nu."""
+    import math
+    G = _golden_setup()
+    nu_l = (G["tau"] - 0.5) / 3.0
+    # disc
+    nx, ny = (int(v) for v in G["disc.n"])
+    d = G["disc.d"]
+    width = G["disc.W_over_d"] * d
+    dx = width / (nx - 1)
+    assert abs((ny - 1) * dx - G["disc.H_over_W"] * width) < 1e-12
+    dt = nu_l * dx * dx / G["nu"]
+    for r_rho in G["disc.r_rho"]:
+        spec = W.sedimenting_disc_2d(density_ratio=r_rho)
+        assert spec["lattice"] == G["lattice"] and tuple(spec["n"]) == (nx, ny) and spec["tau"] == G["tau"]
+        b = spec["bodies"][0]
+        assert b["shape"] == "cylinder" and b["free"] and b["density_ratio"] == r_rho
+        assert math.isclose(b["R"], 0.5 * d / dx, rel_tol=1e-12)
+        x_c, y_c = G["disc.centre"]
+        assert math.isclose(b["X0"][0], 0.5 * (nx - 1) + x_c / dx, rel_tol=1e-12)
+        assert math.isclose(b["X0"][1], (G["disc.origin_above_bottom"] + y_c) / dx, rel_tol=1e-12)
+        assert math.isclose(-spec["gravity"][1], G["g"] * dt * dt / dx, rel_tol=1e-12)
+    # ellipse
+    nx, ny = (int(v) for v in G["ellipse.n"])
+    a = G["ellipse.a"]
+    width = G["ellipse.blockage"] * a
+    dx = width / (nx - 1)
+    assert abs((ny - 1) * dx - G["ellipse.H_over_a"] * a) < 1e-12
+    dt = nu_l * dx * dx / G["nu"]
+    spec = W.sedimenting_ellipse_2d()
+    assert tuple(spec["n"]) == (nx, ny) and spec["tau"] == G["tau"]
+    b = spec["bodies"][0]
+    assert b["shape"] == "ellipse" and b["free"] and b["density_ratio"] == G["ellipse.r_rho"]
+    assert math.isclose(b["R"], 0.5 * a / dx, rel_tol=1e-12)
+    assert math.isclose(b["R2"], 0.5 * a / G["ellipse.aspect"] / dx, rel_tol=1e-12)
+    assert math.isclose(b["theta0"], G["ellipse.theta0_over_pi"] * math.pi, rel_tol=1e-15)
+    cx, cy = G["ellipse.centre_over_W"]
+    assert math.isclose(b["X0"][0], cx * (nx - 1), rel_tol=1e-12)
+    assert math.isclose(b["X0"][1], (G["ellipse.origin_above_bottom"] + cy) / dx, rel_tol=1e-12)
+    assert math.isclose(-spec["gravity"][1], G["g"] * dt * dt / dx, rel_tol=1e-12)
