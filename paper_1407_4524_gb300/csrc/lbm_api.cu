@@ -15,7 +15,9 @@
 // a high-priority side stream beside k_bulk (+ k_zouhe) on the main stream.
 // Each lbm_step call ends with a step event that the series reads wait on.
 // The serving batch (lbm_batch_*) keeps solves of this kind in slots and
-// replays a CUDA graph of batched ticks (lbm_batch.cu).
+// replays a CUDA graph of batched ticks (lbm_batch.cu).  Every persistent
+// device buffer is recorded with its size at allocation, in order: that list
+// is the device part of a state snapshot (lbm_save_state / lbm_load_state).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
