@@ -173,7 +173,7 @@ def cpu_baseline(spec, budget_s: float = 15.0):
         if el >= budget_s or steps >= 200:
             break
     mlups = cells * steps / el / 1e6
-    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": oracle.threads(),
             "kind": "oracle", "sample": f"{desc}; {steps} steps, {el:.1f} s, FP64"}
 
 
@@ -218,7 +218,7 @@ def run_reference(args):
     o.step(steps)
     el = time.perf_counter() - t0
     mlups = cells * steps / el / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    cores = oracle.threads()  # the threads the oracle's loops really run on
     line = {
         "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
         "steps": steps, "warmup": warmup, "ms_per_step": round(1e3 * el / max(1, steps), 3),
@@ -251,11 +251,14 @@ def run_ours(args):
     Q = dom.q
     sbytes = {"fp64": 8, "fp32": 4, "fp16": 2}[args.precision]
 
-    # warm-up, with the stream-collide kernel's timing events already on: the
-    # library replays captured 16-step graphs for runs of >= 16 steps, and the
-    # graph with its timing events is captured here, outside the timed region
+    # warm-up: exactly `warmup` steps, with the stream-collide kernel's timing
+    # events already on.  The library replays captured 16-step graphs for runs
+    # of >= 16 steps; the graph (with its timing events) is recorded here,
+    # after the first warm-up step, outside the timed region.
     dom.set_kernel_timing(True)
-    dom.step(max(args.warmup, 32))
+    dom.step(1)
+    dom.prepare_graph()
+    dom.step(args.warmup - 1)
     torch.cuda.synchronize()
     dom.kernel_time()  # discard the warm-up windows
     launches_per_step = dom.launches_per_step()
@@ -352,7 +355,6 @@ def run_ours(args):
                    "l2": (("inputs larger than L2 (populations %.2f GB)" % (pop_bytes / 1e9)) if pop_bytes > L2_BYTES
                           else ("inputs fit in L2 (populations %.1f MB), steps back to back without a flush: "
                                 "an L2-resident figure, not an HBM one" % (pop_bytes / 1e6))),
-                   "warmup_steps_run": max(args.warmup, 32),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "bulk_share_of_step": round(step_frac, 4) if step_frac else None},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

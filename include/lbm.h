@@ -21,6 +21,9 @@
  *    in its own caching allocator) or with cudaMalloc.
  *  - Work is enqueued asynchronously on the domain's CUDA stream; functions
  *    that return data to the host synchronise that stream first.
+ *  - An entry point that works on a domain or batch makes that object's
+ *    device current while it runs and restores the calling thread's current
+ *    device before it returns (on success and on failure).
  *  - Lattice units: delta_x = delta_t = 1; velocities in cells per step.
  *    Node (x, y, z) sits at integer coordinates; cell index
  *    (z * ny + y) * nx + x; populations are laid out [Q][nz][ny][nx].
@@ -49,7 +52,8 @@ extern "C" {
 #define LBM_ERR_CUDA 3     /* a CUDA runtime call failed (message has the reason) */
 #define LBM_ERR_UNSTABLE 4 /* a NaN or |u| > 0.3 was detected in a checked step
                              (returned by the series / force reads of that solve) */
-#define LBM_ERR_TIMEOUT 5  /* a bounded device wait gave up (serving kernel) */
+#define LBM_ERR_TIMEOUT 5  /* a bounded device wait gave up (the mbarrier waits of
+                             the staged stream-collide kernel, LBM_STAGED=1) */
 #define LBM_ERR_STATE 6    /* call not allowed in the current state */
 
 /* ---- enumerations -------------------------------------------------------------- */
@@ -58,7 +62,9 @@ extern "C" {
 
 /* Precision modes.  FP64: FP64 arithmetic and FP64 storage of f.
  * FP32 / FP16: FP32 arithmetic, populations stored as deviations f_i - w_i
- * in FP32 / FP16.  The momentum-exchange sums are FP64 in every mode. */
+ * in FP32 / FP16.  The per-body momentum-exchange sums are FP64 (sequential,
+ * in link order) in the FP64 mode and exact 64-bit fixed point (units of
+ * 2^-36, order independent) in the FP32 / FP16 modes, read out as FP64. */
 #define LBM_FP64 0
 #define LBM_FP32 1
 #define LBM_FP16 2
@@ -250,6 +256,16 @@ int lbm_update_bodies(lbm_domain *dom, const lbm_body *host_bodies, int n);
  * of Sec. 3). */
 int lbm_step(lbm_domain *dom, int n);
 
+/* Record the domain's step graph now without taking a step.  lbm_step
+ * replays a captured CUDA graph of 16 steps for every run of >= 16 steps that
+ * starts at an even step, and records that graph at the first such run; a
+ * caller that wants no recording cost inside a later timed or
+ * latency-critical run calls this once beforehand (the graph is recorded for
+ * even starts whatever the parity of the current step).  It needs one step
+ * taken since the bodies were placed or changed (LBM_ERR_STATE before);
+ * LBM_OK without recording when the domain runs plain launches. */
+int lbm_prepare_graph(lbm_domain *dom);
+
 /* Copy series rows [first, first+count) of every body into host memory:
  * out[count][n_bodies][6] = (Fx, Fy, Fz, Tx, Ty, Tz) in form `kind`
  * (LBM_FT_*).  Waits only for the steps that wrote those rows (the end of
@@ -280,9 +296,16 @@ int lbm_get_populations(lbm_domain *dom, double *out);
  * LBM_NOALLOC_MAX_VALUES = 4,194,304 doubles (32 MiB), so it serves domains
  * with N*Q <= 4,194,304 and returns LBM_ERR_ARG, with a message naming the
  * limit, for larger ones (nothing is copied then).
- * - The first call on a device (with that device current) looks up the
- *   scratch address; later calls reuse it.  Make the first call before any
- *   stream capture on that device.
+ * - The scratch is a static reservation of 32 MiB per device, taken when
+ *   the first domain (or serving batch) is created on that device and held
+ *   until the process exits.  A serving batch's budget_bytes does not count
+ *   it: it is the same fixed 32 MiB however many solves are admitted.
+ *   lbm_create_domain looks its address up (with the device current), so
+ *   the export itself neither looks anything up nor allocates; if that
+ *   lookup failed, the call returns LBM_ERR_STATE and the domain is
+ *   otherwise unaffected.
+ * - Like every entry point, it restores the calling thread's current device
+ *   before it returns.
  * - No part of the scratch has to start at zero: a call writes every value it
  *   copies out.
  * - The scratch is shared by every domain on the device: calls that overlap

@@ -11,4 +11,4 @@ The arithmetic lives in ``lbm_oracle.c`` (plain C, FP64); this module is the
 ctypes marshalling around it.  Citations are to Giovacchini & Ortiz,
 arXiv:1407.4524 (section / equation labels of the paper).
 """
-from .oracle import Oracle, build, lattice_tables, sincos, SERIES_FIELDS  # noqa: F401
+from .oracle import Oracle, build, lattice_tables, sincos, threads, SERIES_FIELDS  # noqa: F401

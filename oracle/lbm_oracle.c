@@ -42,6 +42,9 @@
  * paper prints no numbers for them.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -77,7 +80,7 @@ typedef struct {
     double u0[3];
     double gravity[3]; /* acceleration of the free bodies (weight less buoyancy) */
     int edge_rule;     /* 0: wall / inlet faces are half-way links; 1: Zou-He nodes on the faces */
-    int pad;
+    int free_scheme;   /* free bodies: 0 explicit, 1 backward sets (Aidun), 2 predictor-corrector */
 } or_desc;
 
 typedef struct {
@@ -113,6 +116,10 @@ typedef struct {
     double edge_me[6];
     long long n_fallback;
     long long n_extrap; /* uncovered nodes refilled by extrapolation */
+    double *imp_prev;   /* free_scheme 1: impulsive terms of the previous displacement [nb][6] */
+    double *pre;        /* free_scheme 2: refill of the predicted uncovered nodes [Q][N] */
+    char *pre_set;      /* free_scheme 2: node uncovered by the prediction */
+    long long n_mismatch; /* free_scheme 2: nodes whose change the prediction got wrong */
 } or_dom;
 
 /* ---- lattice tables (standard D2Q9 / D3Q19; direction order fixed here) -- */
@@ -156,18 +163,15 @@ static long cell(const or_dom *o, int x, int y, int z)
 
 static int periodic(const or_dom *o, int axis) { return o->d.edge[2 * axis] == OR_PERIODIC; }
 
-/* minimum-image displacement x - X along one axis: on a periodic axis the
- * pose is first brought into [0, L), then at most one period is added or
- * removed (both of those steps are exact) */
+/* minimum-image displacement x - X along one axis (the torque lever arm of
+ * Eq. H and the body geometry on periodic axes): the plain definition
+ * v - L * round(v / L), with halves rounded up, for v = x - X */
 static double axis_disp(const or_dom *o, int axis, double x, double X)
 {
-    if (!periodic(o, axis)) return x - X;
+    double v = x - X;
+    if (!periodic(o, axis)) return v;
     double L = (double)o->n[axis];
-    double Xw = X - L * floor(X / L);
-    double v = x - Xw;
-    if (v > 0.5 * L) v = v - L;
-    else if (v < -0.5 * L) v = v + L;
-    return v;
+    return v - L * floor(v / L + 0.5);
 }
 
 /* prescribed pose: X(t) = X0 + (t - t0) U (the body Omega(t) of the problem
@@ -573,6 +577,9 @@ void or_destroy(or_dom *o)
     free(o->solid_next);
     free(o->b);
     free(o->series);
+    free(o->imp_prev);
+    free(o->pre);
+    free(o->pre_set);
     free(o);
 }
 
@@ -598,6 +605,7 @@ or_dom *or_create(const or_desc *d)
     }
     if (!(d->tau > 0.5)) return NULL;
     if (d->edge_rule != 0 && d->edge_rule != 1) return NULL;
+    if (d->free_scheme < 0 || d->free_scheme > 2) return NULL;
     if (d->edge_rule == 1) { /* Zou-He faces: an inner neighbour distinct from both faces */
         const int nn[3] = {d->nx, d->ny, d->nz};
         for (int a = 0; a < 3; ++a)
@@ -624,7 +632,12 @@ or_dom *or_create(const or_desc *d)
     o->u = (double *)calloc(3 * (size_t)o->N, sizeof(double));
     o->solid = (int *)malloc(sizeof(int) * (size_t)o->N);
     o->solid_next = (int *)malloc(sizeof(int) * (size_t)o->N);
-    if (!o->f || !o->fhat || !o->fnew || !o->rho || !o->u || !o->solid || !o->solid_next) {
+    if (d->free_scheme == 2) {
+        o->pre = (double *)malloc(pq);
+        o->pre_set = (char *)calloc((size_t)o->N, 1);
+    }
+    if (!o->f || !o->fhat || !o->fnew || !o->rho || !o->u || !o->solid || !o->solid_next ||
+        (d->free_scheme == 2 && (!o->pre || !o->pre_set))) {
         or_destroy(o);
         return NULL;
     }
@@ -647,6 +660,9 @@ int or_set_bodies(or_dom *o, const or_body *b, int nb)
         if (!o->b) return OR_ERR_OOM;
         memcpy(o->b, b, sizeof(or_body) * (size_t)nb);
     }
+    free(o->imp_prev);
+    o->imp_prev = (double *)calloc((size_t)(nb ? nb : 1) * 6, sizeof(double));
+    if (!o->imp_prev) return OR_ERR_OOM;
     free(o->series);
     o->series = NULL;
     o->nrec = o->cap = 0;
@@ -884,6 +900,163 @@ static void zouhe_node(or_dom *o, int x, int y, int z)
         if (unknown[i]) o->fnew[(long)i * N + xc] = f[i];
 }
 
+/* Covered (A+) and uncovered (A-) nodes between the solid set of t
+ * (o->solid) and o->solid_next, rasterised by the caller for the poses of t+1
+ * that the body records give (Sec. 3, after Eq. ForceInMovement).  An
+ * uncovered node is refilled (rule of the descriptor, u_B from the body's
+ * record at t+1); the impulsive terms of Eqs. ForceInMovement /
+ * TorqueInMovement, -sum_{A-} sum_i c_i f_i(A, t+1) + sum_{A+} sum_i c_i
+ * f_i(A, t+1) and the same with r(A) x (r about the pose of t, Xt), are added
+ * into imp[nb][6] in cell order; f(A, t+1) is the streamed value of a covered
+ * node and the refill of an uncovered one.  mode 0: the refill is stored in
+ * fnew; mode 1 (a predicted displacement): nothing is stored in fnew, the
+ * refill goes to o->pre (o->pre_set marks the node) and the predicted solid
+ * set is kept; mode 2 (the recomputed displacement after a prediction): a
+ * node the prediction also uncovered takes the refill the prediction
+ * computed, any other uncovered node a fresh one; nodes whose change differs
+ * from the prediction are counted. */
+static void cover_uncover(or_dom *o, long long t, const double *Xt, int mode, double *imp)
+{
+    const long N = o->N;
+    const int Q = o->Q;
+    const int nx = o->n[0], ny = o->n[1], nz = o->n[2];
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long A = cell(o, x, y, z);
+                int was = o->solid[A], now = o->solid_next[A];
+                if (mode == 2 && ((o->pre_set[A] == 2) != (was < 0 && now >= 0) ||
+                                  (o->pre_set[A] == 1) != (was >= 0 && now < 0)))
+                    o->n_mismatch++;
+                if ((was >= 0) == (now >= 0)) {
+                    if (mode == 2) o->pre_set[A] = 0;
+                    continue;
+                }
+                int bi = was >= 0 ? was : now;
+                const or_body *b = &o->b[bi];
+                double fv[19];
+                if (was >= 0) {
+                    if (mode == 2 && o->pre_set[A] == 1) {
+                        for (int i = 0; i < Q; ++i) fv[i] = o->pre[(long)i * N + A];
+                    } else {
+                        /* uncovered: refill with an equilibrium (Sec. 3) */
+                        double X1[3], r1[3], uB[3];
+                        pose(b, t + 1, X1);
+                        disp(o, X1, x, y, z, r1);
+                        body_velocity(b, r1, uB);
+                        double sum = 0.0, us[3] = {0.0, 0.0, 0.0};
+                        int cnt = 0;
+                        for (int i = 1; i < Q; ++i) {
+                            int p[3] = {x + o->c[i][0], y + o->c[i][1], z + o->c[i][2]}, ok = 1;
+                            for (int a = 0; a < 3; ++a) {
+                                if (p[a] >= 0 && p[a] < o->n[a]) continue;
+                                if (!periodic(o, a)) ok = 0;
+                                else p[a] += p[a] < 0 ? o->n[a] : -o->n[a];
+                            }
+                            if (!ok) continue;
+                            long nbc = cell(o, p[0], p[1], p[2]);
+                            if (o->solid[nbc] >= 0) continue;
+                            sum += o->rho[nbc];
+                            for (int a = 0; a < 3; ++a) us[a] += o->u[3 * nbc + a];
+                            cnt++;
+                        }
+                        double rbar = cnt ? sum / (double)cnt : o->d.rho0;
+                        double ufill[3];
+                        for (int a = 0; a < 3; ++a)
+                            ufill[a] = (o->d.refill == 1 && cnt) ? us[a] / (double)cnt : uB[a];
+                        long en[3];
+                        if (o->d.refill == 2 && extrap_nodes(o, b, t, x, y, z, en)) {
+                            for (int i = 0; i < Q; ++i) {
+                                const double *fh = o->fhat + (long)i * N;
+                                fv[i] = (3.0 * fh[en[0]] - 3.0 * fh[en[1]]) + fh[en[2]];
+                            }
+                            if (mode != 1) o->n_extrap++;
+                        } else {
+                            for (int i = 0; i < Q; ++i) fv[i] = feq(o, i, rbar, ufill);
+                        }
+                    }
+                    if (mode == 1) {
+                        for (int i = 0; i < Q; ++i) o->pre[(long)i * N + A] = fv[i];
+                        o->pre_set[A] = 1;
+                    } else {
+                        for (int i = 0; i < Q; ++i) o->fnew[(long)i * N + A] = fv[i];
+                        if (mode == 2) o->pre_set[A] = 0;
+                    }
+                } else {
+                    for (int i = 0; i < Q; ++i) fv[i] = o->fnew[(long)i * N + A];
+                    if (mode == 1) o->pre_set[A] = 2;
+                    if (mode == 2) o->pre_set[A] = 0;
+                }
+                /* impulsive terms of Eqs. ForceInMovement / TorqueInMovement */
+                double m[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < Q; ++i) {
+                    double fi = fv[i];
+                    m[0] += o->c[i][0] * fi;
+                    m[1] += o->c[i][1] * fi;
+                    m[2] += o->c[i][2] * fi;
+                }
+                double r[3], tq[3];
+                disp(o, Xt + 3 * bi, x, y, z, r);
+                cross(r, m, tq);
+                double *R = imp + (size_t)bi * 6;
+                if (was >= 0) {
+                    for (int a = 0; a < 3; ++a) {
+                        R[a] -= m[a];
+                        R[3 + a] -= tq[a];
+                    }
+                } else {
+                    for (int a = 0; a < 3; ++a) {
+                        R[a] += m[a];
+                        R[3 + a] += tq[a];
+                    }
+                }
+            }
+}
+
+/* Newton's and Euler's equations of a free body over one step (Sec. 4,
+ * forward Euler): with the flow force F and torque T of step t (plus weight
+ * less buoyancy (rho_b - rho0) V g) U(t+1) = U(t) + (F + (rho_b - rho0) V
+ * g) / M and W(t+1) = W(t) + T / I, M = rho_b V, V = pi R^2 nz (cylinder),
+ * pi R R2 nz (ellipse), 4/3 pi R^3 (sphere), I = M R^2 / 2 (cylinder, about
+ * z), M (R^2 + R2^2) / 4 (ellipse), 2/5 M R^2 (sphere).  The body record then
+ * starts at t+1: X(t+1) = X(t) + U(t) (semi = 0: the displacement the step
+ * already made) or X(t) + U(t+1) (semi = 1), likewise the orientation. */
+static void free_update(or_dom *o, or_body *b, long long t, const double F[3], const double T[3], int semi)
+{
+    const double PI = 3.14159265358979323846;
+    double V, I;
+    if (b->shape == OR_SHAPE_SPHERE) {
+        V = 4.0 / 3.0 * PI * b->R * b->R * b->R;
+    } else if (b->shape == OR_SHAPE_ELLIPSE) {
+        V = PI * b->R * b->R2 * (double)o->n[2];
+    } else {
+        V = PI * b->R * b->R * (double)o->n[2];
+    }
+    double M = b->density_ratio * o->d.rho0 * V;
+    if (b->shape == OR_SHAPE_SPHERE) I = 0.4 * M * b->R * b->R;
+    else if (b->shape == OR_SHAPE_ELLIPSE) I = 0.25 * M * (b->R * b->R + b->R2 * b->R2);
+    else I = 0.5 * M * b->R * b->R;
+    double X1[3], X0[3];
+    pose(b, t + 1, X1);
+    pose(b, t, X0);
+    double th1 = orient(b, t + 1);
+    double th0 = orient(b, t);
+    for (int a = 0; a < 3; ++a)
+        b->U[a] = b->U[a] + (F[a] + (b->density_ratio - 1.0) * o->d.rho0 * V * o->d.gravity[a]) / M;
+    if (b->shape == OR_SHAPE_SPHERE) {
+        for (int a = 0; a < 3; ++a) b->W[a] = b->W[a] + T[a] / I;
+    } else {
+        b->W[2] = b->W[2] + T[2] / I;
+    }
+    if (semi) {
+        for (int a = 0; a < 3; ++a) X1[a] = X0[a] + b->U[a];
+        th1 = th0 + b->W[2];
+    }
+    for (int a = 0; a < 3; ++a) b->X0[a] = X1[a];
+    b->theta0 = th1;
+    b->t0 = t + 1;
+}
+
 static int one_step(or_dom *o)
 {
     const long N = o->N;
@@ -1003,131 +1176,91 @@ static int one_step(or_dom *o)
                 }
             }
 
-    /* 5: prescribed motion; covered (A+) and uncovered (A-) nodes */
-    int moving = 0;
+    /* 5 + 6: body motion.  Prescribed bodies move with their given velocity;
+     * the covered (A+) and uncovered (A-) nodes between t and t+1 give the
+     * impulsive terms of Eqs. ForceInMovement / TorqueInMovement and the
+     * refill of the uncovered nodes (Sec. 3).  Free bodies follow Newton's
+     * and Euler's equations (Sec. 4) by one of three schemes:
+     *   0  explicit: the body moves from t to t+1 with U(t), so the sets
+     *      A+/A- of this step are known before the force; then U(t+1) from
+     *      the force of step t (static plus impulsive terms);
+     *   1  backward sets (the Aidun-type approximation of Sec. 3): the force
+     *      at t takes the impulsive terms of the nodes that entered and left
+     *      the body between t-1 and t, so U(t+1) follows before the body
+     *      moves, and the displacement from t to t+1 is made with U(t+1);
+     *   2  predictor-corrector (the second approximation of Sec. 3): the sets
+     *      of a predicted displacement with U(t) give the force at t, U(t+1)
+     *      follows, and the displacement is recomputed with U(t+1) -- two
+     *      displacements per step; a node uncovered by both keeps the refill
+     *      the force used. */
+    const int scheme = o->d.free_scheme;
+    int moving = 0, any_free = 0;
     for (int bi = 0; bi < o->nb; ++bi) {
         const or_body *b = &o->b[bi];
         for (int a = 0; a < 3; ++a)
             if (b->U[a] != 0.0 || b->W[a] != 0.0) moving = 1;
+        if (b->free) moving = any_free = 1;
     }
+    const size_t nb6 = (size_t)(o->nb ? o->nb : 1) * 6;
+    double *imp = (double *)calloc(nb6, sizeof(double));
+    double *imp_pred = (double *)calloc(nb6, sizeof(double));
+    double *Xt = (double *)malloc(sizeof(double) * (size_t)(o->nb ? o->nb : 1) * 3);
+    if (!imp || !imp_pred || !Xt) {
+        free(imp);
+        free(imp_pred);
+        free(Xt);
+        free(row);
+        return OR_ERR_OOM;
+    }
+    for (int bi = 0; bi < o->nb; ++bi) pose(&o->b[bi], t, Xt + 3 * bi);
+    const int predict = scheme == 2 && any_free;
+    if (moving && predict) {
+        rasterise(o, t + 1, o->solid_next); /* free bodies moving with U(t) */
+        cover_uncover(o, t, Xt, 1, imp_pred);
+    }
+    if (scheme != 0) /* semi-implicit schemes: the velocity of t+1 first */
+        for (int bi = 0; bi < o->nb; ++bi) {
+            if (!o->b[bi].free) continue;
+            const double *Rw = row + (size_t)bi * OR_ROW;
+            const double *ip = scheme == 1 ? o->imp_prev + 6 * bi : imp_pred + 6 * bi;
+            double F[3], T[3];
+            for (int k = 0; k < 3; ++k) {
+                F[k] = Rw[k] + ip[k];
+                T[k] = Rw[3 + k] + ip[3 + k];
+            }
+            free_update(o, &o->b[bi], t, F, T, 1);
+        }
     if (moving) {
-        rasterise(o, t + 1, o->solid_next);
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) {
-                    long A = cell(o, x, y, z);
-                    int was = o->solid[A], now = o->solid_next[A];
-                    if ((was >= 0) == (now >= 0)) continue;
-                    int bi = was >= 0 ? was : now;
-                    const or_body *b = &o->b[bi];
-                    if (was >= 0) {
-                        /* uncovered: refill with an equilibrium (Sec. 3) */
-                        double X1[3], r1[3], uB[3];
-                        pose(b, t + 1, X1);
-                        disp(o, X1, x, y, z, r1);
-                        body_velocity(b, r1, uB);
-                        double sum = 0.0, us[3] = {0.0, 0.0, 0.0};
-                        int cnt = 0;
-                        for (int i = 1; i < Q; ++i) {
-                            int p[3] = {x + o->c[i][0], y + o->c[i][1], z + o->c[i][2]}, ok = 1;
-                            for (int a = 0; a < 3; ++a) {
-                                if (p[a] >= 0 && p[a] < o->n[a]) continue;
-                                if (!periodic(o, a)) ok = 0;
-                                else p[a] += p[a] < 0 ? o->n[a] : -o->n[a];
-                            }
-                            if (!ok) continue;
-                            long nbc = cell(o, p[0], p[1], p[2]);
-                            if (o->solid[nbc] >= 0) continue;
-                            sum += o->rho[nbc];
-                            for (int a = 0; a < 3; ++a) us[a] += o->u[3 * nbc + a];
-                            cnt++;
-                        }
-                        double rbar = cnt ? sum / (double)cnt : o->d.rho0;
-                        double ufill[3];
-                        for (int a = 0; a < 3; ++a)
-                            ufill[a] = (o->d.refill == 1 && cnt) ? us[a] / (double)cnt : uB[a];
-                        long en[3];
-                        if (o->d.refill == 2 && extrap_nodes(o, b, t, x, y, z, en)) {
-                            for (int i = 0; i < Q; ++i) {
-                                const double *fh = o->fhat + (long)i * N;
-                                o->fnew[(long)i * N + A] = (3.0 * fh[en[0]] - 3.0 * fh[en[1]]) + fh[en[2]];
-                            }
-                            o->n_extrap++;
-                        } else {
-                            for (int i = 0; i < Q; ++i) o->fnew[(long)i * N + A] = feq(o, i, rbar, ufill);
-                        }
-                    }
-                    /* impulsive terms of Eqs. ForceInMovement / TorqueInMovement */
-                    double m[3] = {0.0, 0.0, 0.0};
-                    for (int i = 0; i < Q; ++i) {
-                        double fi = o->fnew[(long)i * N + A];
-                        m[0] += o->c[i][0] * fi;
-                        m[1] += o->c[i][1] * fi;
-                        m[2] += o->c[i][2] * fi;
-                    }
-                    double X[3], r[3], tq[3];
-                    pose(b, t, X);
-                    disp(o, X, x, y, z, r);
-                    cross(r, m, tq);
-                    double *R = row + (size_t)bi * OR_ROW;
-                    if (was >= 0) {
-                        for (int a = 0; a < 3; ++a) {
-                            R[6 + a] -= m[a];
-                            R[9 + a] -= tq[a];
-                        }
-                    } else {
-                        for (int a = 0; a < 3; ++a) {
-                            R[6 + a] += m[a];
-                            R[9 + a] += tq[a];
-                        }
-                    }
-                }
+        rasterise(o, t + 1, o->solid_next); /* the poses of t+1 */
+        cover_uncover(o, t, Xt, predict ? 2 : 0, imp);
         int *tmp = o->solid;
         o->solid = o->solid_next;
         o->solid_next = tmp;
     }
-
-    /* 6: free bodies -- Newton's and Euler's equations integrated by forward
-     * Euler (the paper's test section): the pose advances with U(t) (so the
-     * A+/A- sets of this step were explicit), then the lattice-frame force and
-     * torque of step t (Eqs. ForceInMovement / TorqueInMovement: static plus
-     * impulsive terms), with weight less buoyancy (rho_b - rho0) V g, give
-     * U(t+1) and W(t+1).  V: pi R^2 nz (cylinder), 4/3 pi R^3 (sphere); the
-     * moment of inertia about the centre M R^2 / 2 (cylinder, about z) or
-     * 2/5 M R^2 (sphere). */
     for (int bi = 0; bi < o->nb; ++bi) {
-        or_body *b = &o->b[bi];
-        if (!b->free) continue;
-        const double *Rw = row + (size_t)bi * OR_ROW;
-        const double PI = 3.14159265358979323846;
-        double V, I;
-        if (b->shape == OR_SHAPE_SPHERE) {
-            V = 4.0 / 3.0 * PI * b->R * b->R * b->R;
-        } else if (b->shape == OR_SHAPE_ELLIPSE) {
-            V = PI * b->R * b->R2 * (double)o->n[2];
-        } else {
-            V = PI * b->R * b->R * (double)o->n[2];
-        }
-        double M = b->density_ratio * o->d.rho0 * V;
-        if (b->shape == OR_SHAPE_SPHERE) I = 0.4 * M * b->R * b->R;
-        else if (b->shape == OR_SHAPE_ELLIPSE) I = 0.25 * M * (b->R * b->R + b->R2 * b->R2);
-        else I = 0.5 * M * b->R * b->R;
-        double X1[3];
-        pose(b, t + 1, X1);
-        double th1 = orient(b, t + 1);
-        for (int a = 0; a < 3; ++a) b->X0[a] = X1[a];
-        b->theta0 = th1;
-        b->t0 = t + 1;
-        for (int a = 0; a < 3; ++a) {
-            double F = Rw[a] + Rw[6 + a];
-            b->U[a] = b->U[a] + (F + (b->density_ratio - 1.0) * o->d.rho0 * V * o->d.gravity[a]) / M;
-        }
-        if (b->shape == OR_SHAPE_SPHERE) {
-            for (int a = 0; a < 3; ++a) b->W[a] = b->W[a] + (Rw[3 + a] + Rw[9 + a]) / I;
-        } else {
-            b->W[2] = b->W[2] + (Rw[5] + Rw[11]) / I;
-        }
+        double *R = row + (size_t)bi * OR_ROW;
+        const or_body *b = &o->b[bi];
+        const double *ip = imp + 6 * bi;
+        if (b->free && scheme == 1) ip = o->imp_prev + 6 * bi;
+        if (b->free && scheme == 2) ip = imp_pred + 6 * bi;
+        for (int k = 0; k < 6; ++k) R[6 + k] = ip[k];
+        if (b->free && scheme == 1)
+            for (int k = 0; k < 6; ++k) o->imp_prev[6 * bi + k] = imp[6 * bi + k];
     }
+    if (scheme == 0) /* explicit: U(t+1) from the force of step t */
+        for (int bi = 0; bi < o->nb; ++bi) {
+            if (!o->b[bi].free) continue;
+            const double *Rw = row + (size_t)bi * OR_ROW;
+            double F[3], T[3];
+            for (int k = 0; k < 3; ++k) {
+                F[k] = Rw[k] + Rw[6 + k];
+                T[k] = Rw[3 + k] + Rw[9 + k];
+            }
+            free_update(o, &o->b[bi], t, F, T, 0);
+        }
+    free(imp);
+    free(imp_pred);
+    free(Xt);
 
     double *tmp = o->f;
     o->f = o->fnew;
@@ -1148,9 +1281,20 @@ int or_step(or_dom *o, int n)
     return OR_OK;
 }
 
+/* threads the OpenMP loops run on (1 when built without OpenMP) */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 long long or_time(const or_dom *o) { return o ? o->t : -1; }
 long long or_fallbacks(const or_dom *o) { return o ? o->n_fallback : -1; }
 long long or_extrapolated(const or_dom *o) { return o ? o->n_extrap : -1; }
+long long or_mismatches(const or_dom *o) { return o ? o->n_mismatch : -1; }
 
 /* series rows [first, first+count) of every body: out[count][nb][18] with
  * Fs Ts (static form), Fi Ti (impulsive terms), Fm Tm (moving frame) */

@@ -29,7 +29,7 @@ class _Desc(C.Structure):
         ("has_force", C.c_int), ("refill", C.c_int),
         ("tau", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double),
         ("g", C.c_double * 3), ("u0", C.c_double * 3), ("gravity", C.c_double * 3),
-        ("edge_rule", C.c_int), ("pad", C.c_int),
+        ("edge_rule", C.c_int), ("free_scheme", C.c_int),
     ]
 
 
@@ -79,6 +79,8 @@ def _load():
     lib.or_fallbacks.argtypes = [P]
     lib.or_extrapolated.restype = C.c_longlong
     lib.or_extrapolated.argtypes = [P]
+    lib.or_mismatches.restype = C.c_longlong
+    lib.or_mismatches.argtypes = [P]
     lib.or_get_series.argtypes = [P, C.c_longlong, C.c_longlong, P]
     for name in ("or_get_f", "or_get_fhat", "or_get_macro", "or_get_solid", "or_get_edge_me", "or_get_bodies"):
         getattr(lib, name).argtypes = [P, P]
@@ -86,8 +88,15 @@ def _load():
     lib.or_links.argtypes = [P, C.c_int, C.c_longlong, P, P, P]
     lib.or_lattice.argtypes = [C.c_int, P, P, P]
     lib.or_sincos.argtypes = [C.c_double, P, P]
+    lib.or_threads.restype = C.c_int
+    lib.or_threads.argtypes = []
     _lib = lib
     return lib
+
+
+def threads() -> int:
+    """threads the oracle's OpenMP loops use (1 if it was built without OpenMP)"""
+    return int(_load().or_threads())
 
 
 def sincos(x: float):
@@ -150,6 +159,8 @@ class Oracle:
     "periodic" | (lo, hi) kinds among "wall", "inlet", "outlet"), ``inlet``
     ({"profile": "uniform"/"parabolic", "u": ...}), ``force``, ``u0``,
     ``refill`` ("uB"/"ubar"/"extrap"), ``gravity`` (acceleration of free bodies),
+    ``free_scheme`` ("explicit" | "aidun" | "predictor": how free bodies take
+    the covered / uncovered sets of their force, Sec. 3),
     ``edge_rule`` ("link": wall / inlet faces as half-way links; "zouhe": Zou-He
     nodes on the faces),
     ``bodies`` (list of dicts: shape, R, X0, U, W, halfway, invert, t0, free,
@@ -178,6 +189,7 @@ class Oracle:
             d.u0[k] = float(u0[k]) if k < len(u0) else 0.0
         d.refill = {"uB": 0, "ubar": 1, "extrap": 2}[spec.get("refill", "uB")]
         d.edge_rule = {"link": 0, "zouhe": 1}[spec.get("edge_rule", "link")]
+        d.free_scheme = {"explicit": 0, "aidun": 1, "predictor": 2}[spec.get("free_scheme", "explicit")]
         gv = tuple(spec.get("gravity", (0.0, 0.0, 0.0)))
         for k in range(3):
             d.gravity[k] = float(gv[k]) if k < len(gv) else 0.0
@@ -215,6 +227,11 @@ class Oracle:
     @property
     def fallbacks(self) -> int:
         return int(self.lib.or_fallbacks(self.h))
+
+    def mismatches(self) -> int:
+        """free_scheme "predictor": nodes whose covering or uncovering the
+        predicted displacement got wrong so far"""
+        return int(self.lib.or_mismatches(self.h))
 
     def extrapolated(self) -> int:
         """Uncovered nodes refilled by extrapolation so far (refill "extrap")."""

@@ -19,10 +19,12 @@
 // device buffer is recorded with its size at allocation, in order: that list
 // is the device part of a state snapshot (lbm_save_state / lbm_load_state).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -77,6 +79,8 @@ cudaError_t launch_finish(int Q, int prec, const Params &p, const StepBufs &sb, 
 
 using namespace lbm;
 
+void noalloc_scratch_setup(int dev);
+
 namespace {
 
 thread_local std::string g_err;
@@ -93,6 +97,30 @@ int fail(int code, const std::string &msg) {
     } while (0)
 
 constexpr double PI = 3.14159265358979323846;
+
+// Makes `dev` the calling thread's current device for the guard's lifetime
+// and gives the caller's own current device back afterwards: no entry point
+// leaves the calling thread's current device changed.
+struct DevGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DevGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DevGuard(const DevGuard &) = delete;
+    DevGuard &operator=(const DevGuard &) = delete;
+};
+
+// the device of a domain / batch current for the rest of the entry point
+#define DEVICE_SCOPE(dev)                                                                                       \
+    DevGuard dev_guard_(dev);                                                                                   \
+    if (dev_guard_.err != cudaSuccess)                                                                          \
+        return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(dev_guard_.err))
 
 } // namespace
 
@@ -545,6 +573,7 @@ int timing_events(lbm_domain *D, cudaEvent_t &a, cudaEvent_t &b) {
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     if (prec != LBM_FP64 && D->nb) return do_step_overlapped(D);
+    D->lists_dirty = false; // boundary-node lists belong to the overlapped path only
     if (D->nb && (D->n_moving || D->prep_dirty)) {
         // the A+/A- lists of the previous step update the solid flags of t
         CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
@@ -696,8 +725,9 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     }
     if ((d.alloc == nullptr) != (d.free == nullptr)) return fail(LBM_ERR_ARG, "alloc and free go together");
 
-    cudaError_t e = cudaSetDevice(d.device);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    DEVICE_SCOPE(d.device);
+    cudaError_t e = cudaSuccess;
+    noalloc_scratch_setup(d.device); // before any allocation or stream capture of this domain
 
     lbm_domain *D = new lbm_domain();
     D->d = d;
@@ -807,6 +837,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
 
 int lbm_destroy_domain(lbm_domain *D) {
     if (!D) return LBM_OK;
+    DEVICE_SCOPE(D->d.device);
     cudaStreamSynchronize(D->s);
     free_body_buffers(D);
     for (int k = 0; k < 2; ++k) {
@@ -867,6 +898,7 @@ int place_bodies(lbm_domain *D, const lbm_body *hb, int n);
 
 int lbm_set_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if (!D || n < 0 || (n > 0 && !hb)) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     if (D->t != 0) return fail(LBM_ERR_STATE, "bodies can only be placed at t = 0");
     if (n > 65534) return fail(LBM_ERR_ARG, "at most 65534 bodies");
     int rc = validate_bodies(D, hb, n);
@@ -991,6 +1023,7 @@ int place_bodies(lbm_domain *D, const lbm_body *hb, int n) {
 
 int lbm_update_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if (!D || !hb || n != D->nb) return fail(LBM_ERR_ARG, "update needs the same number of bodies");
+    DEVICE_SCOPE(D->d.device);
     if (D->n_free) return fail(LBM_ERR_STATE, "free bodies move with the flow; their kinematics cannot be set");
     for (int b = 0; b < n; ++b) {
         const lbm_body &o = D->hb[b], &v = hb[b];
@@ -1087,7 +1120,7 @@ int capture_graph(lbm_domain *D) {
 
 int lbm_step(lbm_domain *D, int n) {
     if (!D || n < 0) return fail(LBM_ERR_ARG, "invalid arguments");
-    CK(cudaSetDevice(D->d.device));
+    DEVICE_SCOPE(D->d.device);
     const int G = lbm_domain::GRAPH_STEPS;
     for (int k = 0; k < n;) {
         const bool graph = !D->graph_failed && !D->prep_dirty && !D->lists_dirty && (D->t & 1) == 0 && n - k >= G;
@@ -1115,6 +1148,23 @@ int lbm_step(lbm_domain *D, int n) {
     return LBM_OK;
 }
 
+int lbm_prepare_graph(lbm_domain *D) {
+    if (!D) return fail(LBM_ERR_ARG, "null domain");
+    DEVICE_SCOPE(D->d.device);
+    if (D->graph_failed) return LBM_OK; // this domain runs plain launches
+    if (D->prep_dirty || D->lists_dirty)
+        return fail(LBM_ERR_STATE, "the step graph is recorded after the first step of a body set");
+    if (D->gexec && !D->graph_dirty) return LBM_OK;
+    // a graph starts at an even step (the population buffers alternate with
+    // the step parity; the kernels read the step index on the device)
+    const int64_t t = D->t;
+    D->t = t & ~(int64_t)1;
+    const int rc = capture_graph(D);
+    D->t = t;
+    if (rc && !D->graph_failed) return rc;
+    return LBM_OK;
+}
+
 namespace {
 // Makes D->sio wait until the steps before `t_end` are complete: on the
 // earliest recorded step event that covers them, else on all of D->s.
@@ -1133,6 +1183,7 @@ int wait_steps(lbm_domain *D, int64_t t_end) {
 
 int lbm_get_series(lbm_domain *D, int64_t first, int64_t count, double *out) {
     if (!D || !out || first < 0 || count < 0) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     if (first + count > D->t) return fail(LBM_ERR_ARG, "rows beyond the current step");
     if (first < D->t - D->series_cap) return fail(LBM_ERR_ARG, "rows older than the series ring");
     if (D->nb == 0 || count == 0) return LBM_OK;
@@ -1187,6 +1238,7 @@ int lbm_get_force_torque(lbm_domain *D, int64_t first, int64_t count, int kind, 
 
 int lbm_get_populations(lbm_domain *D, double *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     const size_t n = (size_t)D->p.N * D->Q;
     void *tmp = D->alloc(n * sizeof(double));
     if (!tmp) return fail(LBM_ERR_OOM, "temporary export buffer");
@@ -1203,6 +1255,7 @@ constexpr long long IO_CHUNK = 1ll << 22;
 
 int lbm_set_populations(lbm_domain *D, const double *f) {
     if (!D || !f) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     const long long N = D->p.N, chunk = std::min(N, IO_CHUNK);
     double *stage = (double *)D->alloc((size_t)chunk * D->Q * sizeof(double));
     if (!stage) return fail(LBM_ERR_OOM, "temporary staging buffer");
@@ -1224,6 +1277,7 @@ int lbm_set_populations(lbm_domain *D, const double *f) {
 
 int lbm_get_macros(lbm_domain *D, double *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     const long long N = D->p.N, chunk = std::min(N, IO_CHUNK);
     double *stage = (double *)D->alloc((size_t)chunk * 4 * sizeof(double));
     if (!stage) return fail(LBM_ERR_OOM, "temporary staging buffer");
@@ -1244,6 +1298,7 @@ int lbm_get_macros(lbm_domain *D, double *out) {
 
 int lbm_get_body_state(lbm_domain *D, double *out) {
     if (!D || (D->nb && !out)) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     if (D->nb == 0) return LBM_OK;
     std::vector<BodyDev> hb((size_t)D->nb);
     CK(cudaStreamSynchronize(D->s));
@@ -1263,6 +1318,7 @@ int lbm_get_body_state(lbm_domain *D, double *out) {
 
 int lbm_get_solid(lbm_domain *D, int32_t *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     const size_t N = (size_t)D->p.N;
     std::vector<uint16_t> o(N);
     CK(cudaStreamSynchronize(D->s));
@@ -1296,6 +1352,7 @@ int64_t lbm_state_bytes(const lbm_domain *D) {
 
 int lbm_save_state(lbm_domain *D, void *out, int64_t cap) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     const int64_t need = lbm_state_bytes(D);
     if (cap < need) return fail(LBM_ERR_ARG, "snapshot buffer smaller than lbm_state_bytes");
     CK(cudaStreamSynchronize(D->s));
@@ -1335,6 +1392,7 @@ int lbm_save_state(lbm_domain *D, void *out, int64_t cap) {
 
 int lbm_load_state(lbm_domain *D, const void *in, int64_t size) {
     if (!D || !in || size < (int64_t)sizeof(SnapHeader)) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     const char *p = (const char *)in;
     SnapHeader h;
     std::memcpy(&h, p, sizeof(h));
@@ -1382,6 +1440,7 @@ int lbm_load_state(lbm_domain *D, const void *in, int64_t size) {
 
 int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     std::memset(out, 0, sizeof(*out));
     CK(cudaStreamSynchronize(D->s));
     unsigned long long c[N_COUNTERS] = {};
@@ -1422,6 +1481,7 @@ int lbm_set_stream(lbm_domain *D, void *stream) {
 
 int lbm_set_kernel_timing(lbm_domain *D, int enable) {
     if (!D) return fail(LBM_ERR_ARG, "null domain");
+    DEVICE_SCOPE(D->d.device);
     CK(cudaStreamSynchronize(D->s));
     if (D->timing != (enable != 0)) D->graph_dirty = true; // the graph holds the timing events or not
     D->timing = enable != 0;
@@ -1432,6 +1492,7 @@ int lbm_set_kernel_timing(lbm_domain *D, int enable) {
 
 int lbm_kernel_time(lbm_domain *D, int64_t *launches, double *total_ms) {
     if (!D || !launches || !total_ms) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(D->d.device);
     CK(cudaStreamSynchronize(D->s));
     double tot = 0.0;
     for (size_t k = 0; k + 1 < D->ev_used; k += 2) {
@@ -1728,8 +1789,8 @@ int lbm_batch_create(const lbm_batch_desc *desc, lbm_batch **out) {
     if (d.budget_bytes <= 0) return fail(LBM_ERR_ARG, "budget_bytes must be > 0");
     if (d.reserved != 0) return fail(LBM_ERR_ARG, "reserved must be 0");
     if ((d.alloc == nullptr) != (d.free == nullptr)) return fail(LBM_ERR_ARG, "alloc and free go together");
-    cudaError_t e = cudaSetDevice(d.device);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    DEVICE_SCOPE(d.device);
+    cudaError_t e = cudaSuccess;
     lbm_batch *B = new lbm_batch();
     B->d = d;
     B->tpl = d.ticks_per_launch > 0 ? d.ticks_per_launch : 32;
@@ -1772,6 +1833,7 @@ int lbm_batch_create(const lbm_batch_desc *desc, lbm_batch **out) {
 
 int lbm_batch_destroy(lbm_batch *B) {
     if (!B) return LBM_OK;
+    DEVICE_SCOPE(B->d.device);
     if (B->s) cudaStreamSynchronize(B->s);
     for (auto &S : B->slots)
         if (S.D) lbm_destroy_domain(S.D);
@@ -1821,7 +1883,7 @@ int lbm_batch_admit(lbm_batch *B, const lbm_domain_desc *desc, const lbm_body *h
     if (B->used + need > B->d.budget_bytes)
         return fail(LBM_ERR_OOM, "solve needs " + std::to_string(need) + " bytes, " +
                                      std::to_string(B->d.budget_bytes - B->used) + " left in the budget");
-    CK(cudaSetDevice(B->d.device));
+    DEVICE_SCOPE(B->d.device);
     lbm_domain *D = nullptr;
     if ((rc = lbm_create_domain(&d, &D))) return rc;
     if ((rc = lbm_set_bodies(D, hb, n))) {
@@ -1884,7 +1946,7 @@ int lbm_batch_admit(lbm_batch *B, const lbm_domain_desc *desc, const lbm_body *h
 
 int lbm_batch_run(lbm_batch *B, int n) {
     if (!B || n < 0) return fail(LBM_ERR_ARG, "invalid arguments");
-    CK(cudaSetDevice(B->d.device));
+    DEVICE_SCOPE(B->d.device);
     if (B->dirty) {
         int rc = batch_rebuild(B);
         if (rc) return rc;
@@ -1904,6 +1966,7 @@ int lbm_batch_run(lbm_batch *B, int n) {
 
 int lbm_batch_poll(lbm_batch *B, int *slots_out, int cap, int *count_out) {
     if (!B || !count_out || cap < 0 || (cap > 0 && !slots_out)) return fail(LBM_ERR_ARG, "invalid arguments");
+    DEVICE_SCOPE(B->d.device);
     CK(cudaStreamSynchronize(B->s));
     int c = 0;
     for (int sl = 0; sl < (int)B->slots.size() && c < cap; ++sl) {
@@ -1931,6 +1994,7 @@ int64_t lbm_batch_time(const lbm_batch *B, int slot) {
 int lbm_batch_release(lbm_batch *B, int slot) {
     if (!B || slot < 0 || slot >= (int)B->slots.size() || !B->slots[slot].D)
         return fail(LBM_ERR_ARG, "no solve in this slot");
+    DEVICE_SCOPE(B->d.device);
     CK(cudaStreamSynchronize(B->s));
     auto &S = B->slots[slot];
     const bool running = S.D->t < S.t_end;
@@ -1962,17 +2026,35 @@ int lbm_batch_usage(const lbm_batch *B, int *resident, int64_t *bytes) {
 // its memory to an exact budget; a monitoring thread that must not trigger
 // the device-wide synchronisation of releasing CUDA memory) use
 // lbm_get_populations_noalloc, which runs the same export kernel into this
-// fixed scratch array instead.  Its address is looked up once per device
-// (with the device current) and cached.  Nothing in it has to start at zero:
-// each call writes all N*Q values it copies out.  Concurrent calls share it
-// and would race.
+// fixed scratch array instead.  The array is part of this file's device
+// module: it takes its 32 MiB on a device when that module is loaded there.
+// lbm_create_domain resolves its address once per device (with the device
+// current), which also loads the module under lazy module loading, and
+// caches it; the export itself then never looks the symbol up, loads a
+// module or allocates.  Nothing in it has to start at zero: each call writes
+// all N*Q values it copies out.  Calls that overlap on the GPU share it and
+// race.
 
 static __device__ __align__(256) double g_export_scratch[LBM_NOALLOC_MAX_VALUES];
 
 namespace {
 constexpr int NOALLOC_MAX_DEVICES = 64;
-double *g_export_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+std::atomic<double *> g_export_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_export_scratch_mu;
 } // namespace
+
+// called by lbm_create_domain with `dev` current; a failed lookup leaves the
+// domain usable (only the no-allocation export then reports LBM_ERR_STATE)
+void noalloc_scratch_setup(int dev) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES || g_export_scratch_ptr[dev].load()) return;
+    std::lock_guard<std::mutex> lk(g_export_scratch_mu);
+    if (g_export_scratch_ptr[dev].load()) return;
+    double *ptr = nullptr;
+    if (cudaGetSymbolAddress((void **)&ptr, g_export_scratch) == cudaSuccess && ptr)
+        g_export_scratch_ptr[dev].store(ptr);
+    else
+        cudaGetLastError(); // not sticky: clear it, the domain does not depend on the scratch
+}
 
 extern "C" int lbm_get_populations_noalloc(lbm_domain *D, double *out) {
     if (!D || !out) return fail(LBM_ERR_ARG, "invalid arguments");
@@ -1984,15 +2066,9 @@ extern "C" int lbm_get_populations_noalloc(lbm_domain *D, double *out) {
                                      " (use lbm_get_populations)");
     const int dev = D->d.device;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(LBM_ERR_ARG, "device index out of range");
-    CK(cudaSetDevice(dev));
-    if (!g_export_scratch_ptr[dev]) { // set-up, once per device
-        double *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_export_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(LBM_ERR_CUDA, std::string("scratch address lookup: ") + cudaGetErrorString(e));
-        g_export_scratch_ptr[dev] = ptr;
-    }
-    double *scratch = g_export_scratch_ptr[dev];
+    double *scratch = g_export_scratch_ptr[dev].load();
+    if (!scratch) return fail(LBM_ERR_STATE, "the fixed export scratch could not be set up on this device");
+    DEVICE_SCOPE(dev);
     CK(launch_export(D->Q, D->prec, D->p, D->pop[D->t & 1], scratch, D->s));
     CK(cudaMemcpyAsync(out, scratch, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, D->s));
     CK(cudaStreamSynchronize(D->s));

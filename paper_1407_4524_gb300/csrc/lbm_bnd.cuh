@@ -94,15 +94,7 @@ __device__ __forceinline__ void bnd_node(const Params &p, const BndArgs &a, cons
         const double *Pf = a.poses + (long long)bi * POSE_STRIDE + 12; // floor, frac of the pose at t
         float d[3];
         const int c3[3] = {x, y, z};
-        for (int q = 0; q < 3; ++q) {
-            int kk = c3[q] - (int)Pf[q];
-            if (p.per[q]) {
-                const int n = axis_len(p, q);
-                if (2 * kk > n) kk -= n;
-                else if (2 * kk < -n) kk += n;
-            }
-            d[q] = (float)kk - (float)Pf[3 + q];
-        }
+        for (int q = 0; q < 3; ++q) d[q] = frame_axis(c3[q] - (int)Pf[q], (float)Pf[3 + q], axis_len(p, q), p.per[q]);
         const double *Po = a.poses + (long long)bi * POSE_STRIDE + 18; // orientation at t
         const float dl = link_delta_f(Bi.halfway, Bi.shape, (float)Bi.R, (float)Bi.R2, (float)Po[0], (float)Po[1],
                                       d, cxi, cyi, czi);

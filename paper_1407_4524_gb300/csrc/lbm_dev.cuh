@@ -249,21 +249,29 @@ __device__ __forceinline__ void wrap_pose(const Params &p, const double X[3], do
     }
 }
 
-// minimum-image displacement x - X from the wrapped pose: at most one period
-// is added or removed, exactly
-__device__ __forceinline__ double axis_disp(const Params &p, int a, double x, double Xw) {
-    double v = x - Xw;
+// minimum-image displacement along one axis from the unwrapped pose X
+// (reading of the torque reference, Eq. H of Sec. 3): v = x - X, then on a
+// periodic axis v - L floor(v / L + 1/2) -- the oracle's expression, each
+// operation rounded explicitly so that no unit's contraction flags change it
+__device__ __forceinline__ double axis_disp(const Params &p, int a, double x, double X) {
+    const double v = __dsub_rn(x, X);
     if (!p.per[a]) return v;
-    double L = (double)axis_len(p, a);
-    if (v > 0.5 * L) v = v - L;
-    else if (v < -0.5 * L) v = v + L;
-    return v;
+    const double L = (double)axis_len(p, a);
+    return __dsub_rn(v, __dmul_rn(L, floor(__dadd_rn(__ddiv_rn(v, L), 0.5))));
 }
 
-__device__ __forceinline__ void disp(const Params &p, const double Xw[3], int x, int y, int z, double r[3]) {
-    r[0] = axis_disp(p, 0, (double)x, Xw[0]);
-    r[1] = axis_disp(p, 1, (double)y, Xw[1]);
-    r[2] = axis_disp(p, 2, (double)z, Xw[2]);
+// displacement of node (x, y, z) from the unwrapped pose X
+__device__ __forceinline__ void disp_from(const Params &p, const double X[3], int x, int y, int z, double r[3]) {
+    r[0] = axis_disp(p, 0, (double)x, X[0]);
+    r[1] = axis_disp(p, 1, (double)y, X[1]);
+    r[2] = axis_disp(p, 2, (double)z, X[2]);
+}
+
+// the same from Pw, the wrapped pose of t or t+1 inside a pose record: the
+// unwrapped pose of that time sits three entries before it (POSE_STRIDE
+// layout below)
+__device__ __forceinline__ void disp(const Params &p, const double *Pw, int x, int y, int z, double r[3]) {
+    disp_from(p, Pw - 3, x, y, z, r);
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
@@ -366,19 +374,20 @@ __device__ __forceinline__ float link_delta_f(int halfway, int shape, float R, f
 struct Frame {
     int xi[3];
     float fr[3];
-    double Xw[3];
+    double X[3]; // unwrapped pose (the displacement of the FP64 decision)
     double co, si;   // orientation (ellipse)
     float cof, sif;
 };
 
 // Xw points at the wrapped pose of t or t+1 in a poses record; the matching
-// orientation (cos, sin) sits 15 entries further (see POSE_STRIDE)
+// orientation (cos, sin) sits 15 entries further, the unwrapped pose three
+// entries before it (see POSE_STRIDE)
 __device__ __forceinline__ void make_frame(const double Xw[3], Frame &f) {
     for (int a = 0; a < 3; ++a) {
         double fl = floor(Xw[a]);
         f.xi[a] = (int)fl;
         f.fr[a] = (float)(Xw[a] - fl);
-        f.Xw[a] = Xw[a];
+        f.X[a] = Xw[a - 3];
     }
     f.co = Xw[15];
     f.si = Xw[16];
@@ -386,16 +395,27 @@ __device__ __forceinline__ void make_frame(const double Xw[3], Frame &f) {
     f.sif = (float)f.si;
 }
 
+// FP32 displacement k - fr of a node from a body frame along one axis (k =
+// node - floor(pose), fr = pose - floor(pose) in [0, 1)).  On a periodic axis
+// of n nodes it is the minimum image in [-n/2, n/2), with the tie at exactly
+// n/2 taken as -n/2: the FP64 minimum image v - n floor(v / n + 1/2) of
+// axis_disp, decided from the integer k and fr so that the choice is exact.
+__device__ __forceinline__ float frame_axis(int k, float fr, int n, int per) {
+    if (per) {
+        if (2 * k > n) k -= n;
+        else if (2 * k < -n) k += n;
+        // k - fr now lies in [-n/2 - 1, n/2]: bring its ends into [-n/2, n/2)
+        if ((float)(2 * k - n) >= 2.0f * fr) k -= n;
+        else if ((float)(2 * k + n) < 2.0f * fr) k += n;
+    }
+    return (float)k - fr;
+}
+
 __device__ __forceinline__ void frame_disp_f(const Params &p, const Frame &f, int x, int y, int z, float d[3]) {
     const int c[3] = {x, y, z};
     for (int a = 0; a < 3; ++a) {
-        int k = c[a] - f.xi[a];
-        if (p.per[a]) {
-            const int n = a == 0 ? p.nx : (a == 1 ? p.ny : p.nz);
-            if (2 * k > n) k -= n;
-            else if (2 * k < -n) k += n;
-        }
-        d[a] = (float)k - f.fr[a];
+        const int n = a == 0 ? p.nx : (a == 1 ? p.ny : p.nz);
+        d[a] = frame_axis(c[a] - f.xi[a], f.fr[a], n, p.per[a]);
     }
 }
 
@@ -424,7 +444,7 @@ __device__ __forceinline__ bool inside_screened(const Params &p, const BodyDev &
         if (s > R2 + band) return false;
     }
     double r[3];
-    disp(p, f.Xw, x, y, z, r);
+    disp_from(p, f.X, x, y, z, r);
     return inside(B, r, f.co, f.si);
 }
 

@@ -903,15 +903,7 @@ __device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, c
         const double *Pf = X + 9; // floor(Xw), frac(Xw)
         const int c3[3] = {x, y, z};
         float df[3], rb[3];
-        for (int a = 0; a < 3; ++a) {
-            int kk = c3[a] - (int)Pf[a];
-            if (p.per[a]) {
-                const int n = axis_len(p, a);
-                if (2 * kk > n) kk -= n;
-                else if (2 * kk < -n) kk += n;
-            }
-            df[a] = (float)kk - (float)Pf[3 + a];
-        }
+        for (int a = 0; a < 3; ++a) df[a] = frame_axis(c3[a] - (int)Pf[a], (float)Pf[3 + a], axis_len(p, a), p.per[a]);
         const float dl = (float)delta;
         rb[0] = df[0] - dl * cxi;
         rb[1] = df[1] - dl * cyi;

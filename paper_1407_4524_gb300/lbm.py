@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_set_bodies.argtypes = [P, C.POINTER(lbm_body), C.c_int]
     lib.lbm_update_bodies.argtypes = [P, C.POINTER(lbm_body), C.c_int]
     lib.lbm_step.argtypes = [P, C.c_int]
+    lib.lbm_prepare_graph.argtypes = [P]
     lib.lbm_get_force_torque.argtypes = [P, C.c_int64, C.c_int64, C.c_int, P]
     lib.lbm_get_series.argtypes = [P, C.c_int64, C.c_int64, P]
     lib.lbm_get_populations.argtypes = [P, P]
@@ -291,6 +292,11 @@ class Domain:
 
     def step(self, n: int = 1):
         _check(self.lib.lbm_step(self.h, int(n)))
+
+    def prepare_graph(self):
+        """record the 16-step graph now (lbm_prepare_graph): later runs of
+        >= 16 steps replay it without the recording cost"""
+        _check(self.lib.lbm_prepare_graph(self.h))
 
     @property
     def t(self) -> int:

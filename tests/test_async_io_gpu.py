@@ -83,3 +83,31 @@ def test_free_body_graph_replay_matches():
     dom.step(40)
     assert np.array_equal(dom.body_state(), want)
     dom.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_prepared_graph_matches_step_by_step(prec):
+    """lbm_prepare_graph records the 16-step graph at an odd step without
+    stepping; the runs that replay it afterwards give the bits of one-step
+    calls, and it refuses before the first step of a body set."""
+    from paper_1407_4524_gb300 import lbm
+    spec = dict(CASES_3D["moving_spheres_periodic"], precision=prec)
+    steps = 40
+    ref = lbm.Domain(spec, device=0)
+    for _ in range(steps):
+        ref.step(1)
+    want_ft = ref.force_torque("lattice")
+    want_f = ref.populations()
+    ref.close()
+    dom = lbm.Domain(spec, device=0)
+    with pytest.raises(lbm.LbmError, match="LBM_ERR_STATE"):
+        dom.prepare_graph()
+    dom.step(3)  # odd step
+    dom.prepare_graph()
+    dom.prepare_graph()  # already recorded: nothing to do
+    assert dom.t == 3
+    dom.step(steps - 3)  # one plain step, two replays, plain remainder
+    assert dom.t == steps
+    assert np.array_equal(dom.force_torque("lattice"), want_ft)
+    assert np.array_equal(dom.populations(), want_f)
+    dom.close()

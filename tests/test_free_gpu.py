@@ -8,7 +8,7 @@ the stated tolerance over the run.
 import numpy as np
 import pytest
 
-from parity_util import TOL_RED_FT, ft_rel_error
+from parity_util import TOL_FP16_FT, TOL_RED_FT, ft_rel_error
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,7 @@ def test_free_bodies_reduced_precision(oracle_mod, name, prec):
     spec = dict(CASES[name], precision=prec)
     dom, ref = _run(oracle_mod, spec, STEPS[name])
     e = ft_rel_error(dom.force_torque("lattice"), ref.force_torque("lattice"), spec=spec)
-    tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    tol = TOL_RED_FT if prec == "fp32" else TOL_FP16_FT
     assert e <= tol, f"lattice-frame force/torque {e:.3e}"
     dx = np.abs(dom.body_state()[:, :3] - ref.body_state()[:, :3]).max()
     assert dx <= (1e-5 if prec == "fp32" else 1e-3), f"positions differ by {dx:.3e}"

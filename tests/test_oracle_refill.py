@@ -137,3 +137,105 @@ def test_force_noise_by_form_and_refill(oracle_mod):
     # the same mean drag within a few per cent, whatever the rule
     d = [r["drag"] for r in out.values()]
     assert max(d) - min(d) < 0.03 * abs(np.mean(d))
+
+
+# ---- refill values on fields whose answer is known in closed form ----------
+#
+# The state is set to f = f^eq(rho(x), U0) at every node, with rho a quadratic
+# polynomial in the coordinates and U0 a constant fluid velocity: the BGK
+# collision leaves an equilibrium unchanged, so fhat(t) = f(t) is a quadratic
+# field along every lattice line.  After one step each uncovered node A must
+# hold, by the rule:
+#   "uB"    f^eq(rho_bar, u_B(A)),  rho_bar the mean of rho over A's lattice
+#           neighbours that are fluid at t, u_B the body's velocity at A, t+1;
+#   "ubar"  f^eq(rho_bar, u_bar), u_bar the mean of u over the same neighbours
+#           (= U0 here, which differs from u_B since the body moves and turns
+#           with its own velocity);
+#   "extrap" quadratic extrapolation along a lattice line reproduces a
+#           quadratic field exactly, so f^eq(rho(A), U0) whichever line is
+#           taken -- or, where the rule falls back, the "uB" value.
+# The expected values use the lattice tables and the definitions only (no
+# part of the oracle's refill code), so a wrong neighbour set, average,
+# velocity, time level or extrapolation coefficient fails.
+
+def _feq(c, w, rho, u, rho0=1.0):
+    cu = c @ u
+    return w * (rho + rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * float(u @ u)))
+
+
+def _known_field_case(lat):
+    if lat == "D2Q9":
+        n = (40, 34, 1)
+        b = dict(shape="cylinder", R=6.4, X0=(17.3, 16.2), U=(0.23, -0.11), W=0.02)
+        U0 = np.array([0.03, 0.012, 0.0])
+    else:
+        n = (26, 24, 22)
+        b = dict(shape="sphere", R=5.2, X0=(11.6, 12.3, 10.8), U=(0.21, 0.09, -0.13), W=(0.01, -0.02, 0.015))
+        U0 = np.array([0.025, -0.01, 0.015])
+    return n, b, U0
+
+
+def _rho_field(n, X0):
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    X0 = tuple(X0) + (0.0,) * (3 - len(X0))
+    dx, dy, dz = (x - X0[0]) / 10.0, (y - X0[1]) / 10.0, (z - X0[2]) / 10.0
+    return (1.0 + 1e-3 * dx - 7e-4 * dy + 4e-4 * dz + 2e-4 * dx * dx - 1.5e-4 * dy * dy
+            + 1e-4 * dx * dy + 1.2e-4 * dz * dz - 0.8e-4 * dy * dz)
+
+
+@pytest.mark.parametrize("refill", ["uB", "ubar", "extrap"])
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+def test_refill_values_on_known_fields(oracle_mod, lat, refill):
+    n, b, U0 = _known_field_case(lat)
+    q = 9 if lat == "D2Q9" else 19
+    c, w, _ = oracle_mod.lattice_tables(q)
+    c = c.astype(float)
+    spec = dict(lattice=lat, n=n[:2] if lat == "D2Q9" else n, tau=0.7, refill=refill, bodies=[b])
+    o = oracle_mod.Oracle(spec)
+    rho = _rho_field(n, b["X0"])
+    f0 = np.empty((q,) + rho.shape)
+    for k in np.ndindex(rho.shape):
+        f0[(slice(None),) + k] = _feq(c, w, rho[k], U0)
+    o.set_f(f0)
+    solid0 = o.solid().copy()
+    ex0 = o.extrapolated()
+    o.step(1)
+    solid1 = o.solid()
+    f1 = o.f()
+    unc = np.argwhere((solid0 >= 0) & (solid1 < 0))
+    assert len(unc) >= 4
+    L = np.array(n, float)
+    X1 = np.array(tuple(b["X0"]) + (0.0,) * (3 - len(b["X0"]))) + np.array(tuple(b["U"]) + (0.0,) * (3 - len(b["U"])))
+    Wv = np.array([0.0, 0.0, b["W"]]) if np.isscalar(b["W"]) else np.array(b["W"])
+    Uv = np.array(tuple(b["U"]) + (0.0,) * (3 - len(b["U"])))
+    n_extrap = 0
+    for zz, yy, xx in unc:
+        A = np.array([xx, yy, zz], float)
+        r1 = A - X1
+        r1 = r1 - L * np.floor(r1 / L + 0.5)
+        if lat == "D2Q9":
+            r1[2] = 0.0
+        uB = Uv + np.cross(Wv, r1)
+        vals = []
+        for i in range(1, q):
+            p = (np.array([xx, yy, zz]) + c[i].astype(int)) % np.array(n)
+            if solid0[p[2], p[1], p[0]] < 0:
+                vals.append(rho[p[2], p[1], p[0]])
+        rbar = float(np.mean(vals)) if vals else 1.0
+        got = f1[:, zz, yy, xx]
+        if refill == "uB":
+            want = _feq(c, w, rbar, uB)
+        elif refill == "ubar":
+            want = _feq(c, w, rbar, U0)
+            assert np.abs(_feq(c, w, rbar, uB) - want).max() > 1e-4  # the rules differ here
+        else:
+            exact = _feq(c, w, rho[zz, yy, xx], U0)
+            fallback = _feq(c, w, rbar, uB)
+            if np.abs(got - exact).max() <= 1e-14:
+                n_extrap += 1
+                continue
+            want = fallback
+        np.testing.assert_allclose(got, want, rtol=0.0, atol=1e-14)
+    if refill == "extrap":
+        assert n_extrap == o.extrapolated() - ex0
+        assert n_extrap >= len(unc) // 2

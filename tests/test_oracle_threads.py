@@ -45,6 +45,16 @@ def _run(tmp_path, threads):
     return np.load(path)
 
 
+def test_oracle_is_built_with_openmp():
+    """The thread-count test below and the CPU baseline's core count mean
+    something only if the oracle really runs on several threads."""
+    code = f"import sys; sys.path.insert(0, {ROOT!r}); import oracle; print(oracle.threads())"
+    env = dict(os.environ, OMP_NUM_THREADS="3")
+    out = subprocess.run([sys.executable, "-c", code], env=env, check=True, capture_output=True, text=True,
+                         timeout=300)
+    assert int(out.stdout.strip().splitlines()[-1]) == 3
+
+
 def test_oracle_is_independent_of_thread_count(tmp_path, oracle_mod):
     a = _run(tmp_path, 1)
     b = _run(tmp_path, 3)

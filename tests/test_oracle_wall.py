@@ -188,13 +188,15 @@ def test_moving_body_momentum_balance(oracle_mod, lat, refill):
         assert o.extrapolated() > 0
 
 
+@pytest.mark.parametrize("refill", ["uB", "ubar", "extrap"])
 @pytest.mark.parametrize("eq", ["incomp", "standard"])
 @pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
-def test_galilean_comoving_uniform_flow(oracle_mod, lat, eq):
+def test_galilean_comoving_uniform_flow(oracle_mod, lat, eq, refill):
     """A uniform flow co-moving with a translating body stays exactly f^eq(1,U)
-    through the curved-wall rule, refill and A+/A- changes; the moving-frame
-    force is zero and the lattice-frame force reduces to the impulsive
-    rho0 U (N+ - N-) noise."""
+    through the curved-wall rule, every refill rule (rho_bar = 1 and u_bar =
+    u_B = U there; extrapolation of a uniform field is exact) and A+/A-
+    changes; the moving-frame force is zero and the lattice-frame force
+    reduces to the impulsive rho0 U (N+ - N-) noise."""
     if lat == "D2Q9":
         U = (0.05, 0.03)
         b = [dict(shape="cylinder", R=6.2, X0=(15.3, 14.6), U=U)]
@@ -203,7 +205,7 @@ def test_galilean_comoving_uniform_flow(oracle_mod, lat, eq):
         U = (0.05, 0.03, -0.04)
         b = [dict(shape="sphere", R=4.3, X0=(9.3, 8.6, 8.2), U=U)]
         n = (20, 18, 17)
-    o = oracle_mod.Oracle(dict(lattice=lat, n=n, tau=0.62, eq=eq, u0=U, bodies=b))
+    o = oracle_mod.Oracle(dict(lattice=lat, n=n, tau=0.62, eq=eq, u0=U, bodies=b, refill=refill))
     f0 = o.f()[:, 0, 0, 0].copy()
     o.step(40)
     fl = o.solid() < 0

@@ -10,7 +10,8 @@ bit-identical); FP32 / FP16 modes to the stated reduced-precision tolerance.
 import numpy as np
 import pytest
 
-from parity_util import TOL_FP64_FT, TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP, ft_rel_error, pop_error, report
+from parity_util import (TOL_FP16_FT, TOL_FP16_POP, TOL_FP64_FT, TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP,
+                         ft_rel_error, pop_error, report)
 
 pytestmark = pytest.mark.gpu
 
@@ -175,8 +176,8 @@ def test_fp64_is_bit_identical(oracle_mod):
 def test_reduced_precision_2d(oracle_mod, name, prec):
     spec = dict(CASES_2D[name], precision=prec)
     dom, ref = _run_both(oracle_mod, spec, 120)
-    pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
-    ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    pop_tol = TOL_RED_POP if prec == "fp32" else TOL_FP16_POP
+    ft_tol = TOL_RED_FT if prec == "fp32" else TOL_FP16_FT
     report(f"{name}_{prec}_120", _compare(dom, ref, 1e9, 1e9))
     _compare(dom, ref, pop_tol, ft_tol)
 
@@ -186,8 +187,8 @@ def test_reduced_precision_2d(oracle_mod, name, prec):
 def test_reduced_precision_3d(oracle_mod, name, prec):
     spec = dict(CASES_3D[name], precision=prec)
     dom, ref = _run_both(oracle_mod, spec, 40)
-    pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
-    ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+    pop_tol = TOL_RED_POP if prec == "fp32" else TOL_FP16_POP
+    ft_tol = TOL_RED_FT if prec == "fp32" else TOL_FP16_FT
     report(f"{name}_{prec}_40", _compare(dom, ref, 1e9, 1e9))
     _compare(dom, ref, pop_tol, ft_tol)
 

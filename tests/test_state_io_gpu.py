@@ -4,7 +4,7 @@ parity cases of test_parity_gpu otherwise all start from an equilibrium."""
 import numpy as np
 import pytest
 
-from parity_util import TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP, ft_rel_error, pop_error
+from parity_util import TOL_FP16_FT, TOL_FP16_POP, TOL_FP64_POP, TOL_RED_FT, TOL_RED_POP, ft_rel_error, pop_error
 from test_parity_gpu import CASES_2D, CASES_3D
 
 pytestmark = pytest.mark.gpu
@@ -56,12 +56,12 @@ def test_reduced_from_random_state(oracle_mod, dim, name, prec):
     steps = 60 if dim == "2d" else 20
     dom.step(steps)
     ref.step(steps)
-    pop_tol = TOL_RED_POP if prec == "fp32" else 2e-4
+    pop_tol = TOL_RED_POP if prec == "fp32" else TOL_FP16_POP
     assert pop_error(dom.populations(), ref.fhat(), ref.solid()) <= pop_tol
     m_gpu, m_ref = dom.macros(), ref.macro()
     assert np.abs(m_gpu - m_ref).max() <= (2e-6 if prec == "fp32" else 2e-4)
     if ref.bodies:
-        ft_tol = TOL_RED_FT if prec == "fp32" else 2e-2
+        ft_tol = TOL_RED_FT if prec == "fp32" else TOL_FP16_FT
         for kind in ("static", "lattice", "moving"):
             assert ft_rel_error(dom.force_torque(kind), ref.force_torque(kind), spec=spec) <= ft_tol, kind
 

@@ -68,3 +68,42 @@ def test_noalloc_d3q19_and_limit():
     assert "4194304" in dom.lib.lbm_last_error().decode()
     assert np.all(out == 7.0)
     dom.close()
+
+
+def test_noalloc_with_every_allocation_refused():
+    """A caller whose allocator refuses everything (a budget that is full)
+    can still export: the refusing allocator makes lbm_get_populations fail
+    with LBM_ERR_OOM, while the no-allocation export succeeds, twice in a
+    row and after further steps, with the values lbm_get_populations gives
+    once allocation is allowed again."""
+    import torch
+    from paper_1407_4524_gb300 import lbm
+    from test_fault_injection_gpu import _FailingAllocator, _desc
+    from test_parity_gpu import CASES_2D
+    lib = lbm.load()
+    fn = _noalloc(lib)
+    stream_ptr = int(torch.cuda.current_stream(0).cuda_stream)
+    fa = _FailingAllocator(stream_ptr)
+    spec = dict(CASES_2D["moving_cylinders_periodic"], precision="fp32")
+    d, q, n = _desc(spec, fa, stream_ptr)
+    h = C.c_void_p()
+    assert lib.lbm_create_domain(C.byref(d), C.byref(h)) == 0
+    bodies = lbm.body_array(spec["bodies"])
+    assert lib.lbm_set_bodies(h, bodies, len(spec["bodies"])) == 0
+    size = q * int(np.prod(n))
+    for steps in (5, 9):
+        assert lib.lbm_step(h, steps) == 0
+        fa.left = 0  # from here on every allocation is refused
+        blocked = np.empty(size)
+        assert lib.lbm_get_populations(h, blocked.ctypes.data) == 2  # LBM_ERR_OOM
+        got = [np.full(size, np.nan), np.full(size, np.nan)]
+        for g in got:
+            rc = fn(h, g.ctypes.data)
+            assert rc == 0, lib.lbm_last_error().decode()
+        fa.left = None
+        ref = np.empty(size)
+        assert lib.lbm_get_populations(h, ref.ctypes.data) == 0
+        for g in got:
+            np.testing.assert_allclose(g, ref, rtol=TOL, atol=TOL)
+    assert lib.lbm_destroy_domain(h) == 0
+    assert not fa.live
