@@ -179,6 +179,7 @@ struct lbm_domain {
     int bnd_grid = 0, bnd_grid_full = 0;
     int side_blocks = 0; // block cap of the side-stream kernels
     bool side_serial = false; // run the surface kernels before k_bulk on one stream, uncapped
+    bool batch = false;       // a serving batch's solve: boundary-node kernel instead of link mode
     bool prep_dirty = true;
     int links_grid = 0;
     int64_t t = 0;
@@ -533,6 +534,10 @@ int do_step_overlapped(lbm_domain *D);
 
 // reduced-precision modes: boundary-node lists of step t from scratch
 int build_bnd_lists(lbm_domain *D) {
+    if (D->p.linkmode) { // link mode keeps cut-link lists instead
+        D->lists_dirty = false;
+        return LBM_OK;
+    }
     const int cur = (int)(D->t & 1);
     CK(cudaMemsetAsync(D->bn_cnt, 0, 3 * sizeof(unsigned long long), D->s));
     GeomArgs gl = geom_args(D, false);
@@ -612,13 +617,16 @@ int do_step(lbm_domain *D) {
 // side stream writes fhat(t+1) of the boundary and refilled nodes, the owner
 // array of t+1, the lists and the accumulators: the two streams touch
 // disjoint data.  Flag changes are applied by the next prep.
+int do_step_links(lbm_domain *D);
+
 int do_step_overlapped(lbm_domain *D) {
+    if (D->p.linkmode) return do_step_links(D);
     const int Q = D->Q, prec = D->prec;
     const int cur = (int)(D->t & 1), nxt = cur ^ 1;
     if (D->n_moving || D->prep_dirty || D->lists_dirty) {
         CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->counters + 9 + (D->t & 1), D->flags, D->chg_cnt, D->chg_cell,
                         D->chg_val, D->chg_cap,
-                        D->apm_cnt, D->bn_cnt + 1 + nxt, D->s));
+                        D->apm_cnt, D->bn_cnt + 1 + nxt, nullptr, nullptr, nullptr, D->s));
         D->prep_dirty = false;
     }
     if (D->lists_dirty) {
@@ -667,6 +675,61 @@ int do_step_overlapped(lbm_domain *D) {
     return LBM_OK;
 }
 
+// Link mode (reduced precision, single domain).  Stream s: prep -> cut links
+// (wall values into the solid nodes' slots, momentum exchange) -> stream-collide
+// of every fluid node (boundary nodes included; moments kept at the nodes near
+// bodies).  Side stream: after prep, the owners, covered/uncovered lists, flag
+// changes and cut links of t+1 of the moving bodies; after the cut links, the
+// end of step (series row, impulsive terms with covered nodes re-pulled from
+// fhat(t) and its wall values, refill of uncovered nodes) and the free-body
+// update.  The side stream overlaps the stream-collide pass and touches no
+// data it reads or writes: the links of t+1 go to the other list buffer, the
+// kept-moment band only gains flags, refilled nodes were solid at t.
+int do_step_links(lbm_domain *D) {
+    const int Q = D->Q, prec = D->prec;
+    const int cur = (int)(D->t & 1), nxt = cur ^ 1;
+    if (D->n_moving || D->prep_dirty || D->lists_dirty) {
+        CK(launch_fprep(D->p, D->dbodies, D->poses, D->t, D->counters + 9 + (D->t & 1), D->flags, D->chg_cnt, D->chg_cell,
+                        D->chg_val, D->chg_cap, D->apm_cnt, D->bn_cnt + 1 + nxt, D->link_cnt[cur], D->link_cnt[nxt],
+                        D->tile_pre, D->s));
+        D->prep_dirty = false;
+        D->lists_dirty = false;
+    }
+    const bool side = !D->side_serial;
+    cudaStream_t ss = side ? D->s2 : D->s;
+    StepBufs sb = step_bufs(D);
+    if (side) {
+        CK(cudaEventRecord(D->ev_prep, D->s));
+        CK(cudaStreamWaitEvent(D->s2, D->ev_prep, 0));
+    }
+    if (D->n_moving) {
+        GeomArgs g = geom_args(D, true);
+        g.grid_cap = side ? D->side_blocks : 0;
+        CK(launch_fgeom1(Q, D->p, g, ss));
+        CK(launch_fgeom2(Q, D->p, g, ss));
+    }
+    CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
+    if (side) {
+        CK(cudaEventRecord(D->ev_links, D->s));
+        CK(cudaStreamWaitEvent(D->s2, D->ev_links, 0));
+    }
+    CK(launch_finish(Q, prec, D->p, sb, ss));
+    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->counters + 9 + (D->t & 1), ss));
+    if (side) CK(cudaEventRecord(D->ev_side, D->s2));
+    cudaEvent_t ta = nullptr, tb = nullptr;
+    if (D->timing) {
+        int trc = timing_events(D, ta, tb);
+        if (trc) return trc;
+        CK(record_timing(D, ta));
+    }
+    CK(launch_bulk(Q, prec, D->p, sb, D->s));
+    if (D->timing) CK(record_timing(D, tb));
+    if (side) CK(cudaStreamWaitEvent(D->s, D->ev_side, 0));
+    D->t += 1;
+    if (D->capturing) D->cap_k += 1;
+    return LBM_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -689,7 +752,16 @@ int lbm_lattice_table(int lattice, int *c, double *w, int *opp) {
     return LBM_OK;
 }
 
-int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
+namespace {
+int create_domain_impl(const lbm_domain_desc *desc, lbm_domain **out, bool batch);
+} // namespace
+
+int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) { return create_domain_impl(desc, out, false); }
+
+namespace {
+// batch: a serving batch's solve (the boundary-node kernel steps its
+// boundary nodes; no cut-link lists, no kept moments)
+int create_domain_impl(const lbm_domain_desc *desc, lbm_domain **out, bool batch) {
     if (!desc || !out) return fail(LBM_ERR_ARG, "null argument");
     *out = nullptr;
     const lbm_domain_desc &d = *desc;
@@ -731,6 +803,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
 
     lbm_domain *D = new lbm_domain();
     D->d = d;
+    D->batch = batch;
     D->Q = d.lattice;
     D->prec = d.precision;
     D->s = (cudaStream_t)d.stream;
@@ -745,6 +818,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     for (int k = 0; k < 6; ++k) p.edge[k] = d.edge[k];
     p.nonper = !(p.per[0] && p.per[1] && p.per[2]);
     p.exact = d.precision == LBM_FP64;
+    p.linkmode = (!batch && d.precision != LBM_FP64) ? 1 : 0;
     {
         // LBM_STAGED=1 selects the stream-collide kernel that stages the
         // source rows in shared memory by bulk copies (same results bit for
@@ -791,10 +865,10 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     int rc;
     for (int k = 0; k < 2; ++k) {
         if ((rc = alloc_into(D, &D->pop[k], N * D->Q * D->Ssize, nullptr))) return bail(rc);
-        // moments are stored only in the FP64 mode (the reduced-precision modes
-        // take them from the collided populations)
-        if ((rc = alloc_into(D, &D->mac[k], d.precision == LBM_FP64 ? N * 4 * D->Csize : 256, nullptr)))
-            return bail(rc);
+        // moments near bodies: FP64 (rho, u) in the FP64 mode, float4 (rho - 1, u)
+        // in link mode; serving solves take them from the collided populations
+        const size_t macb = d.precision == LBM_FP64 ? N * 4 * D->Csize : (p.linkmode ? N * 16 : 256);
+        if ((rc = alloc_into(D, &D->mac[k], macb, nullptr))) return bail(rc);
         if ((rc = alloc_t(D, &D->owner[k], N, nullptr))) return bail(rc);
     }
     if ((rc = alloc_t(D, &D->flags, N, nullptr))) return bail(rc);
@@ -834,6 +908,7 @@ int lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     *out = D;
     return LBM_OK;
 }
+} // namespace
 
 int lbm_destroy_domain(lbm_domain *D) {
     if (!D) return LBM_OK;
@@ -945,17 +1020,18 @@ int place_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->chunk_mov, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->chunk_cnt_apm, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->chunk_cnt_link, (size_t)std::max<long long>(chunks, 1), &T))) return rc;
-    // cut-link lists and per-link contributions: FP64 mode only (the
-    // reduced-precision modes evaluate links inside the boundary-node kernel)
+    // cut-link lists: FP64 mode and link mode (serving solves evaluate links
+    // inside the boundary-node kernel); per-link contributions: FP64 mode
     const bool exact = D->prec == LBM_FP64;
-    const size_t Lsz = exact ? (size_t)std::max<long long>(loff, 1) : 1;
+    const bool lists = exact || D->p.linkmode;
+    const size_t Lsz = lists ? (size_t)std::max<long long>(loff, 1) : 1;
     for (int k = 0; k < 2; ++k) {
         if ((rc = alloc_t(D, &D->Lcell[k], Lsz, &T))) return rc;
         if ((rc = alloc_t(D, &D->Ldir[k], Lsz, &T))) return rc;
         if ((rc = alloc_t(D, &D->Ldelta[k], Lsz, &T))) return rc;
         if ((rc = alloc_t(D, &D->link_cnt[k], nbx, &T))) return rc;
     }
-    if ((rc = alloc_t(D, &D->me, Lsz * ME_PER_LINK, &T))) return rc;
+    if ((rc = alloc_t(D, &D->me, (exact ? Lsz : 1) * ME_PER_LINK, &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_cell, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_sign, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_cnt, nbx, &T))) return rc;
@@ -1001,7 +1077,8 @@ int place_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     CK(launch_raster(D->Q, D->p, g, D->owner[0], 0, D->s));
     CK(cudaMemcpyAsync(D->owner[1], D->owner[0], N * sizeof(uint16_t), cudaMemcpyDeviceToDevice, D->s));
     CK(launch_flags_full(D->Q, D->p, D->owner[0], D->flags, D->s));
-    if (exact) {
+    if (D->p.linkmode) CK(launch_macband(D->p, g, D->s)); // kept moments around every body
+    if (lists) {
         CK(launch_geom_b(D->Q, D->p, g, D->s));
         CK(launch_geom_c(D->Q, D->p, g, D->s));
         const size_t L = Lsz;
@@ -1456,7 +1533,7 @@ int lbm_get_stats(lbm_domain *D, lbm_stats *out) {
     out->extrapolated = (int64_t)c[8];
     out->h2d_bytes = D->h2d;
     out->d2h_bytes = D->d2h;
-    if (D->nb && D->prec != LBM_FP64 && D->t > 0) {
+    if (D->nb && D->prec != LBM_FP64 && !D->p.linkmode && D->t > 0) {
         out->links = (int64_t)c[4]; // counted by the boundary-node kernel in the last step
     } else if (D->nb) {
         std::vector<long long> lc(D->nb);
@@ -1885,7 +1962,7 @@ int lbm_batch_admit(lbm_batch *B, const lbm_domain_desc *desc, const lbm_body *h
                                      std::to_string(B->d.budget_bytes - B->used) + " left in the budget");
     DEVICE_SCOPE(B->d.device);
     lbm_domain *D = nullptr;
-    if ((rc = lbm_create_domain(&d, &D))) return rc;
+    if ((rc = create_domain_impl(&d, &D, true))) return rc;
     if ((rc = lbm_set_bodies(D, hb, n))) {
         lbm_destroy_domain(D);
         return rc;
@@ -1894,7 +1971,7 @@ int lbm_batch_admit(lbm_batch *B, const lbm_domain_desc *desc, const lbm_body *h
     if (n > 0) {
         // poses of t = 0 and the boundary-node list (all static)
         cudaError_t e = launch_fprep(D->p, D->dbodies, D->poses, 0, nullptr, D->flags, D->chg_cnt, D->chg_cell, D->chg_val,
-                                     D->chg_cap, D->apm_cnt, D->bn_cnt + 2, D->s);
+                                     D->chg_cap, D->apm_cnt, D->bn_cnt + 2, nullptr, nullptr, nullptr, D->s);
         if (e == cudaSuccess && (rc = build_bnd_lists(D))) {
             lbm_destroy_domain(D);
             return rc;

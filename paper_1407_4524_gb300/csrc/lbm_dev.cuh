@@ -29,6 +29,11 @@ constexpr int GEOM_THREADS = 512;
 constexpr int GEOM_CELLS = 8; // consecutive region cells per thread
 constexpr int GEOM_CHUNK = GEOM_THREADS * GEOM_CELLS;
 constexpr int REGION_MARGIN = 4;
+// link mode: moments are kept at fluid nodes within R + MAC_BAND of a body
+// (a cut link's fluid end and its x_F + c_i lie within 2 sqrt(2) of the
+// surface; a body moves less than a quarter cell per step; the region of a
+// body reaches R + REGION_MARGIN)
+constexpr float MAC_BAND = 4.0f;
 
 // ---------------------------------------------------------------- lattices --
 template <int Q_> struct Lat;
@@ -140,6 +145,11 @@ struct Params {
     int stage_expire_test; // test hook: the staged kernel issues no copy, so its waits expire
     int nsm;     // multiprocessors of the device
     int zouhe;   // wall / inlet faces are Zou-He nodes (else half-way links)
+    int linkmode; // reduced precision, single domain: wall values on cut links are written
+                  // into the solid nodes' slots before the stream-collide pass (which then
+                  // steps the boundary nodes too); the moments (drho, u) of the nodes near
+                  // bodies are kept as float4 per cell (FL_MAC).  0: the boundary-node kernel
+                  // steps the boundary nodes (serving batches)
     long long series_cap;
     long long me_stride; // ME contribution arrays are [ME_PER_LINK][me_stride]
     double tau, omega, rho0, u_in;

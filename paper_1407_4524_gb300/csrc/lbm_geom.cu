@@ -376,8 +376,19 @@ __global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies,
                                                 const unsigned long long *tdev, uint8_t *flags,
                                                 unsigned long long *chg_cnt, const uint32_t *chg_cell,
                                                 const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
-                                                unsigned long long *bn_mov_next_cnt) {
+                                                unsigned long long *bn_mov_next_cnt, const long long *link_cnt_t,
+                                                long long *link_cnt_t1, long long *tile_pre) {
     const long long t = tdev ? (long long)*tdev : t_arg; // the device step counter, when given
+    if (p.linkmode && link_cnt_t) {
+        // link mode: the cut links of t are complete (static bodies: from their
+        // placement; moving ones: appended by the previous step's geometry);
+        // the tiles of the link kernel follow them, and the moving bodies'
+        // lists of t+1 start empty
+        prefix_over_bodies(p, link_cnt_t, tile_pre, 1);
+        for (int b = threadIdx.x; b < p.nb; b += 1024)
+            if (bodies[b].moving) link_cnt_t1[b] = 0;
+        __syncthreads();
+    }
     const long long n = (long long)min((unsigned long long)chg_cap, *chg_cnt);
     for (long long e = threadIdx.x; e < n; e += 1024) {
         const long long c = chg_cell[e];
@@ -425,9 +436,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom1(Params p, GeomArgs g) {
         const uint16_t me = (uint16_t)(b + 1);
         const float Rin = body_rin(B), Rout = body_rout(B);
         for (int j = 0; j < GEOM_CELLS; ++j) {
-            RegionCell rc = region_cell(p, B, lo, cm.y, j);
+            RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
             if (!rc.valid) continue;
             const float dist = frame_dist(p, B, F, rc);
+            // link mode: the nodes whose moments the cut links of the next
+            // steps read (within R + 4 of the body at t+1; never cleared)
+            if (p.linkmode && dist <= Rout + MAC_BAND && !(g.flags[rc.cell] & FL_MAC)) g.flags[rc.cell] |= FL_MAC;
             if (dist < Rin - 2.0f || dist > Rout + 2.0f) continue;
             const bool in_t = g.owner_t[rc.cell] == me;
             const bool in1 = inside_screened(p, B, F, rc.x, rc.y, rc.z);
@@ -460,7 +474,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
         region_lo(p, B, P, REGION_MARGIN, lo);
         const float Rin = body_rin(B), Rout = body_rout(B);
         for (int j = 0; j < GEOM_CELLS; ++j) {
-            RegionCell rc = region_cell(p, B, lo, cm.y, j);
+            RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
             if (!rc.valid) continue;
             const float dist = frame_dist(p, B, F, rc);
             if (dist < Rin - 2.0f || dist > Rout + 3.0f) continue;
@@ -507,6 +521,86 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2(Params p, GeomArgs g) {
     }
 }
 
+// link mode: the solid flags of t+1 in the shell R-2 .. R+3 (changes
+// appended; link mode reads no boundary-node flag), and the cut links of t+1
+// to this body (fluid node at t+1 within R + 1.5, direction i with x - c_i
+// inside the body at t+1, Delta in FP32 from the pose of t+1), appended to the
+// body's segment of the other list buffer: a thread first finds the links of
+// its GEOM_CELLS cells, then one block scan and one atomic per chunk place them
+// (their order does not matter: exact fixed-point sums)
+template <class L>
+__global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2l(Params p, GeomArgs g) {
+    __shared__ Frame F;
+    for (int ch = blockIdx.x; ch < g.nchunks; ch += gridDim.x) {
+        const int2 cm = g.chunk_map[ch];
+        const int b = cm.x;
+        const BodyDev &B = g.bodies[b];
+        const double *P = g.poses + (long long)b * POSE_STRIDE;
+        __syncthreads();
+        if (threadIdx.x == 0) make_frame(P + 9, F);
+        __syncthreads();
+        int lo[3];
+        region_lo(p, B, P, REGION_MARGIN, lo);
+        const float Rin = body_rin(B), Rout = body_rout(B);
+        const uint16_t me = (uint16_t)(b + 1);
+        unsigned mj[GEOM_CELLS]; // directions of each cell's cut links to the body
+        int nl = 0;
+#pragma unroll
+        for (int j = 0; j < GEOM_CELLS; ++j) {
+            mj[j] = 0u;
+            const RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+            if (!rc.valid) continue;
+            const float dist = frame_dist(p, B, F, rc);
+            if (dist < Rin - 2.0f || dist > Rout + 3.0f) continue;
+            const bool solid1 = g.owner_t1[rc.cell] != 0;
+            const uint8_t nf = solid1 ? FL_SOLID : 0;
+            if ((g.flags[rc.cell] & FL_SOLID) != nf) {
+                const unsigned long long at = atomicAdd(g.chg_cnt, 1ull);
+                if ((long long)at < g.chg_cap) {
+                    g.chg_cell[at] = (uint32_t)rc.cell;
+                    g.chg_val[at] = nf;
+                }
+            }
+            if (solid1 || dist > Rout + 1.5f) continue;
+            unsigned m = 0u;
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                m |= ((a >= 0 && g.owner_t1[a] == me) ? 1u : 0u) << i;
+            }
+            mj[j] = m;
+            nl += __popc(m);
+        }
+        int total;
+        const long long first = block_excl_scan(nl, &total); // (syncs the block)
+        __shared__ unsigned long long base_s;
+        if (threadIdx.x == 0)
+            base_s = total ? atomicAdd((unsigned long long *)&g.link_cnt[b], (unsigned long long)total) : 0ull;
+        __syncthreads();
+        long long at = (long long)base_s + first;
+        if (!nl) continue;
+#pragma unroll
+        for (int j = 0; j < GEOM_CELLS; ++j) {
+            const unsigned m = mj[j];
+            if (!m) continue;
+            const RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+            float df[3];
+            frame_disp_f(p, F, rc.x, rc.y, rc.z, df);
+            for (int i = 1; i < L::Q; ++i) {
+                if (!((m >> i) & 1u)) continue;
+                if (at < B.link_cap) {
+                    const long long jj = B.link_off + at;
+                    g.Lcell[jj] = (uint32_t)rc.cell;
+                    g.Ldir[jj] = (uint8_t)i;
+                    g.Ldelta[jj] = (double)link_delta_f(B.halfway, B.shape, (float)B.R, (float)B.R2, F.cof, F.sif,
+                                                        df, L::cx(i), L::cy(i), L::cz(i));
+                }
+                ++at;
+            }
+        }
+    }
+}
+
 // boundary-node lists of step t from scratch: nodes next only to static
 // bodies go to the static list, nodes next to a moving body to the moving
 // list of step t (each node once: by the lowest-numbered neighbour body)
@@ -548,7 +642,32 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_bnd_lists(Params p, GeomArgs g
     }
 }
 
+// link mode, at body placement: the nodes within R + 4 of every body at t
+__global__ void __launch_bounds__(GEOM_THREADS) k_macband(Params p, GeomArgs g) {
+    const int2 cm = g.chunk_map[blockIdx.x];
+    const int b = cm.x;
+    const BodyDev &B = g.bodies[b];
+    const double *P = g.poses + (long long)b * POSE_STRIDE;
+    __shared__ Frame F;
+    if (threadIdx.x == 0) make_frame(P + 3, F);
+    __syncthreads();
+    int lo[3];
+    region_lo(p, B, P, REGION_MARGIN, lo);
+    const float Rout = body_rout(B);
+    for (int j = 0; j < GEOM_CELLS; ++j) {
+        RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+        if (!rc.valid) continue;
+        if (frame_dist(p, B, F, rc) <= Rout + MAC_BAND) g.flags[rc.cell] |= FL_MAC;
+    }
+}
+
 } // namespace
+
+cudaError_t launch_macband(const Params &p, const GeomArgs &g, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
+    k_macband<<<g.nchunks, GEOM_THREADS, 0, s>>>(p, g);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long *link_cnt, long long *link_pre,
                         long long *tile_pre, double *poses, long long t, const unsigned long long *tdev,
@@ -562,9 +681,10 @@ cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long 
 cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t,
                          const unsigned long long *tdev, uint8_t *flags, unsigned long long *chg_cnt,
                          const uint32_t *chg_cell, const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
-                         unsigned long long *bn_mov_next_cnt, cudaStream_t s) {
+                         unsigned long long *bn_mov_next_cnt, const long long *link_cnt_t, long long *link_cnt_t1,
+                         long long *tile_pre, cudaStream_t s) {
     k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, tdev, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt,
-                               bn_mov_next_cnt);
+                               bn_mov_next_cnt, link_cnt_t, link_cnt_t1, tile_pre);
     return cudaGetLastError();
 }
 
@@ -585,8 +705,14 @@ cudaError_t launch_fgeom1(int, const Params &p, const GeomArgs &g, cudaStream_t 
 cudaError_t launch_fgeom2(int Q, const Params &p, const GeomArgs &g, cudaStream_t s) {
     if (g.nchunks == 0) return cudaSuccess;
     const int grid = g.grid_cap > 0 ? min(g.nchunks, g.grid_cap) : g.nchunks;
-    if (Q == 9) k_fgeom2<Lat<9>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
-    else k_fgeom2<Lat<19>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
+    if (p.linkmode) {
+        if (Q == 9) k_fgeom2l<Lat<9>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
+        else k_fgeom2l<Lat<19>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
+    } else if (Q == 9) {
+        k_fgeom2<Lat<9>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
+    } else {
+        k_fgeom2<Lat<19>><<<grid, GEOM_THREADS, 0, s>>>(p, g);
+    }
     return cudaGetLastError();
 }
 

@@ -91,10 +91,15 @@ cudaError_t launch_prep(const Params &p, const BodyDev *bodies, const long long 
                         cudaStream_t s);
 // reduced-precision modes: poses, and the flag changes of the previous step;
 // clears the change list and the covered/uncovered counters
+// link mode (link_cnt_t given): the tile prefix of the links of t, and the
+// moving bodies' link counts of t+1 cleared
 cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, long long t,
                          const unsigned long long *tdev, uint8_t *flags, unsigned long long *chg_cnt,
                          const uint32_t *chg_cell, const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
-                         unsigned long long *bn_mov_next_cnt, cudaStream_t s);
+                         unsigned long long *bn_mov_next_cnt, const long long *link_cnt_t, long long *link_cnt_t1,
+                         long long *tile_pre, cudaStream_t s);
+// link mode: FL_MAC on the nodes within R + MAC_BAND of every body at t
+cudaError_t launch_macband(const Params &p, const GeomArgs &g, cudaStream_t s);
 
 // geometry (all FP64, mode independent)
 cudaError_t launch_raster(int Q, const Params &p, const GeomArgs &g, uint16_t *owner, long long t_pose,

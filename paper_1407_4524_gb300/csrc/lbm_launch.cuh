@@ -56,7 +56,7 @@ template <class L, class P> void staged_launch(const Params &p, const StepBufs &
     const long long nseg = (long long)((p.nx + seg - 1) / seg) * p.ny * p.nz;
     const int grid = (int)std::min<long long>(nseg, (long long)std::max(1, p.nsm) * STAGE_BLOCKS_PER_SM);
     k_bulk_staged<L, P><<<grid, seg, stage_smem<L, S>(seg), s>>>(p, (const S *)sb.src, (S *)sb.dst, sb.flags,
-                                                                  sb.counters);
+                                                                  sb.counters, (float *)sb.mac_t1);
 }
 
 // one kernel per face mode: the fewer faces, the less code in the loop

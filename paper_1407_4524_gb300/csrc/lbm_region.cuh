@@ -35,6 +35,29 @@ __device__ __forceinline__ RegionCell region_cell(const Params &p, const BodyDev
     return rc;
 }
 
+// the same cells as region_cell, interleaved: pass j of a chunk takes cells
+// j * GEOM_THREADS + threadIdx.x, so a warp reads consecutive cells (for the
+// kernels whose lists do not depend on the order, appended with atomics)
+__device__ __forceinline__ RegionCell region_cell_i(const Params &p, const BodyDev &B, const int lo[3], int chunk,
+                                                    int j) {
+    RegionCell rc{false, 0, 0, 0, 0};
+    const int e0 = B.ext[0], e1 = B.ext[1];
+    const int vol = e0 * e1 * B.ext[2];
+    const int k = chunk * GEOM_CHUNK + j * GEOM_THREADS + (int)threadIdx.x;
+    if (k >= vol) return rc;
+    const int kz = k / (e0 * e1);
+    const int rem = k - kz * e0 * e1;
+    const int ky = rem / e0;
+    const int kx = rem - ky * e0;
+    rc.x = region_axis(kx, lo[0], e0, p.nx, p.per[0]);
+    rc.y = region_axis(ky, lo[1], e1, p.ny, p.per[1]);
+    rc.z = region_axis(kz, lo[2], B.ext[2], p.nz, p.per[2]);
+    if (rc.x < 0 || rc.y < 0 || rc.z < 0) return rc;
+    rc.valid = true;
+    rc.cell = cell_of(p, rc.x, rc.y, rc.z);
+    return rc;
+}
+
 // neighbour x - k c_i; -1 if it falls outside a non-periodic axis
 template <class L>
 __device__ __forceinline__ long long nbr(const Params &p, int x, int y, int z, int i, int k) {

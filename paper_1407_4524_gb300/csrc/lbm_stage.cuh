@@ -144,7 +144,7 @@ __device__ __forceinline__ void stage_issue(const Params &p, const S *__restrict
 template <class L, class P>
 __global__ void __launch_bounds__(STAGE_SEG, STAGE_BLOCKS_PER_SM)
     k_bulk_staged(Params p, const typename P::S *__restrict__ src, typename P::S *__restrict__ dst,
-                  const uint8_t *__restrict__ flags, unsigned long long *counters) {
+                  const uint8_t *__restrict__ flags, unsigned long long *counters, float *__restrict__ mac_t1) {
     using S = typename P::S;
     constexpr int PAD = 16 / (int)sizeof(S);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(STAGE_SEG, STAGE_BLOCKS_PER_SM)
         if (x < p.nx) {
             const long long cell = cell_of(p, x, g.y, g.z);
             const uint8_t fl = __ldg(flags + cell);
-            if (!(fl & (FL_SOLID | FL_BND))) {
+            if (!(fl & FL_SOLID) && (p.linkmode || !(fl & FL_BND))) {
                 // y / z wall bounces of the row (same for every node of the segment)
                 int ym, yp, zm, zp;
                 unsigned ffl = 0u;
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(STAGE_SEG, STAGE_BLOCKS_PER_SM)
                 if (bounce) face_terms<L, P>(p, src, (const float *)nullptr, g.y, cell, bounce, inlet_only, f);
                 float drho, u[3];
                 moments_f<L>(p, f, drho, u);
+                if (p.linkmode && (fl & FL_MAC)) store_mac(mac_t1, cell, drho, u);
                 collide_f<L>(p, f, drho, u);
 #pragma unroll
                 for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);

@@ -170,6 +170,16 @@ __device__ __forceinline__ void moments_f(const Params &p, const float f[], floa
     u[2] = j2 * inv;
 }
 
+// link mode: the moments (drho, u) of f(t) of a node near a body, one float4
+// per cell, for the cut links of the next step and the refill
+__device__ __forceinline__ void store_mac(float *mac, long long cell, float drho, const float u[3]) {
+    reinterpret_cast<float4 *>(mac)[cell] = make_float4(drho, u[0], u[1], u[2]);
+}
+__device__ __forceinline__ float4 load_mac(const float *mac, long long cell) {
+    return reinterpret_cast<const float4 *>(mac)[cell];
+}
+__device__ __forceinline__ void store_mac(double *, long long, double, const double *) {}
+
 // c_i . u with the lattice components folded in (adds and subtracts only:
 // the library is built without contraction, so products with 0 and +-1 are
 // not removed by the compiler)
@@ -698,6 +708,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_init(Params p, typename P::S *
         for (int i = 0; i < L::Q; ++i) f[i] = dfeq_f<L>(p, i, 0.0f, u0, usq15);
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
+        if (p.linkmode && mac_here) store_mac(mac, cell, drho, u);
         collide_f<L>(p, f, drho, u);
     }
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
@@ -731,6 +742,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_load(Params p, const double *_
         for (int i = 0; i < L::Q; ++i) f[i] = (float)(stage[(long long)i * n + k] - L::template w<double>(i));
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
+        if (p.linkmode && (flags[cell] & FL_MAC)) store_mac(mac, cell, drho, u);
         collide_f<L>(p, f, drho, u);
     }
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
@@ -778,7 +790,7 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
     const uint8_t fl = __ldg(flags + cell);
     if (fl & FL_SOLID) return;
     if constexpr (!P::exact) {
-        if (fl & FL_BND) return; // boundary nodes: k_bnd
+        if (!p.linkmode && (fl & FL_BND)) return; // boundary nodes: k_bnd
     }
     C f[L::Q];
     pull_all<L, P, FM>(p, src, mac_t, x, y, z, cell, f);
@@ -795,6 +807,7 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
     } else {
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
+        if (p.linkmode && (fl & FL_MAC)) store_mac(mac_t1, cell, drho, u);
         collide_f<L>(p, f, drho, u);
     }
     const unsigned N32 = (unsigned)p.N, c32 = (unsigned)cell;
@@ -860,6 +873,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_zouhe(Params p, const typename
     } else {
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
+        if (p.linkmode && (fl & FL_MAC)) store_mac(mac_t1, cell, drho, u);
         collide_f<L>(p, f, drho, u);
     }
     for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + cell, f[i]);
@@ -967,14 +981,23 @@ __device__ __forceinline__ void link_work(const Params &p, const StepBufs &sb, c
         for (int a = 0; a < 3; ++a) pm[a] = -(cc[a] - uB[a]) * fa + (cb[a] - uB[a]) * fb;
     } else {
         const float fbf = ldP(pop + (long long)ib * N + cell);
-        float drF, uF[3];
-        moments_hat<L>(p, pop, cell, drF, uF);
+        // moments of f(t) at x_F (and at x_F + c_i): kept by the previous
+        // stream-collide pass (or the refill, or the initial state)
+        const float *macf = (const float *)sb.mac_t;
+        const float4 mF = load_mac(macf, cell);
+        const float drF = mF.x;
+        const float uF[3] = {mF.y, mF.z, mF.w};
+        // stability check at the fluid end of every cut link: a NaN or
+        // |u| > 0.3 marks the solve unstable (counters[5]; LBM_ERR_UNSTABLE)
+        if (!(uF[0] * uF[0] + uF[1] * uF[1] + uF[2] * uF[2] < 0.09f)) atomicOr(&sb.counters[5], 1ull);
         float ubf[3], chi;
         const float dl = (float)delta;
         if (delta < 0.5) {
             if (G >= 0) {
-                float drG;
-                moments_hat<L>(p, pop, G, drG, ubf);
+                const float4 mG = load_mac(macf, G);
+                ubf[0] = mG.y;
+                ubf[1] = mG.z;
+                ubf[2] = mG.w;
                 chi = (2.0f * dl - 1.0f) / ((float)p.tau - 2.0f);
             } else {
                 ubf[0] = uF[0];
@@ -1067,6 +1090,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
     } else {
         // tile -> body map in shared memory (binary search), global beyond 1024 bodies
         __shared__ long long tp_s[1025];
+        __shared__ unsigned long long part[LINK_THREADS / 32][ME_PER_LINK];
         const bool in_smem = p.nb < 1025;
         if (in_smem)
             for (int k = threadIdx.x; k <= p.nb; k += blockDim.x) tp_s[k] = sb.tile_pre[k];
@@ -1084,20 +1108,29 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(Params p, StepBufs sb) {
             const BodyDev &B = sb.bodies[b];
             const double *X = sb.poses + (long long)b * POSE_STRIDE + 3;
             const long long k = (tile - tp[b]) * LINK_THREADS + threadIdx.x;
-            const long long cnt = sb.link_cnt[b];
-            const long long warp_first = k - lane;
-            if (warp_first >= cnt) continue; // whole warp past the body's links
+            // appended lists count past a full segment; only its links exist
+            const long long cnt = min(sb.link_cnt[b], B.link_cap);
             double out[ME_PER_LINK];
             float outf[ME_PER_LINK];
             for (int c = 0; c < ME_PER_LINK; ++c) outf[c] = 0.0f;
             if (k < cnt) link_work<L, P>(p, sb, tb, B, X, B.link_off + k, out, outf);
-            unsigned long long *acc = sb.acc + (long long)b * SERIES_ROW;
+            // the tile's sums: warp shuffles, then one atomic per block and
+            // component (every tile of a body adds into the same 12 words)
+            const int wid = threadIdx.x >> 5;
 #pragma unroll
             for (int c = 0; c < ME_PER_LINK; ++c) {
                 unsigned long long v = to_fx(outf[c]);
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                if (lane == 0) atomicAdd(acc + (c < 6 ? c : c + 6), v);
+                if (lane == 0) part[wid][c] = v;
             }
+            __syncthreads();
+            if (threadIdx.x < ME_PER_LINK) {
+                unsigned long long v = 0ull;
+                for (int w = 0; w < LINK_THREADS / 32; ++w) v += part[w][threadIdx.x];
+                const int c = threadIdx.x;
+                if (v) atomicAdd(sb.acc + (long long)b * SERIES_ROW + (c < 6 ? c : c + 6), v);
+            }
+            __syncthreads();
         }
     }
 }
@@ -1318,12 +1351,9 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
         coords_of(p, A, x, y, z);
         float m[3] = {0.f, 0.f, 0.f};
         float f[L::Q];
-        if (s > 0) { // covered: the streamed values f_i(A, t+1)
-            if (sb.flags[A] & FL_BND) { // a boundary node at t: kept by k_bnd
-                for (int i = 0; i < L::Q; ++i) f[i] = ldP(dst + (long long)i * p.N + A);
-            } else {
-                pull_all<L, P>(p, src, (const float *)nullptr, x, y, z, A, f);
-            }
+        if (s > 0) { // covered: the streamed values f_i(A, t+1) (cut links read the
+                     // wall values that k_links left in the solid nodes' slots)
+            pull_all<L, P>(p, src, (const float *)nullptr, x, y, z, A, f);
             atomicAdd(&sb.counters[1], 1ull);
         } else { // uncovered: refill f(A, t+1) = f^eq(rho_bar, u_B or u_bar)
             double r1[3], uBd[3];
@@ -1344,12 +1374,11 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
                 if (!ok) continue;
                 const long long nb = cell_of(p, q[0], q[1], q[2]);
                 if (sb.owner_t[nb] != 0) continue;
-                float dr, uu[3];
-                moments_hat<L>(p, src, nb, dr, uu);
-                sum += dr;
-                us[0] += uu[0];
-                us[1] += uu[1];
-                us[2] += uu[2];
+                const float4 m = load_mac((const float *)sb.mac_t, nb); // moments of f(t)
+                sum += m.x;
+                us[0] += m.y;
+                us[1] += m.z;
+                us[2] += m.w;
                 nn++;
             }
             long long ec[3];
@@ -1376,6 +1405,7 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
         if (s < 0) { // the refilled node starts the next step collided
             float drho, u[3];
             moments_f<L>(p, f, drho, u);
+            store_mac((float *)sb.mac_t1, A, drho, u);
             collide_f<L>(p, f, drho, u);
             for (int i = 0; i < L::Q; ++i) stS(dst + (long long)i * p.N + A, f[i]);
         }
