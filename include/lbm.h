@@ -160,7 +160,7 @@ typedef struct lbm_domain_desc {
     double gravity[3];       /* acceleration of the free bodies: each feels its
                                 weight less buoyancy, (rho_b - rho0) V gravity */
     int edge_rule;           /* LBM_EDGE_RULE_* */
-    int reserved_edge;       /* must be 0 */
+    int free_scheme;         /* LBM_FREE_*: covered / uncovered sets of free bodies */
 } lbm_domain_desc;
 
 typedef struct lbm_body {
@@ -179,15 +179,34 @@ typedef struct lbm_body {
                         theta(t) = theta0 + (t - t0) W[2] */
 } lbm_body;
 /* Free bodies follow Newton's and Euler's equations by forward Euler, as the
- * paper's sedimentation tests do: in step t the body moves with U(t), W(t)
- * (so the covered / uncovered sets of the step are explicit), then
+ * paper's sedimentation tests do:
  *   U(t+1) = U(t) + (F(t) + (rho_b - rho0) V gravity) / M,  M = rho_b V
  *   W(t+1) = W(t) + T(t) / I
  * with F, T the lattice-frame force and torque of step t (Eqs. ForceInMovement,
- * TorqueInMovement: static plus impulsive terms), V = pi R^2 nz (cylinder) or
- * 4/3 pi R^3 (sphere), I = M R^2 / 2 (cylinder, about z) or 2/5 M R^2 (sphere).
- * A free body that comes within 2 cells of a non-periodic face or whose
- * surface speed exceeds 0.25 makes the series reads return LBM_ERR_STATE. */
+ * TorqueInMovement: static plus impulsive terms), V = pi R^2 nz (cylinder),
+ * pi R R2 nz (ellipse) or 4/3 pi R^3 (sphere), I = M R^2 / 2 (cylinder, about
+ * z), M (R^2 + R2^2) / 4 (ellipse) or 2/5 M R^2 (sphere).  The impulsive terms
+ * need the nodes a body covers and uncovers, which for a free body depend on
+ * its motion; the descriptor's free_scheme picks how (Sec. 3, after Eq.
+ * ForceInMovement):
+ *   LBM_FREE_EXPLICIT (0): in step t the body moves with U(t), W(t), so the
+ *     sets of the step are known before its force;
+ *   LBM_FREE_AIDUN (1): the force at t takes the impulsive terms of the nodes
+ *     covered and uncovered between t-1 and t (the Aidun-type approximation;
+ *     the series row of step t reports those), and the body moves from t to
+ *     t+1 with U(t+1), W(t+1);
+ *   LBM_FREE_PREDICTOR (2): the force at t takes the sets of a displacement
+ *     predicted with U(t), W(t); then the displacement is recomputed with
+ *     U(t+1), W(t+1) (two displacements per step); a node uncovered by both
+ *     keeps the refill the force used, one uncovered only by the second is
+ *     refilled then.
+ * These schemes act on free bodies; prescribed bodies always take the exact
+ * sets of their motion.  A free body that comes within 2 cells of a
+ * non-periodic face or whose surface speed exceeds 0.25 makes the series
+ * reads return LBM_ERR_STATE. */
+#define LBM_FREE_EXPLICIT 0
+#define LBM_FREE_AIDUN 1
+#define LBM_FREE_PREDICTOR 2
 
 typedef struct lbm_stats {
     int64_t step;            /* current time step t */

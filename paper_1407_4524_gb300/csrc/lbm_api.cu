@@ -161,6 +161,13 @@ struct lbm_domain {
     int8_t *apm_sign = nullptr;
     long long *apm_cnt = nullptr;
     long long apm_cap_total = 0;
+    // semi-implicit free-body schemes: impulsive terms of the previous
+    // displacement (scheme 1) and the covered / uncovered lists of the
+    // predicted displacement (scheme 2)
+    double *imp_prev = nullptr;
+    uint32_t *apm_pred_cell = nullptr;
+    int8_t *apm_pred_sign = nullptr;
+    long long *apm_pred_cnt = nullptr;
     double *series = nullptr;
     long long series_cap = 0;
     double *poses = nullptr;
@@ -283,6 +290,10 @@ void free_body_buffers(lbm_domain *D) {
     D->apm_cell = nullptr;
     D->apm_sign = nullptr;
     D->apm_cnt = nullptr;
+    D->imp_prev = nullptr;
+    D->apm_pred_cell = nullptr;
+    D->apm_pred_sign = nullptr;
+    D->apm_pred_cnt = nullptr;
     D->series = nullptr;
     D->poses = nullptr;
     D->link_pre = nullptr;
@@ -443,6 +454,11 @@ StepBufs step_bufs(lbm_domain *D) {
     sb.counters = D->counters;
     sb.t = D->t;
     sb.par = (int)(D->t & 1);
+    sb.phase = PH_ALL;
+    sb.imp_prev = D->imp_prev;
+    sb.apm_pred_cell = D->apm_pred_cell;
+    sb.apm_pred_sign = D->apm_pred_sign;
+    sb.apm_pred_cnt = D->apm_pred_cnt;
     return sb;
 }
 
@@ -575,10 +591,59 @@ int timing_events(lbm_domain *D, cudaEvent_t &a, cudaEvent_t &b) {
     return LBM_OK;
 }
 
+// the free-body scheme a step runs (the explicit one when no body is free)
+int step_scheme(const lbm_domain *D) { return D->n_free ? D->p.free_scheme : LBM_FREE_EXPLICIT; }
+
+// semi-implicit schemes, after the stream-collide pass: the force row of step
+// t (with the impulsive terms of the previous displacement, or of the
+// predicted one whose lists sb_pred names), the velocities of t+1, the poses
+// of t+1 they give, the owners, lists and cut links of the displacement made,
+// then its impulsive terms and refill (scheme 1) or the refill of the nodes
+// the prediction did not uncover (scheme 2).  All on stream s.
+int finish_semi(lbm_domain *D, int scheme, const StepBufs &sb) {
+    const int Q = D->Q, prec = D->prec;
+    StepBufs s1 = sb;
+    if (scheme == LBM_FREE_AIDUN) {
+        s1.phase = PH_REDUCE;
+    } else {
+        s1.apm_cell = D->apm_pred_cell;
+        s1.apm_sign = D->apm_pred_sign;
+        s1.apm_cnt = D->apm_pred_cnt;
+    }
+    CK(launch_finish(Q, prec, D->p, s1, D->s));
+    const unsigned long long *tdev = D->counters + 9 + (D->t & 1);
+    CK(launch_free(D->p, D->dbodies, D->series, D->counters, tdev, D->s));
+    CK(launch_pose1(D->p, D->dbodies, D->poses, tdev, D->s));
+    GeomArgs g = geom_args(D, true);
+    if (prec == LBM_FP64) {
+        CK(launch_geom_a(Q, D->p, g, D->s));
+        CK(launch_geom_b(Q, D->p, g, D->s));
+        CK(launch_geom_c(Q, D->p, g, D->s));
+    } else {
+        CK(launch_fgeom1(Q, D->p, g, D->s));
+        CK(launch_fgeom2(Q, D->p, g, D->s));
+    }
+    StepBufs s2 = sb;
+    s2.phase = scheme == LBM_FREE_AIDUN ? PH_IMP : PH_FIX;
+    CK(launch_finish(Q, prec, D->p, s2, D->s));
+    return LBM_OK;
+}
+
+// scheme 2, before the stream-collide pass: owners and covered / uncovered
+// lists of the displacement predicted with U(t), into the prediction's lists
+GeomArgs predicted_geom(lbm_domain *D) {
+    GeomArgs g = geom_args(D, true);
+    g.apm_cell = D->apm_pred_cell;
+    g.apm_sign = D->apm_pred_sign;
+    g.apm_cnt = D->apm_pred_cnt;
+    return g;
+}
+
 int do_step(lbm_domain *D) {
     const int Q = D->Q, prec = D->prec;
     if (prec != LBM_FP64 && D->nb) return do_step_overlapped(D);
     D->lists_dirty = false; // boundary-node lists belong to the overlapped path only
+    const int scheme = step_scheme(D);
     if (D->nb && (D->n_moving || D->prep_dirty)) {
         // the A+/A- lists of the previous step update the solid flags of t
         CK(launch_prep(D->p, D->dbodies, D->link_cnt[D->t & 1], D->link_pre, D->tile_pre, D->poses, D->t,
@@ -586,10 +651,13 @@ int do_step(lbm_domain *D) {
         D->prep_dirty = false;
     }
     if (D->n_moving) {
-        GeomArgs g = geom_args(D, true);
+        // semi-implicit schemes: the node flags of t+1 (moments kept on a band
+        // around the free bodies) from the displacement with U(t), and scheme
+        // 2's predicted lists; the cut links follow the displacement made
+        GeomArgs g = scheme == LBM_FREE_PREDICTOR ? predicted_geom(D) : geom_args(D, true);
         CK(launch_geom_a(Q, D->p, g, D->s));
         CK(launch_geom_b(Q, D->p, g, D->s));
-        CK(launch_geom_c(Q, D->p, g, D->s));
+        if (scheme == LBM_FREE_EXPLICIT) CK(launch_geom_c(Q, D->p, g, D->s));
     }
     StepBufs sb = step_bufs(D);
     if (D->nb) CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
@@ -601,8 +669,13 @@ int do_step(lbm_domain *D) {
     }
     CK(launch_bulk(Q, prec, D->p, sb, D->s));
     if (D->timing) CK(record_timing(D, tb));
-    if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
-    if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->counters + 9 + (D->t & 1), D->s));
+    if (scheme != LBM_FREE_EXPLICIT) {
+        int rc = finish_semi(D, scheme, sb);
+        if (rc) return rc;
+    } else {
+        if (D->nb) CK(launch_finish(Q, prec, D->p, sb, D->s));
+        if (D->n_free) CK(launch_free(D->p, D->dbodies, D->series, D->counters, D->counters + 9 + (D->t & 1), D->s));
+    }
     D->t += 1;
     if (D->capturing) D->cap_k += 1;
     return LBM_OK;
@@ -694,6 +767,28 @@ int do_step_links(lbm_domain *D) {
                         D->tile_pre, D->s));
         D->prep_dirty = false;
         D->lists_dirty = false;
+    }
+    const int scheme = step_scheme(D);
+    if (scheme != LBM_FREE_EXPLICIT) { // semi-implicit free-body schemes: one stream
+        StepBufs sb = step_bufs(D);
+        if (scheme == LBM_FREE_PREDICTOR) {
+            CK(cudaMemsetAsync(D->apm_pred_cnt, 0, sizeof(long long) * (size_t)D->nb, D->s));
+            CK(launch_fgeom1(Q, D->p, predicted_geom(D), D->s));
+        }
+        CK(launch_links(Q, prec, D->p, sb, D->links_grid, D->s));
+        cudaEvent_t ta = nullptr, tb = nullptr;
+        if (D->timing) {
+            int trc = timing_events(D, ta, tb);
+            if (trc) return trc;
+            CK(record_timing(D, ta));
+        }
+        CK(launch_bulk(Q, prec, D->p, sb, D->s));
+        if (D->timing) CK(record_timing(D, tb));
+        int rc = finish_semi(D, scheme, sb);
+        if (rc) return rc;
+        D->t += 1;
+        if (D->capturing) D->cap_k += 1;
+        return LBM_OK;
     }
     const bool side = !D->side_serial;
     cudaStream_t ss = side ? D->s2 : D->s;
@@ -787,8 +882,10 @@ int create_domain_impl(const lbm_domain_desc *desc, lbm_domain **out, bool batch
         return fail(LBM_ERR_ARG, "unknown refill rule");
     if (d.inlet_profile != LBM_INLET_UNIFORM && d.inlet_profile != LBM_INLET_PARABOLIC)
         return fail(LBM_ERR_ARG, "unknown inlet profile");
-    if ((d.edge_rule != LBM_EDGE_RULE_LINK && d.edge_rule != LBM_EDGE_RULE_ZOUHE) || d.reserved_edge)
+    if (d.edge_rule != LBM_EDGE_RULE_LINK && d.edge_rule != LBM_EDGE_RULE_ZOUHE)
         return fail(LBM_ERR_ARG, "unknown edge rule");
+    if (d.free_scheme < LBM_FREE_EXPLICIT || d.free_scheme > LBM_FREE_PREDICTOR)
+        return fail(LBM_ERR_ARG, "unknown free-body scheme");
     if (d.edge_rule == LBM_EDGE_RULE_ZOUHE) {
         const int nn[3] = {d.nx, d.ny, d.nz};
         for (int a = 0; a < 3; ++a)
@@ -819,6 +916,7 @@ int create_domain_impl(const lbm_domain_desc *desc, lbm_domain **out, bool batch
     p.nonper = !(p.per[0] && p.per[1] && p.per[2]);
     p.exact = d.precision == LBM_FP64;
     p.linkmode = (!batch && d.precision != LBM_FP64) ? 1 : 0;
+    p.free_scheme = d.free_scheme;
     {
         // LBM_STAGED=1 selects the stream-collide kernel that stages the
         // source rows in shared memory by bulk copies (same results bit for
@@ -1035,6 +1133,12 @@ int place_bodies(lbm_domain *D, const lbm_body *hb, int n) {
     if ((rc = alloc_t(D, &D->apm_cell, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_sign, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
     if ((rc = alloc_t(D, &D->apm_cnt, nbx, &T))) return rc;
+    if ((rc = alloc_t(D, &D->imp_prev, nbx * 6, &T))) return rc; // zero: no displacement before t = 0
+    if (D->p.free_scheme == LBM_FREE_PREDICTOR) {
+        if ((rc = alloc_t(D, &D->apm_pred_cell, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
+        if ((rc = alloc_t(D, &D->apm_pred_sign, (size_t)std::max<long long>(aoff, 1), &T))) return rc;
+        if ((rc = alloc_t(D, &D->apm_pred_cnt, nbx, &T))) return rc;
+    }
     if ((rc = alloc_t(D, &D->series, (size_t)D->series_cap * nbx * SERIES_ROW, &T))) return rc;
     if ((rc = alloc_t(D, &D->poses, nbx * POSE_STRIDE, &T))) return rc;
     if ((rc = alloc_t(D, &D->link_pre, nbx + 1, &T))) return rc;
@@ -1600,6 +1704,8 @@ int lbm_launches_per_step(const lbm_domain *D, int *out) {
     else
         *out = 1 + (D->nb ? 2 : 0) + (D->n_moving ? 4 : 0) + (D->nb && D->prep_dirty && !D->n_moving ? 1 : 0);
     if (D->n_free) *out += 1; // free-body update
+    if (step_scheme(D) != LBM_FREE_EXPLICIT) // poses of t+1, second end-of-step pass, geometry after the force
+        *out += D->prec == LBM_FP64 ? 4 : (D->p.free_scheme == LBM_FREE_PREDICTOR ? 3 : 2);
     if (D->p.zouhe) *out += 1; // Zou-He face nodes
     return LBM_OK;
 }

@@ -145,6 +145,8 @@ struct Params {
     int stage_expire_test; // test hook: the staged kernel issues no copy, so its waits expire
     int nsm;     // multiprocessors of the device
     int zouhe;   // wall / inlet faces are Zou-He nodes (else half-way links)
+    int free_scheme; // covered / uncovered sets of free bodies: 0 explicit, 1 backward sets
+                     // of the previous displacement, 2 predictor-corrector
     int linkmode; // reduced precision, single domain: wall values on cut links are written
                   // into the solid nodes' slots before the stream-collide pass (which then
                   // steps the boundary nodes too); the moments (drho, u) of the nodes near

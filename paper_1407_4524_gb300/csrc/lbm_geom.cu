@@ -239,9 +239,16 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_geom_b(Params p, GeomArgs g) {
                 if (in1) apm_sign |= 1u << j;
             }
         }
-        // node flags (FP64 mode: the moment-store flag follows the geometry of t+1)
-        if (g.do_flags && dist >= Rin - 2.0f && dist <= Rout + 5.5f)
-            g.flags[rc.cell] = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
+        // node flags (FP64 mode: the moment-store flag follows the geometry of t+1;
+        // under the semi-implicit schemes a free body's pose of t+1 is known only
+        // after the step's force, so its moments are kept on the band within
+        // R + MAC_BAND of the pose the flags are built from, which holds the
+        // nodes within two links of the body at t+1 and t+2 whatever the update)
+        if (g.do_flags && dist >= Rin - 2.0f && dist <= Rout + 5.5f) {
+            uint8_t nf = node_flags<L>(p, g.owner_t, owner_L, rc.x, rc.y, rc.z, rc.cell);
+            if (p.free_scheme && B.free && dist <= Rout + MAC_BAND) nf |= FL_MAC;
+            g.flags[rc.cell] = nf;
+        }
         if (dist >= Rin - 0.5f && dist <= Rout + 2.0f && owner_L[rc.cell] == 0) {
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
@@ -770,8 +777,11 @@ static cudaError_t import_t(int prec, const Params &p, const double *in, void *p
 }
 
 // Free bodies (one thread per body), after the force/torque row of step t is
-// complete: the pose advances with U(t) -- the motion the step's A+/A- sets
-// were built from --, then forward Euler gives U(t+1) and W(t+1) from the
+// complete.  Explicit scheme: the pose advances with U(t) -- the motion the
+// step's A+/A- sets were built from.  Semi-implicit schemes (the row holds the
+// impulsive terms of the previous displacement or of a predicted one): the
+// pose advances with U(t+1), and the step's A+/A- sets are built afterwards.
+// Forward Euler gives U(t+1) and W(t+1) from the
 // lattice-frame force and torque (Eqs. ForceInMovement, TorqueInMovement:
 // static plus impulsive terms), weight less buoyancy (rho_b - rho0) V g and
 // M = rho_b V, I = M R^2/2 (cylinder, about z), M (R^2 + R2^2)/4 (ellipse,
@@ -796,12 +806,11 @@ __global__ void k_free(Params p, BodyDev *bodies, const double *series, unsigned
     if (B.shape == 1) I = 0.4 * M * B.R * B.R;
     else if (B.shape == 2) I = 0.25 * M * (B.R * B.R + B.R2 * B.R2);
     else I = 0.5 * M * B.R * B.R;
-    double X1[3];
+    double X1[3], X0[3];
     pose(B, t + 1, X1);
-    const double th1 = orient(B, t + 1);
-    for (int a = 0; a < 3; ++a) B.X0[a] = X1[a];
-    B.theta0 = th1;
-    B.t0 = t + 1;
+    pose(B, t, X0);
+    double th1 = orient(B, t + 1);
+    const double th0 = orient(B, t);
     for (int a = 0; a < 3; ++a) {
         const double F = Rw[a] + Rw[6 + a];
         B.U[a] = B.U[a] + (F + (B.density_ratio - 1.0) * p.rho0 * V * p.gravity[a]) / M;
@@ -811,6 +820,13 @@ __global__ void k_free(Params p, BodyDev *bodies, const double *series, unsigned
     } else {
         B.W[2] = B.W[2] + (Rw[5] + Rw[11]) / I;
     }
+    if (p.free_scheme) { // semi-implicit: the step's displacement is made with U(t+1)
+        for (int a = 0; a < 3; ++a) X1[a] = X0[a] + B.U[a];
+        th1 = th0 + B.W[2];
+    }
+    for (int a = 0; a < 3; ++a) B.X0[a] = X1[a];
+    B.theta0 = th1;
+    B.t0 = t + 1;
     bool bad = false;
     for (int a = 0; a < 3; ++a) {
         if (p.per[a] || (a == 2 && along_z(B.shape))) continue;
@@ -827,6 +843,25 @@ cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, 
                         const unsigned long long *tdev, cudaStream_t s) {
     if (p.nb == 0) return cudaSuccess;
     k_free<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, series, counters, tdev);
+    return cudaGetLastError();
+}
+
+// semi-implicit schemes, after k_free: the poses of t+1 of the free bodies
+// from their new records (wrapped pose and orientation of t+1; those of t stay)
+__global__ void k_pose1(Params p, const BodyDev *bodies, double *poses, const unsigned long long *tdev) {
+    const long long t = (long long)*tdev;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nb || !bodies[b].free) return;
+    double *P = poses + (long long)b * POSE_STRIDE;
+    pose(bodies[b], t + 1, P + 6);
+    wrap_pose(p, P + 6, P + 9);
+    if (bodies[b].shape == 2) sincos_cw(orient(bodies[b], t + 1), P[25], P[24]);
+}
+
+cudaError_t launch_pose1(const Params &p, const BodyDev *bodies, double *poses, const unsigned long long *tdev,
+                         cudaStream_t s) {
+    if (p.nb == 0) return cudaSuccess;
+    k_pose1<<<(p.nb + 127) / 128, 128, 0, s>>>(p, bodies, poses, tdev);
     return cudaGetLastError();
 }
 

@@ -134,6 +134,11 @@ cudaError_t launch_bnd_lists(int Q, const Params &p, const GeomArgs &g, cudaStre
 cudaError_t launch_free(const Params &p, BodyDev *bodies, const double *series, unsigned long long *counters,
                         const unsigned long long *tdev, cudaStream_t s);
 
+// semi-implicit free-body schemes: poses of t+1 of the free bodies from the
+// records k_free left
+cudaError_t launch_pose1(const Params &p, const BodyDev *bodies, double *poses, const unsigned long long *tdev,
+                         cudaStream_t s);
+
 // population export: fhat as FP64 f (adds w back for the shifted modes)
 cudaError_t launch_export(int Q, int prec, const Params &p, const void *pop, double *out, cudaStream_t s);
 cudaError_t launch_import(int Q, int prec, const Params &p, const double *in, void *pop, cudaStream_t s);

@@ -77,7 +77,31 @@ struct StepBufs {
     unsigned long long *acc;      // reduced-precision modes: per body SERIES_ROW fixed-point sums
     long long t;
     int par; // parity of the step: its index is counters[9 + par] on the device
+    // free-body schemes (Params::free_scheme 1 / 2): what the end-of-step kernel does
+    int phase;                    // PH_ALL, PH_REDUCE, PH_IMP or PH_FIX
+    double *imp_prev;             // scheme 1: impulsive terms of the last displacement [nb][6]
+    const uint32_t *apm_pred_cell; // scheme 2: covered / uncovered lists of the prediction
+    const int8_t *apm_pred_sign;
+    const long long *apm_pred_cnt;
 };
+
+// end-of-step phases: PH_ALL the series row and the impulsive terms with the
+// refill of the step's covered / uncovered lists; the schemes of free bodies
+// split it into PH_REDUCE (the row of the link sums; a scheme-1 free body's
+// impulsive terms are those of its previous displacement) before the body
+// moves, PH_IMP (impulsive terms and refill of the lists of the displacement
+// made: prescribed bodies into the row, scheme-1 free bodies kept for the next
+// step) after it, and PH_FIX (scheme 2: refill of the nodes the recomputed
+// displacement uncovers and the predicted one did not)
+constexpr int PH_ALL = 0, PH_REDUCE = 1, PH_IMP = 2, PH_FIX = 3;
+
+// scheme 2: did the predicted displacement of body b uncover node A?
+__device__ __forceinline__ bool pred_uncovered(const StepBufs &sb, const BodyDev &B, int b, long long A) {
+    const long long n = sb.apm_pred_cnt[b];
+    for (long long e = 0; e < n; ++e)
+        if (sb.apm_pred_cell[B.apm_off + e] == (uint32_t)A && sb.apm_pred_sign[B.apm_off + e] < 0) return true;
+    return false;
+}
 
 // =================================================================== exact ==
 // FP64, operation order of the oracle (one expression per formula).
@@ -1215,9 +1239,14 @@ __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long base = 0; base < cnt; base += IMP_THREADS) {
         const long long e = base + threadIdx.x;
-        if (e < cnt) {
-            const long long A = sb.apm_cell[B.apm_off + e];
-            const int s = sb.apm_sign[B.apm_off + e];
+        const long long A0 = e < cnt ? sb.apm_cell[B.apm_off + e] : 0;
+        const int s0 = e < cnt ? sb.apm_sign[B.apm_off + e] : 0;
+        // PH_FIX: only the nodes uncovered now and not by the prediction
+        const bool skip = sb.phase == PH_FIX && (s0 > 0 || pred_uncovered(sb, B, b, A0));
+        if (e < cnt && skip) sgn[threadIdx.x] = 0;
+        if (e < cnt && !skip) {
+            const long long A = A0;
+            const int s = s0;
             int x, y, z;
             coords_of(p, A, x, y, z);
             double m[3] = {0.0, 0.0, 0.0};
@@ -1303,7 +1332,9 @@ __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &
             double r[3], tq[3];
             disp(p, X, x, y, z, r);
             cross3(r, m, tq);
-            sb.flags[A] = (uint8_t)((sb.flags[A] & ~FL_SOLID) | (s > 0 ? FL_SOLID : 0));
+            // the free-body schemes leave the solid flags to the next prep (the
+            // lists it applies are those of the displacement made)
+            if (p.free_scheme == 0) sb.flags[A] = (uint8_t)((sb.flags[A] & ~FL_SOLID) | (s > 0 ? FL_SOLID : 0));
             part[threadIdx.x][0] = m[0];
             part[threadIdx.x][1] = m[1];
             part[threadIdx.x][2] = m[2];
@@ -1318,15 +1349,16 @@ __device__ __forceinline__ void imp_body_exact(const Params &p, const StepBufs &
             for (int e2 = 0; e2 < m_; ++e2) {
                 if (sgn[e2] > 0)
                     for (int a = 0; a < 6; ++a) acc[a] += part[e2][a];
-                else
+                else if (sgn[e2] < 0)
                     for (int a = 0; a < 6; ++a) acc[a] -= part[e2][a];
             }
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && sb.phase != PH_FIX) {
         double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
-        for (int a = 0; a < 6; ++a) row[6 + a] = acc[a];
+        double *to = (sb.phase == PH_IMP && B.free && p.free_scheme == 1) ? sb.imp_prev + 6 * b : row + 6;
+        for (int a = 0; a < 6; ++a) to[a] = acc[a];
     }
 }
 
@@ -1347,6 +1379,8 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
     for (long long e = threadIdx.x; e < cnt; e += IMP_THREADS) {
         const long long A = sb.apm_cell[B.apm_off + e];
         const int s = sb.apm_sign[B.apm_off + e];
+        // PH_FIX: only the nodes uncovered now and not by the prediction
+        if (sb.phase == PH_FIX && (s > 0 || pred_uncovered(sb, B, b, A))) continue;
         int x, y, z;
         coords_of(p, A, x, y, z);
         float m[3] = {0.f, 0.f, 0.f};
@@ -1420,9 +1454,10 @@ __device__ __forceinline__ void imp_body_fast(const Params &p, const StepBufs &s
         }
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < 6 && sb.phase != PH_FIX) {
         double *row = sb.series + ((sb.t % p.series_cap) * p.nb + b) * SERIES_ROW;
-        row[6 + threadIdx.x] = from_fx(acc_s[threadIdx.x]);
+        double *to = (sb.phase == PH_IMP && B.free && p.free_scheme == 1) ? sb.imp_prev + 6 * b : row + 6;
+        to[threadIdx.x] = from_fx(acc_s[threadIdx.x]);
     }
 }
 
@@ -1446,6 +1481,10 @@ template <bool EXACT> __device__ __forceinline__ void reduce_body(const Params &
         if (!isfinite(acc)) atomicOr(&sb.counters[5], 1ull); // FP64 mode: a non-finite force marks the solve unstable
     }
     if (!B.moving && threadIdx.x < 6) row[6 + threadIdx.x] = 0.0;
+    // scheme 1: a free body's impulsive terms are those of its previous
+    // displacement (known before the body moves)
+    if (sb.phase == PH_REDUCE && B.free && p.free_scheme == 1 && threadIdx.x < 6)
+        row[6 + threadIdx.x] = sb.imp_prev[6 * b + threadIdx.x];
 }
 
 // end of step: blocks [0, nb) reduce the link contributions of one body,
@@ -1456,15 +1495,17 @@ template <class L, class P> __global__ void __launch_bounds__(IMP_THREADS) k_fin
     // there); the next step's index goes into the other parity's word, which
     // no kernel of this step reads
     sb.t = (long long)sb.counters[9 + sb.par];
-    if (blockIdx.x == 0 && threadIdx.x == 0) sb.counters[9 + (sb.par ^ 1)] = (unsigned long long)(sb.t + 1);
-    if (!P::exact && blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool reduce = sb.phase == PH_ALL || sb.phase == PH_REDUCE; // once per step
+    if (reduce && blockIdx.x == 0 && threadIdx.x == 0) sb.counters[9 + (sb.par ^ 1)] = (unsigned long long)(sb.t + 1);
+    if (!P::exact && reduce && blockIdx.x == 0 && threadIdx.x == 0) {
         sb.counters[4] = sb.counters[3];
         sb.counters[3] = 0ull;
     }
     if ((int)blockIdx.x < p.nb) {
-        reduce_body<P::exact>(p, sb, blockIdx.x);
+        if (reduce) reduce_body<P::exact>(p, sb, blockIdx.x);
         return;
     }
+    if (sb.phase == PH_REDUCE) return;
     if constexpr (P::exact) imp_body_exact<L, P>(p, sb, sb.moving_ids[blockIdx.x - p.nb]);
     else imp_body_fast<L, P>(p, sb, sb.moving_ids[blockIdx.x - p.nb]);
 }

@@ -39,7 +39,7 @@ class lbm_domain_desc(C.Structure):
         ("device", C.c_int), ("tau", C.c_double), ("rho0", C.c_double), ("u_in", C.c_double),
         ("force", C.c_double * 3), ("u0", C.c_double * 3), ("series_capacity", C.c_int64),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-        ("gravity", C.c_double * 3), ("edge_rule", C.c_int), ("reserved_edge", C.c_int),
+        ("gravity", C.c_double * 3), ("edge_rule", C.c_int), ("free_scheme", C.c_int),
     ]
 
 
@@ -187,6 +187,7 @@ def domain_desc(spec: dict, device: int = 0, series_capacity: int = 0):
     d.u_in = float(inlet.get("u", 0.0))
     d.refill = {"uB": 0, "ubar": 1, "extrap": 2}[spec.get("refill", "uB")]
     d.edge_rule = {"link": 0, "zouhe": 1}[spec.get("edge_rule", "link")]
+    d.free_scheme = {"explicit": 0, "aidun": 1, "predictor": 2}[spec.get("free_scheme", "explicit")]
     g = spec.get("force")
     d.has_force = int(g is not None)
     for j in range(3):

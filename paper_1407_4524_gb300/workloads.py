@@ -24,6 +24,8 @@ units per step):
              "W", "halfway", "t0"; free bodies: "free", "density_ratio";
              ellipses: "R2" (second semi-axis), "theta0"}
   gravity    acceleration of the free bodies (lattice units)
+  free_scheme "explicit" | "aidun" | "predictor": covered / uncovered sets of
+             free bodies (Sec. 3, after Eq. ForceInMovement)
   precision  "fp64" | "fp32" | "fp16"  (CUDA side only)
 """
 from __future__ import annotations
