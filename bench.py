@@ -231,26 +231,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
+def _device_timed(spec, args, dev, world, stream, sampler=None):
+    """Build the domain, run exactly `warmup` untimed steps (stream-collide
+    timing events on), then time `steps` steps between CUDA events on the
+    launching stream.  Returns the open domain and the figures."""
     import torch
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
     from paper_1407_4524_gb300 import lbm
-    spec = _workload(args.workload, args.precision, args.n, args.bodies)
-    stream = torch.cuda.Stream(dev)
     dom = lbm.Domain(spec, device=dev, stream=stream, series_capacity=max(8192, args.steps + args.warmup + 16))
-    cells = dom.N
-    st0 = dom.stats()
-    fluid_cells = st0["fluid_cells"]
-    Q = dom.q
-    sbytes = {"fp64": 8, "fp32": 4, "fp16": 2}[args.precision]
-
     # warm-up: exactly `warmup` steps, with the stream-collide kernel's timing
     # events already on.  The library replays captured 16-step graphs for runs
     # of >= 16 steps; the graph (with its timing events) is recorded here,
@@ -261,10 +248,6 @@ def run_ours(args):
     dom.step(args.warmup - 1)
     torch.cuda.synchronize()
     dom.kernel_time()  # discard the warm-up windows
-    launches_per_step = dom.launches_per_step()
-
-    # device-timed region: K steps, events on the launching stream
-    sampler = ClockSampler(dev) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
@@ -281,7 +264,54 @@ def run_ours(args):
     n_bulk, bulk_ms = dom.kernel_time()
     dom.set_kernel_timing(False)
     clocks = sampler.stop() if sampler else None
-    ms, mlups = replica_mlups(ms, cells, args.steps, world)
+    ms, mlups = replica_mlups(ms, dom.N, args.steps, world)
+    return dom, dict(ms=ms, mlups=mlups, n_bulk=n_bulk, bulk_ms=bulk_ms, clocks=clocks,
+                     launches_per_step=dom.launches_per_step())
+
+
+def _roofline(args, precision, dom, fluid_cells, n_bulk, bulk_ms):
+    """roofline object of the stream-collide kernel: algorithmic bytes (one
+    read and one write of Q stored values per fluid node) over its mean
+    CUDA-event window, against the measured copy bandwidth"""
+    peak, peak_kind = _peaks()
+    sbytes = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    bulk_avg_s = bulk_ms * 1e-3 / max(1, n_bulk)
+    alg_bytes = 2.0 * dom.q * sbytes * fluid_cells
+    achieved = alg_bytes / bulk_avg_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tpath) as fh:
+            tj = json.load(fh)
+        key = f"{args.workload}:{precision}"
+        if key in tj and tj[key].get("kernel_rev") == _kernel_rev():
+            traffic = tj[key]["bytes_per_launch"]
+    except Exception:
+        traffic = None
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "k_bulk (pull-stream + BGK collide)", "kernel_ms": round(bulk_avg_s * 1e3, 4),
+            "alg_bytes_per_launch": int(alg_bytes)}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    spec = _workload(args.workload, args.precision, args.n, args.bodies)
+    stream = torch.cuda.Stream(dev)
+    sampler = ClockSampler(dev) if rank == 0 else None
+    dom, m = _device_timed(spec, args, dev, world, stream, sampler)
+    cells = dom.N
+    fluid_cells = dom.stats()["fluid_cells"]
+    ms, mlups, clocks = m["ms"], m["mlups"], m["clocks"]
+    launches_per_step = m["launches_per_step"]
 
     # end-to-end through the C ABI with host buffers: each step uploads the
     # bodies' kinematics (lbm_update_bodies: host array -> pinned staging ->
@@ -313,38 +343,34 @@ def run_ours(args):
     e2e = {"value": round(world * cells * e2e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / e2e_steps),
            "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / e2e_steps)}
+    roofline = _roofline(args, args.precision, dom, fluid_cells, m["n_bulk"], m["bulk_ms"])
+    # the bulk kernel's mean window over the mean step (the windows measured
+    # cover the plain steps and the last graph replay, not every step)
+    step_frac = (roofline["kernel_ms"] / max(1e-9, ms / args.steps)) if world == 1 else None
+    dom.close()
+
+    # the same workload with FP16 storage of f - w: its own device-timed run
+    # (same steps and warm-up), reported beside the main line
+    fp16 = None
+    if args.precision == "fp32" and not args.no_fp16:
+        spec16 = _workload(args.workload, "fp16", args.n, args.bodies)
+        sampler16 = ClockSampler(dev) if rank == 0 else None
+        dom16, m16 = _device_timed(spec16, args, dev, world, stream, sampler16)
+        fc16 = dom16.stats()["fluid_cells"]
+        fp16 = dict(value=round(m16["mlups"], 1), ms_per_step=round(m16["ms"] / args.steps, 4),
+                    roofline=_roofline(args, "fp16", dom16, fc16, m16["n_bulk"], m16["bulk_ms"]),
+                    clocks=m16["clocks"], launches_per_step=m16["launches_per_step"])
+        dom16.close()
 
     if rank != 0:
-        dom.close()
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    peak, peak_kind = _peaks()
-    bulk_avg_s = bulk_ms * 1e-3 / max(1, n_bulk)
-    alg_bytes = 2.0 * Q * sbytes * fluid_cells
-    achieved = alg_bytes / bulk_avg_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(tpath) as fh:
-            tj = json.load(fh)
-        key = f"{args.workload}:{args.precision}"
-        if key in tj and tj[key].get("kernel_rev") == _kernel_rev():
-            traffic = tj[key]["bytes_per_launch"]
-    except Exception:
-        traffic = None
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_bulk (pull-stream + BGK collide)", "kernel_ms": round(bulk_avg_s * 1e3, 4),
-                "alg_bytes_per_launch": int(alg_bytes)}
-    # the bulk kernel's mean window over the mean step (the windows measured
-    # cover the plain steps and the last graph replay, not every step)
-    step_frac = (bulk_avg_s * 1e3 / max(1e-9, ms / args.steps)) if world == 1 else None
-    dom.close()
     serving = run_serving(args, dev) if (world == 1 and args.serving_requests > 0) else None
     cpu = cpu_baseline(spec, budget_s=args.cpu_budget) if (world == 1 and not args.no_cpu) else None
-    pop_bytes = 2 * Q * sbytes * cells
+    sbytes = {"fp64": 8, "fp32": 4, "fp16": 2}[args.precision]
+    pop_bytes = 2 * dom.q * sbytes * cells
     line = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -359,8 +385,15 @@ def run_ours(args):
                    "bulk_share_of_step": round(step_frac, 4) if step_frac else None},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks,
-        "serving": serving,
     }
+    if fp16:
+        # FP16 storage (FP32 arithmetic): whole-job MLUPS of the same workload
+        line["value_fp16"] = fp16["value"]
+        line["ms_per_step_fp16"] = fp16["ms_per_step"]
+        line["roofline_fp16"] = fp16["roofline"]
+        line["clocks_fp16"] = fp16["clocks"]
+        line["gpu_launches_fp16"] = int(fp16["launches_per_step"] * args.steps)
+    line["serving"] = serving
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -440,6 +473,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage run beside an FP32 one")
     ap.add_argument("--print-kernel-rev", action="store_true")
     ap.add_argument("--n", default=None, help="override the box size, e.g. 256,256,128 (profiling cases)")
     ap.add_argument("--bodies", type=int, default=None)

@@ -926,6 +926,10 @@ int create_domain_impl(const lbm_domain_desc *desc, lbm_domain **out, bool batch
         p.staged = (es && es[0] == '1') ? 1 : 0;
         // LBM_STAGED_TEST_EXPIRE=1 (tests only): the staged kernel's waits
         // expire, which must surface as LBM_ERR_TIMEOUT
+        // LBM_PAIR=0 keeps the single-node stream-collide kernel where the
+        // two-node one applies (same results bit for bit)
+        const char *ep = std::getenv("LBM_PAIR");
+        p.pair = (ep && ep[0] == '0') ? 0 : 1;
         const char *ex = std::getenv("LBM_STAGED_TEST_EXPIRE");
         p.stage_expire_test = (ex && ex[0] == '1') ? 1 : 0;
         int sms = 0;
@@ -974,7 +978,9 @@ int create_domain_impl(const lbm_domain_desc *desc, lbm_domain **out, bool batch
     {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
-        int per = 3;
+        // one block per multiprocessor for the side-stream kernels: measured
+        // against 2 and 3, the stream-collide pass beside them loses least
+        int per = 1;
         if (const char *ev = std::getenv("LBM_SIDE_BLOCKS_PER_SM")) per = std::max(1, std::atoi(ev));
         D->side_blocks = std::max(1, sms) * per;
         // LBM_SIDE_SERIAL=1: surface kernels before k_bulk on one stream
@@ -1825,6 +1831,8 @@ int domain_bytes(const lbm_domain_desc &d, const lbm_body *hb, int n, int64_t *b
     b += 2 * (Lsz * 4 + Lsz * 1 + Lsz * 8 + nbx * 8);            // link lists and counts
     b += Lsz * ME_PER_LINK * 8;                                  // per-link contributions
     b += A * 4 + A * 1 + nbx * 8;                                // covered/uncovered lists
+    b += nbx * 6 * 8;                                            // impulsive terms of the last displacement
+    if (d.free_scheme == LBM_FREE_PREDICTOR) b += A * 4 + A * 1 + nbx * 8; // predicted lists
     b += cap * nbx * SERIES_ROW * 8 + nbx * POSE_STRIDE * 8;     // series, poses
     b += 2 * (nbx + 1) * 8 + nbx * SERIES_ROW * 8;               // prefixes, accumulators
     b += 8 + A * 4 + A * 1;                                      // flag-change list

@@ -142,6 +142,7 @@ struct Params {
     int nonper;  // 1 if any axis is non-periodic
     int exact;   // FP64 mode: link geometry in FP64 (else FP32)
     int staged;  // reduced precision: stream-collide from rows staged in shared memory
+    int pair;    // reduced precision: two nodes per thread where that kernel applies
     int stage_expire_test; // test hook: the staged kernel issues no copy, so its waits expire
     int nsm;     // multiprocessors of the device
     int zouhe;   // wall / inlet faces are Zou-He nodes (else half-way links)

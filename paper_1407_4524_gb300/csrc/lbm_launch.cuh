@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "lbm_internal.h"
+#include "lbm_pair.cuh"
 #include "lbm_stage.cuh"
 
 namespace lbm {
@@ -72,7 +73,16 @@ template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &
     typename P::S *dst = (typename P::S *)sb.dst;
     const typename P::C *mt = (const typename P::C *)sb.mac_t;
     typename P::C *mt1 = (typename P::C *)sb.mac_t1;
-    if (fm == FM_PERIODIC)
+    bool pair = false;
+    if constexpr (!P::exact) pair = p.pair && pair_ok(p, fm);
+    if (pair) {
+        if constexpr (!P::exact) {
+            if (fm == FM_PERIODIC)
+                k_bulk_pair<L, P, FM_PERIODIC><<<pair_grid(p), pair_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
+            else
+                k_bulk_pair<L, P, FM_XFACES><<<pair_grid(p), pair_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
+        }
+    } else if (fm == FM_PERIODIC)
         k_bulk<L, P, FM_PERIODIC><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
     else if (fm == FM_XFACES)
         k_bulk<L, P, FM_XFACES><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
