@@ -414,16 +414,13 @@ def run_serving(args, dev):
     def rnd(d):
         return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
 
-    by_slots = {}
-    for slots in sorted({args.serving_slots, 256}):
-        res, _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=slots, ticks_per_launch=32, device=dev)
-        by_slots[slots] = res
-    batched = by_slots[args.serving_slots]
+    batched, _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=args.serving_slots, ticks_per_launch=32,
+                                       device=dev)
     seq, _ = serving.serve_sequential(trace, device=dev)
     # the same trace with smallest-work-first queues, for both loops (fewer
     # resident solves suit this order: the small ones are not slowed by sharing)
     sjf_b = {}
-    for slots in sorted({8, args.serving_slots}):
+    for slots in (8,):
         sjf_b[slots], _ = serving.serve_batched(trace, budget_bytes=budget, max_slots=slots, ticks_per_launch=32,
                                                 device=dev, policy="sjf")
     sjf_s, _ = serving.serve_sequential(trace, device=dev, policy="sjf")
@@ -433,7 +430,6 @@ def run_serving(args, dev):
         "budget_bytes": budget,
         "slots": args.serving_slots,
         "batched": rnd(batched),
-        "batched_by_slots": {str(k): rnd(v) for k, v in by_slots.items()},
         "one_at_a_time": rnd(seq),
         "sjf": {"batched_by_slots": {str(k): rnd(v) for k, v in sjf_b.items()}, "one_at_a_time": rnd(sjf_s)},
         "mlups_ratio": round(batched["mlups"] / seq["mlups"], 3) if seq["mlups"] else None,
@@ -477,10 +473,10 @@ def main():
     ap.add_argument("--print-kernel-rev", action="store_true")
     ap.add_argument("--n", default=None, help="override the box size, e.g. 256,256,128 (profiling cases)")
     ap.add_argument("--bodies", type=int, default=None)
-    ap.add_argument("--serving-requests", type=int, default=40,
+    ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests of the serving trace (0: skip the serving measurement)")
     ap.add_argument("--serving-slots", type=int, default=16,
-                    help="resident solves at most in the batched serving run (a run with 256 is added)")
+                    help="resident solves at most in the FIFO batched serving run")
     args = ap.parse_args()
     if args.n:
         args.n = tuple(int(v) for v in args.n.split(","))

@@ -76,12 +76,7 @@ template <class L, class P> cudaError_t bulk_t(const Params &p, const StepBufs &
     bool pair = false;
     if constexpr (!P::exact) pair = p.pair && pair_ok(p, fm);
     if (pair) {
-        if constexpr (!P::exact) {
-            if (fm == FM_PERIODIC)
-                k_bulk_pair<L, P, FM_PERIODIC><<<pair_grid(p), pair_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
-            else
-                k_bulk_pair<L, P, FM_XFACES><<<pair_grid(p), pair_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
-        }
+        if constexpr (!P::exact) k_bulk_pair<L, P><<<pair_grid(p), pair_block(p), 0, s>>>(p, src, dst, sb.flags, mt1);
     } else if (fm == FM_PERIODIC)
         k_bulk<L, P, FM_PERIODIC><<<bulk_grid(p), bulk_block(p), 0, s>>>(p, src, dst, sb.flags, mt, mt1);
     else if (fm == FM_XFACES)

@@ -14,9 +14,8 @@
 // 3 cu + 4.5 cu^2 - 1.5 u^2 at -cu is the negated fma chain
 // -(cu (3 - 4.5 cu) + 1.5 u^2), also exact.
 //
-// Used for domains without a body force whose x extent is even, in the
-// fully periodic and the x-faces face modes; the warps that hold a node on a
-// non-periodic x face step their nodes with the single-node code.
+// Used for fully periodic domains without a body force whose x extent is
+// even.
 #pragma once
 
 #include "lbm_step.cuh"
@@ -30,16 +29,16 @@ struct F2 {
     unsigned long long v;
 };
 
+// lane 0 in the low 32 bits (plain integer packing: the compiler pairs the
+// registers itself)
 __device__ __forceinline__ F2 f2(float a, float b) {
     F2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    r.v = ((unsigned long long)__float_as_uint(b) << 32) | (unsigned long long)__float_as_uint(a);
     return r;
 }
 __device__ __forceinline__ F2 f2s(float a) { return f2(a, a); }
 __device__ __forceinline__ float2 unf2(F2 x) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(x.v));
-    return r;
+    return make_float2(__uint_as_float((unsigned)(x.v & 0xffffffffull)), __uint_as_float((unsigned)(x.v >> 32)));
 }
 __device__ __forceinline__ F2 vadd(F2 a, F2 b) {
     F2 r;
@@ -176,31 +175,20 @@ template <> struct Pair<float> {
     }
 };
 
-// the nodes (x0, y, z), (x0 + 1, y, z) of every thread (x0 even; nx even)
-template <class L, class P, int FM>
-__global__ void __launch_bounds__(PAIR_THREADS, 8) k_bulk_pair(Params p, const typename P::S *__restrict__ src,
-                                                            typename P::S *__restrict__ dst,
-                                                            const uint8_t *__restrict__ flags,
-                                                            const typename P::C *__restrict__ mac_t,
-                                                            typename P::C *__restrict__ mac_t1) {
+// The nodes (x0, y, z) and (x0 + 1, y, z) of the calling thread (x0 even, nx
+// even, every axis periodic); all 32 lanes of the warp call it for the same
+// row, lanes past the row with x0 >= nx.
+template <class L, class P>
+__device__ __forceinline__ void pair_nodes(const Params &p, const typename P::S *__restrict__ src,
+                                           typename P::S *__restrict__ dst, const uint8_t *__restrict__ flags,
+                                           typename P::C *__restrict__ mac_t1, int x0, int y, int z) {
     using S = typename P::S;
     using PT = Pair<S>;
     using T = typename PT::T;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y, z = blockIdx.z;
     const int nx = p.nx;
     const bool valid = x0 < nx;
-    if constexpr (FM == FM_XFACES) {
-        // warps with a node on an x face: the single-node code (face rules)
-        if (__any_sync(FULL, valid && (x0 == 0 || x0 + 2 >= nx))) {
-            if (valid) {
-                bulk_node<L, P, FM>(p, src, dst, flags, mac_t, mac_t1, x0, y, z);
-                bulk_node<L, P, FM>(p, src, dst, flags, mac_t, mac_t1, x0 + 1, y, z);
-            }
-            return;
-        }
-    }
     const int xc = valid ? x0 : nx - 2; // lanes past the row load in bounds, store nothing
     const unsigned ny = (unsigned)p.ny, N32 = (unsigned)p.N;
     const unsigned cell0 = ((unsigned)z * ny + (unsigned)y) * (unsigned)nx + (unsigned)xc;
@@ -262,9 +250,24 @@ __global__ void __launch_bounds__(PAIR_THREADS, 8) k_bulk_pair(Params p, const t
     }
 }
 
-// the pair kernel's conditions: no body force, nx even, a face mode without
-// y / z faces, reduced precision
-inline bool pair_ok(const Params &p, int fm) { return !p.has_force && p.nx % 2 == 0 && p.nx >= 4 && fm != FM_GENERAL; }
+// resident blocks of PAIR_THREADS the two-node kernel is built for: 8 (64
+// registers) with FP16 storage, 7 with FP32 (its float2 pairs need 68
+// registers to run without spills)
+template <class P> constexpr int pair_min_blocks() { return sizeof(typename P::S) == 2 ? 8 : 7; }
+
+// every thread a pair of one row: blockIdx.y = y, blockIdx.z = z
+template <class L, class P>
+__global__ void __launch_bounds__(PAIR_THREADS, pair_min_blocks<P>()) k_bulk_pair(Params p, const typename P::S *__restrict__ src,
+                                                            typename P::S *__restrict__ dst,
+                                                            const uint8_t *__restrict__ flags,
+                                                            typename P::C *__restrict__ mac_t1) {
+    pair_nodes<L, P>(p, src, dst, flags, mac_t1, 2 * (blockIdx.x * blockDim.x + threadIdx.x), blockIdx.y, blockIdx.z);
+}
+
+// the pair kernel's conditions: no body force, nx even, every axis periodic,
+// reduced precision.  (Where faces cut the rows, the face rules of the
+// single-node kernel measured faster than two-node rows with face lanes.)
+inline bool pair_ok(const Params &p, int fm) { return !p.has_force && p.nx % 2 == 0 && p.nx >= 4 && fm == FM_PERIODIC; }
 
 inline dim3 pair_block(const Params &p) {
     int bx = PAIR_THREADS;

@@ -39,6 +39,12 @@ CASES = {
         lattice="D2Q9", n=(98, 50), tau=0.7, u0=(0.03, 0.01),
         bodies=[dict(shape="cylinder", R=7.2, X0=(30.6, 24.3), U=(0.02, -0.01), W=0.002),
                 dict(shape="ellipse", R=8.1, R2=4.2, theta0=0.5, X0=(70.2, 20.4), W=-0.001)]),
+    "d2q9_channel_walls": dict(  # walls on y: the face rows fall back (general face mode)
+        lattice="D2Q9", n=(130, 42), tau=0.6, edges={"x": ("inlet", "outlet"), "y": ("wall", "wall")},
+        inlet={"profile": "parabolic", "u": 0.05}, bodies=[dict(shape="cylinder", R=6.3, X0=(32.4, 20.2))]),
+    "d3q19_box_walls": dict(  # walls on z, periodic x and y
+        lattice="D3Q19", n=(72, 30, 28), tau=0.7, edges={"z": ("wall", "wall")}, u0=(0.02, 0.0, 0.0),
+        bodies=[dict(shape="sphere", R=5.2, X0=(30.3, 14.1, 13.6), U=(0.01, 0.0, 0.0))]),
     "free_spheres": dict(
         lattice="D3Q19", n=(40, 34, 32), tau=0.8, u0=(0.0, 0.0, 0.0),
         bodies=[dict(shape="sphere", R=5.1, X0=(12.6, 14.2, 15.1), U=(0.01, 0.0, -0.005), free=True,
@@ -82,7 +88,7 @@ def test_pair_kernel_bit_identical(name, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("name", ["box_moving_spheres", "channel_zouhe", "d2q9_periodic"])
+@pytest.mark.parametrize("name", ["box_moving_spheres", "channel_zouhe", "d2q9_periodic", "d2q9_channel_walls"])
 def test_pair_kernel_vs_oracle(oracle_mod, name, prec):
     from paper_1407_4524_gb300 import lbm
     spec = dict(CASES[name], precision=prec)
