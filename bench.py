@@ -439,7 +439,8 @@ def run_serving(args, dev):
 
 # the sources that define the stream-collide kernel and its launch (the
 # kernel the traffic figure belongs to)
-BULK_SOURCES = ("lbm_dev.cuh", "lbm_step.cuh", "lbm_launch.cuh", "lbm_stage.cuh", "lbm_fp32.cu", "lbm_fp64.cu")
+BULK_SOURCES = ("lbm_dev.cuh", "lbm_step.cuh", "lbm_pair.cuh", "lbm_launch.cuh", "lbm_stage.cuh", "lbm_fp32.cu",
+                "lbm_fp64.cu")
 
 
 def _kernel_rev() -> str:
