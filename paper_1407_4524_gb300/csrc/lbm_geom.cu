@@ -442,8 +442,10 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom1(Params p, GeomArgs g) {
         region_lo(p, B, P, REGION_MARGIN, lo);
         const uint16_t me = (uint16_t)(b + 1);
         const float Rin = body_rin(B), Rout = body_rout(B);
-        for (int j = 0; j < GEOM_CELLS; ++j) {
-            RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+        RegionWalk w;
+        walk_start(w, p, B, lo, cm.y);
+        for (int j = 0; j < GEOM_CELLS; ++j, walk_next(w)) {
+            RegionCell rc = walk_cell(w, p, lo);
             if (!rc.valid) continue;
             const float dist = frame_dist(p, B, F, rc);
             // link mode: the nodes whose moments the cut links of the next
@@ -552,10 +554,13 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2l(Params p, GeomArgs g) 
         const uint16_t me = (uint16_t)(b + 1);
         unsigned mj[GEOM_CELLS]; // directions of each cell's cut links to the body
         int nl = 0;
+        const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+        RegionWalk w;
+        walk_start(w, p, B, lo, cm.y);
 #pragma unroll
-        for (int j = 0; j < GEOM_CELLS; ++j) {
+        for (int j = 0; j < GEOM_CELLS; ++j, walk_next(w)) {
             mj[j] = 0u;
-            const RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+            const RegionCell rc = walk_cell(w, p, lo);
             if (!rc.valid) continue;
             const float dist = frame_dist(p, B, F, rc);
             if (dist < Rin - 2.0f || dist > Rout + 3.0f) continue;
@@ -570,10 +575,16 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2l(Params p, GeomArgs g) 
             }
             if (solid1 || dist > Rout + 1.5f) continue;
             unsigned m = 0u;
+            if (inner1(p, rc.x, rc.y, rc.z)) {
 #pragma unroll
-            for (int i = 1; i < L::Q; ++i) {
-                const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
-                m |= ((a >= 0 && g.owner_t1[a] == me) ? 1u : 0u) << i;
+                for (int i = 1; i < L::Q; ++i)
+                    m |= (g.owner_t1[nbr1_inner<L>(rc.cell, sy, sz, i)] == me ? 1u : 0u) << i;
+            } else {
+#pragma unroll
+                for (int i = 1; i < L::Q; ++i) {
+                    const long long a = nbr<L>(p, rc.x, rc.y, rc.z, i, 1);
+                    m |= ((a >= 0 && g.owner_t1[a] == me) ? 1u : 0u) << i;
+                }
             }
             mj[j] = m;
             nl += __popc(m);
@@ -586,11 +597,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_fgeom2l(Params p, GeomArgs g) 
         __syncthreads();
         long long at = (long long)base_s + first;
         if (!nl) continue;
+        walk_start(w, p, B, lo, cm.y);
 #pragma unroll
-        for (int j = 0; j < GEOM_CELLS; ++j) {
+        for (int j = 0; j < GEOM_CELLS; ++j, walk_next(w)) {
             const unsigned m = mj[j];
             if (!m) continue;
-            const RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+            const RegionCell rc = walk_cell(w, p, lo);
             float df[3];
             frame_disp_f(p, F, rc.x, rc.y, rc.z, df);
             for (int i = 1; i < L::Q; ++i) {
@@ -661,8 +673,10 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_macband(Params p, GeomArgs g) 
     int lo[3];
     region_lo(p, B, P, REGION_MARGIN, lo);
     const float Rout = body_rout(B);
-    for (int j = 0; j < GEOM_CELLS; ++j) {
-        RegionCell rc = region_cell_i(p, B, lo, cm.y, j);
+    RegionWalk w;
+    walk_start(w, p, B, lo, cm.y);
+    for (int j = 0; j < GEOM_CELLS; ++j, walk_next(w)) {
+        RegionCell rc = walk_cell(w, p, lo);
         if (!rc.valid) continue;
         if (frame_dist(p, B, F, rc) <= Rout + MAC_BAND) g.flags[rc.cell] |= FL_MAC;
     }
