@@ -1740,7 +1740,7 @@ struct lbm_batch {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // extra capture streams: the bulk kernels of different groups run on
     // parallel branches of the tick graph (their solves are disjoint)
-    static constexpr int NBRANCH = 3;
+    static constexpr int NBRANCH = 7;
     cudaStream_t sb[NBRANCH] = {};
     cudaEvent_t ev_branch[NBRANCH] = {};
     int tpl = 32;
@@ -1770,6 +1770,10 @@ struct lbm_batch {
     std::vector<void *> table_allocs;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;
+    // stream-collide launches per resident solve (up to PER_SOLVE_MAX solves)
+    // instead of one batched kernel per group; LBM_BATCH_GROUPED=1 turns it off
+    static constexpr int PER_SOLVE_MAX = 32;
+    bool per_solve = true;
 
     void *alloc(size_t n) {
         if (n == 0) n = 256;
@@ -1929,9 +1933,23 @@ int batch_rebuild(lbm_batch *B) {
     // one tick: fork; the boundary kernels of every group on the high-priority
     // branch, the bulk kernel of each group on a branch of its own (groups
     // beyond the branches share them); join; end-of-tick kernel
+    // With few resident solves each solve's stream-collide pass is a launch of
+    // the standalone kernel on a branch of its own (its parameters in the
+    // constant bank, its source and destination arrays fixed per tick: the
+    // solves advance in lockstep, an even number of ticks per replay, so each
+    // keeps the parity it had at capture); with many solves, or an odd tick
+    // count, one batched kernel per group.  A solve that finishes inside a replay keeps being streamed (not
+    // read: its series rows stop at t_end) until the tables are rebuilt.
     int ngrp = 0;
     for (int k = 0; k < NG; ++k) ngrp += B->g[k].nslots ? 1 : 0;
-    const int nbr = std::min(ngrp, lbm_batch::NBRANCH + 1); // branch 0 is B->s itself
+    std::vector<int> live; // resident unfinished slots, largest first
+    for (int sl = 0; sl < (int)B->slots.size(); ++sl)
+        if (B->slots[sl].D && B->slots[sl].D->t < B->slots[sl].t_end) live.push_back(sl);
+    std::sort(live.begin(), live.end(), [&](int a, int b) { return B->slots[a].D->p.N > B->slots[b].D->p.N; });
+    // (an even tick count per replay keeps each solve's parity pattern from one
+    // replay to the next)
+    const bool per_solve = B->per_solve && B->tpl % 2 == 0 && (int)live.size() <= lbm_batch::PER_SOLVE_MAX;
+    const int nbr = std::min(per_solve ? (int)live.size() : ngrp, lbm_batch::NBRANCH + 1); // branch 0 is B->s
     for (int t = 0; t < B->tpl && e == cudaSuccess; ++t) {
         if ((e = cudaEventRecord(B->ev_fork, B->s)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(B->s2, B->ev_fork, 0)) != cudaSuccess) break;
@@ -1942,9 +1960,24 @@ int batch_rebuild(lbm_batch *B) {
             if (G.nslots == 0) continue;
             if (G.grid > 0)
                 e = launch_bbnd(G.Q, G.prec, B->dsolves, G.slots, G.node_pre, G.nslots, G.grid, B->s2);
+            if (per_solve) continue;
             const int b = gi++ % nbr;
             cudaStream_t bs = b == 0 ? B->s : B->sb[b - 1];
             if (e == cudaSuccess) e = launch_bbulk(G.Q, G.kind, G.fm, B->dsolves, G.work, G.nwork, bs);
+        }
+        if (per_solve) {
+            for (int q = 0; q < (int)live.size() && e == cudaSuccess; ++q) {
+                lbm_domain *D = B->slots[live[q]].D;
+                const int par = (int)((D->t + t) & 1);
+                StepBufs sbuf{};
+                sbuf.src = D->pop[par];
+                sbuf.dst = D->pop[par ^ 1];
+                sbuf.mac_t = D->mac[par];
+                sbuf.mac_t1 = D->mac[par ^ 1];
+                sbuf.flags = D->flags;
+                const int b = q % nbr;
+                e = launch_bulk(D->Q, D->prec, D->p, sbuf, b == 0 ? B->s : B->sb[b - 1]);
+            }
         }
         for (int b = 1; b < nbr && e == cudaSuccess; ++b) {
             if ((e = cudaEventRecord(B->ev_branch[b - 1], B->sb[b - 1])) != cudaSuccess) break;
@@ -1989,6 +2022,7 @@ int lbm_batch_create(const lbm_batch_desc *desc, lbm_batch **out) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d.device);
     B->side_blocks = std::max(1, sms) * 3;
+    if (const char *eg = std::getenv("LBM_BATCH_GROUPED")) B->per_solve = eg[0] != '1';
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (d.stream) {
