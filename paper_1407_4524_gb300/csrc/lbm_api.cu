@@ -1725,10 +1725,11 @@ int lbm_launches_per_step(const lbm_domain *D, int *out) {
 // device keeps a table of SolveDev records (one per slot) that the batched
 // kernels read; for each (lattice, precision) group the host keeps a block
 // work table (slot, first cell) for the bulk kernel and a prefix of the
-// boundary-node counts for the boundary-node kernel.  A tick is: fork; bulk
-// kernels of every group on the batch stream and boundary-node kernels on the
-// high-priority side stream (disjoint nodes, both read fhat(t)); join; one
-// end-of-step kernel for every resident solve.  ticks_per_launch ticks are
+// boundary-node counts for the boundary-node kernel.  A tick is: fork; the
+// stream-collide passes (one launch per resident solve on parallel branches
+// for up to PER_SOLVE_MAX solves, else the batched kernel of every group) and
+// the boundary-node kernels on the high-priority side stream (disjoint nodes,
+// both read fhat(t)); join; one end-of-step kernel for every resident solve.  ticks_per_launch ticks are
 // captured once into a CUDA graph, re-captured whenever the resident set
 // changes.  Admission and release synchronise the batch stream, so the tables
 // are never rewritten under a running graph.

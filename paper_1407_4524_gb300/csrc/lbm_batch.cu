@@ -1,9 +1,10 @@
 // lbm_batch.cu -- batched kernels of the serving mode.
 //
 // A serving batch keeps many independent solves resident (reduced-precision
-// modes, static bodies) and advances all of them by one step per tick with
-// five launches in total, whatever their number and sizes: the bulk kernel
-// of each lattice over a block table covering every solve's rows, the
+// modes, static bodies) and advances all of them by one step per tick: the
+// stream-collide pass of each solve (the standalone kernel, one launch per
+// solve on parallel graph branches while few are resident; with many, the
+// batched kernel below over a block table covering every solve's rows), the
 // boundary-node kernel of each lattice over the concatenated node lists, and
 // one end-of-step kernel (series rows, step counters).  Every solve runs the
 // same per-node arithmetic as a standalone domain, and its force/torque sums
