@@ -37,20 +37,25 @@ def test_resume_continues_bit_for_bit(dim, name, prec):
     b.close()
 
 
+@pytest.mark.parametrize("scheme", ["explicit", "aidun", "predictor"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_resume_free_bodies(prec):
+def test_resume_free_bodies(prec, scheme):
+    """the backward-set scheme carries the impulsive terms of the last
+    displacement from step to step: they travel with the snapshot"""
     from paper_1407_4524_gb300 import lbm
-    spec = dict(FREE["ellipse_channel"], precision=prec)
+    spec = dict(FREE["ellipse_channel"], precision=prec, free_scheme=scheme)
     a = lbm.Domain(spec, device=0)
     a.step(30)
     blob = a.save_state()
     a.step(50)
     want = a.body_state()
+    want_ft = a.force_torque("lattice")
     a.close()
     b = lbm.Domain(spec, device=0)
     b.load_state(blob)
     b.step(50)
     assert np.array_equal(b.body_state(), want)
+    assert np.array_equal(b.force_torque("lattice"), want_ft)
     b.close()
 
 
