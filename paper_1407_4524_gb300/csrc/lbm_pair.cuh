@@ -185,7 +185,6 @@ __device__ __forceinline__ void pair_nodes(const Params &p, const typename P::S 
     using S = typename P::S;
     using PT = Pair<S>;
     using T = typename PT::T;
-    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nx = p.nx;
     const bool valid = x0 < nx;
@@ -195,8 +194,9 @@ __device__ __forceinline__ void pair_nodes(const Params &p, const typename P::S 
     const unsigned fl2 = __ldg(reinterpret_cast<const unsigned short *>(flags + cell0));
     const unsigned fl0 = fl2 & 0xffu, fl1 = fl2 >> 8;
     const uint8_t skip = FL_SOLID | (p.linkmode ? 0 : FL_BND);
+    // (the pulls do not wait for the flags: a pair with no node to store is
+    // stepped all the same, so the flag load overlaps the population loads)
     const bool act0 = valid && !(fl0 & skip), act1 = valid && !(fl1 & skip);
-    if (!__any_sync(FULL, act0 || act1)) return;
     const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
     // the element left of x0 (lane 0) and the pair right of x0 + 1 (lane 31,

@@ -812,10 +812,14 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
     }
     const long long cell = cell_of(p, x, y, z);
     const uint8_t fl = __ldg(flags + cell);
-    if (fl & FL_SOLID) return;
-    if constexpr (!P::exact) {
-        if (!p.linkmode && (fl & FL_BND)) return; // boundary nodes: k_bnd
+    if constexpr (P::exact) {
+        if (fl & FL_SOLID) return;
     }
+    // reduced precision: the pulls do not wait for the flag (a solid node, or
+    // a boundary node left to k_bnd, is stepped and not stored), so the flag
+    // load and the population loads are in flight together
+    bool store = true;
+    if constexpr (!P::exact) store = !(fl & FL_SOLID) && (p.linkmode || !(fl & FL_BND));
     C f[L::Q];
     pull_all<L, P, FM>(p, src, mac_t, x, y, z, cell, f);
     if constexpr (P::exact) {
@@ -831,9 +835,10 @@ __device__ __forceinline__ void bulk_node(const Params &p, const typename P::S *
     } else {
         float drho, u[3];
         moments_f<L>(p, f, drho, u);
-        if (p.linkmode && (fl & FL_MAC)) store_mac(mac_t1, cell, drho, u);
+        if (store && p.linkmode && (fl & FL_MAC)) store_mac(mac_t1, cell, drho, u);
         collide_f<L>(p, f, drho, u);
     }
+    if (!store) return;
     const unsigned N32 = (unsigned)p.N, c32 = (unsigned)cell;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) stS(dst + (size_t)N32 * (unsigned)i + c32, f[i]);
