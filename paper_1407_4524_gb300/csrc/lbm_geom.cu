@@ -379,34 +379,43 @@ __global__ void k_import(Params p, const double *in, typename P::S *pop) {
 // Reduced-precision modes.  Momentum-exchange sums are order independent
 // there (exact fixed point), so lists are appended with atomics.
 
+// Three independent parts, one block each, so that their memory latencies
+// overlap instead of adding up: block 0 the link tiles of t (and the empty
+// lists of t+1), block 1 the solid flags of t+1 queued by the previous step's
+// geometry, block 2 the poses of t and t+1.
 __global__ void __launch_bounds__(1024) k_fprep(Params p, const BodyDev *bodies, double *poses, long long t_arg,
                                                 const unsigned long long *tdev, uint8_t *flags,
                                                 unsigned long long *chg_cnt, const uint32_t *chg_cell,
                                                 const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
                                                 unsigned long long *bn_mov_next_cnt, const long long *link_cnt_t,
                                                 long long *link_cnt_t1, long long *tile_pre) {
+    if (blockIdx.x == 0) {
+        if (p.linkmode && link_cnt_t) {
+            // link mode: the cut links of t are complete (static bodies: from
+            // their placement; moving ones: appended by the previous step's
+            // geometry); the tiles of the link kernel follow them, and the
+            // moving bodies' lists of t+1 start empty
+            prefix_over_bodies(p, link_cnt_t, tile_pre, 1);
+            for (int b = threadIdx.x; b < p.nb; b += blockDim.x)
+                if (bodies[b].moving) link_cnt_t1[b] = 0;
+        }
+        return;
+    }
+    if (blockIdx.x == 1) {
+        const long long n = (long long)min((unsigned long long)chg_cap, *chg_cnt);
+        for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+            const long long c = chg_cell[e];
+            flags[c] = (uint8_t)((flags[c] & ~(FL_SOLID | FL_BND)) | chg_val[e]);
+        }
+        __syncthreads(); // every thread has read the count
+        if (threadIdx.x == 0) {
+            *chg_cnt = 0ull;
+            *bn_mov_next_cnt = 0ull;
+        }
+        return;
+    }
     const long long t = tdev ? (long long)*tdev : t_arg; // the device step counter, when given
-    if (p.linkmode && link_cnt_t) {
-        // link mode: the cut links of t are complete (static bodies: from their
-        // placement; moving ones: appended by the previous step's geometry);
-        // the tiles of the link kernel follow them, and the moving bodies'
-        // lists of t+1 start empty
-        prefix_over_bodies(p, link_cnt_t, tile_pre, 1);
-        for (int b = threadIdx.x; b < p.nb; b += 1024)
-            if (bodies[b].moving) link_cnt_t1[b] = 0;
-        __syncthreads();
-    }
-    const long long n = (long long)min((unsigned long long)chg_cap, *chg_cnt);
-    for (long long e = threadIdx.x; e < n; e += 1024) {
-        const long long c = chg_cell[e];
-        flags[c] = (uint8_t)((flags[c] & ~(FL_SOLID | FL_BND)) | chg_val[e]);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *chg_cnt = 0ull;
-        *bn_mov_next_cnt = 0ull;
-    }
-    for (int b = threadIdx.x; b < p.nb; b += 1024) {
+    for (int b = threadIdx.x; b < p.nb; b += blockDim.x) {
         apm_cnt[b] = 0;
         double *P = poses + (long long)b * POSE_STRIDE;
         pose(bodies[b], t, P);
@@ -704,7 +713,7 @@ cudaError_t launch_fprep(const Params &p, const BodyDev *bodies, double *poses, 
                          const uint32_t *chg_cell, const uint8_t *chg_val, long long chg_cap, long long *apm_cnt,
                          unsigned long long *bn_mov_next_cnt, const long long *link_cnt_t, long long *link_cnt_t1,
                          long long *tile_pre, cudaStream_t s) {
-    k_fprep<<<1, 1024, 0, s>>>(p, bodies, poses, t, tdev, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt,
+    k_fprep<<<3, 1024, 0, s>>>(p, bodies, poses, t, tdev, flags, chg_cnt, chg_cell, chg_val, chg_cap, apm_cnt,
                                bn_mov_next_cnt, link_cnt_t, link_cnt_t1, tile_pre);
     return cudaGetLastError();
 }
